@@ -1,0 +1,195 @@
+/*
+ * dd.h -- C ABI of the GB300 discord-discovery library (libdd.so).
+ *
+ * Problem (Polyakov & Zymbler, arXiv:1901.00155, Section 2.1 and Eq. 1-2):
+ * given a series T = (t_0 .. t_{m-1}) and a subsequence length n, let
+ * N = m - n + 1 and let T_i = (t^_i .. t^_{i+n-1}) be the i-th subsequence of
+ * the series z-normalised as a whole (Eq. 2: t^ = (t - mu) / sigma, mu and the
+ * population sigma over all m points; sigma == 0 gives t^ == 0).  Two
+ * subsequences are a non-self match when |i - j| >= n.  The nearest-neighbour
+ * distance of T_i is nn_i = min_{|i-j|>=n} ED(T_i, T_j) (Eq. 1), and the discord
+ * is the i maximising nn_i; ties go to the smallest i.  Indices are 0-based
+ * (the paper counts from 1).
+ *
+ * The search follows PhiDD (Algorithms 2-4): SAX words (Eq. 3-4, Eq. 9) order
+ * the rows -- the rarest words (Cand, Eq. 7) are searched first
+ * (PotentialDiscord, Algorithm 3), then every other row (RefineDiscord,
+ * Algorithm 4), each row scanning the rows that share its word (Index_Word,
+ * Eq. 10) first and being abandoned as soon as one distance falls below the
+ * best-so-far.  The ordering only changes the speed, never the result.
+ *
+ * Conventions for every entry point
+ *   - Device pointers are CUDA device addresses of the current device; the
+ *     caller owns them and keeps them valid and unmodified until the call's
+ *     work on `stream` has finished.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *   - Errors are returned as dd_status_t; nothing is printed and nothing
+ *     aborts the process.  After DD_ECUDA the plan should be destroyed.
+ *   - A plan holds per-(m, n, options) device workspace and serves one call at
+ *     a time: a call on a plan whose previous call is still being set up on
+ *     another host thread returns DD_EBUSY.  Calls on one plan must be ordered
+ *     on one stream (or synchronised by the caller).
+ *   - Valid problems need n >= 1 and N >= 2n (m >= 3n - 1), so that every
+ *     subsequence has at least one non-self match; otherwise DD_EINVAL.
+ *   - A series holding NaN or +-Inf gives DD_ENONFINITE.
+ */
+#ifndef DD_H_
+#define DD_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define DD_API __attribute__((visibility("default")))
+#else
+#define DD_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dd_plan_s* dd_plan_t;
+
+typedef enum {
+    DD_OK = 0,
+    DD_EINVAL = 1,      /* bad sizes, null pointers, bad options */
+    DD_ENOMEM = 2,      /* device (or pinned host) allocation failed / workspace too small */
+    DD_ENONFINITE = 3,  /* T holds NaN or Inf */
+    DD_ETIMEOUT = 4,    /* a bounded device-side wait expired */
+    DD_ECUDA = 5,       /* any other CUDA runtime error */
+    DD_EBUSY = 6,       /* the plan is in use by another host thread */
+    DD_ENOTSUP = 7      /* option combination not supported for these sizes */
+} dd_status_t;
+
+/* Arithmetic of the distance tiles.
+ *   DD_FP32     direct differences sum_k (x_k - y_k)^2 in FP32 on the CUDA cores
+ *               (Eq. 1 squared); nn_distance within ~1e-5 relative.
+ *   DD_TC_FP16  Gram tiles <x', y'> of mean-centred rows on the tcgen05 tensor
+ *   DD_TC_BF16  cores (FP16 / BF16 operands, FP32 accumulation), a rigorous
+ *               error bound per row, and exact FP64 rescoring of every row the
+ *               bound cannot rule out: exact index, FP64 distance. */
+typedef enum { DD_FP32 = 0, DD_TC_FP16 = 1, DD_TC_BF16 = 2 } dd_precision_t;
+
+typedef struct {
+    int32_t precision;     /* dd_precision_t (default DD_FP32) */
+    int32_t paa_w;         /* PAA segments per word, Eq. 3 (default 4; min(paa_w, n) is used) */
+    int32_t alphabet;      /* SAX alphabet size, Eq. 4 (default 4); alphabet^paa_w <= 4096 */
+    int32_t early_abandon; /* 1 = abandon rows against the best-so-far (default); 0 = full scans */
+    int32_t paa_mode;      /* 0 = PAA of each subsequence z-normalised on its own (default),
+                              1 = PAA of the globally normalised values */
+    int32_t phase1_max;    /* at most this many Cand rows run in phase 1 (default 4096) */
+    int32_t refine_k;      /* rows with the largest first-wave upper bounds that get a full scan
+                              before the other survivors, to raise the best-so-far (default 512) */
+    int32_t reserved[9];   /* must be zero */
+} dd_options_t;
+
+typedef struct {
+    int64_t index;          /* 0-based start of the discord (-1 if status != DD_OK) */
+    double nn_distance;     /* ED from the discord to its nearest non-self match, on the
+                               z-normalised series */
+    int32_t status;         /* dd_status_t of the call that produced it */
+    int32_t exact;          /* 1: nn_distance is an FP64 rescore (tensor-core forms) */
+    int64_t computed_pairs; /* distance pairs evaluated on the GPU by the search */
+    int64_t candidates;     /* rows that completed a full scan (FP32) / rows rescored in FP64 (TC) */
+} dd_result_t;
+
+/* Read-only device views of a plan's preparation arrays (Section 3.1 data
+ * structures), for inspection and testing.  All pointers are device
+ * addresses owned by the plan; valid until dd_plan_destroy. */
+typedef struct {
+    int64_t m, N;
+    int32_t n, dict_size;
+    const double* stats;       /* [0]=mu [1]=sigma [2]=max|t^| of the series (Eq. 2) */
+    const double* P1;          /* [m+1] exclusive prefix sums of t^ (FP64) */
+    const double* P2;          /* [m+1] exclusive prefix sums of t^^2 (FP64) */
+    const double* mu_w;        /* [N] mean of each subsequence of t^ */
+    const double* c_w;         /* [N] centred sum of squares of each subsequence of t^ */
+    const int32_t* code;       /* [N] SAX word of each subsequence (Eq. 3, 4, 9) */
+    const int32_t* freq_hist;  /* [dict] rows per word (Eq. 8 is freq_i = freq_hist[code_i]) */
+    const int32_t* order;      /* [N] row order: words by ascending frequency (then word),
+                                  rows ascending inside a word = Index_Word (Eq. 10) */
+    const int32_t* word_start; /* [dict] offset of each word's rows in `order` */
+    const int32_t* ncand;      /* [1] |Cand| (Eq. 7): Cand = order[0 .. ncand) */
+    const float* t32;          /* [m] t^ rounded to FP32 */
+} dd_view_t;
+
+/* ---- plans ------------------------------------------------------------- */
+
+/* Fills the defaults listed above. */
+DD_API void dd_options_default(dd_options_t* opt);
+
+/* Bytes of device workspace a plan for (m, n, opt) needs (0 if invalid). */
+DD_API size_t dd_plan_footprint(int64_t m, int32_t n, const dd_options_t* opt);
+
+/* Creates a plan for series of length m and subsequence length n on the
+ * current device.  opt == NULL means defaults.  workspace == NULL: the plan
+ * allocates dd_plan_footprint() bytes itself (cudaMalloc) and frees them in
+ * dd_plan_destroy; otherwise the caller passes device memory of at least that
+ * size (256-byte aligned) that it owns and keeps alive until dd_plan_destroy.
+ * Errors: DD_EINVAL (sizes, options), DD_ENOMEM, DD_ECUDA. */
+DD_API dd_status_t dd_plan_create(dd_plan_t* plan, int64_t m, int32_t n, const dd_options_t* opt,
+                           void* workspace, size_t workspace_bytes);
+
+/* Releases the plan (and its workspace if the plan allocated it). NULL is a no-op. */
+DD_API void dd_plan_destroy(dd_plan_t plan);
+
+/* ---- discord search ---------------------------------------------------- */
+
+/* Algorithm 2 (PhiDD) on the device: preparation, PotentialDiscord,
+ * RefineDiscord, argmax.  T_dev: m float32 values in device memory.
+ * Enqueues everything on `stream`, waits for it, and writes the result to
+ * *out (host memory).  Errors: DD_EINVAL, DD_ENONFINITE, DD_ECUDA, DD_EBUSY. */
+DD_API dd_status_t dd_find_discord(dd_plan_t plan, const float* T_dev, dd_result_t* out, void* stream);
+
+/* Same work, enqueued only: returns once everything is on `stream`, with no
+ * host synchronisation.  out_dev: a dd_result_t in device memory or in
+ * pinned (page-locked, mapped) host memory; it is written by the last kernel
+ * of the call.  A non-finite series is reported in out_dev->status.
+ * Returns DD_EINVAL / DD_EBUSY / DD_ECUDA for launch-time errors only. */
+DD_API dd_status_t dd_find_discord_async(dd_plan_t plan, const float* T_dev, dd_result_t* out_dev, void* stream);
+
+/* End-to-end form: T_host is m float32 values in host memory (pinned or
+ * pageable).  Copies it to the plan's device buffer, searches, copies the
+ * result back, waits.  Errors as dd_find_discord. */
+DD_API dd_status_t dd_find_discord_host(dd_plan_t plan, const float* T_host, dd_result_t* out, void* stream);
+
+/* Independent searches over `count` series of possibly different lengths
+ * and subsequence lengths (T_dev[k]: m[k] float32 values on the device,
+ * n[k]); one options struct for all (NULL = defaults).  Results go to
+ * out[k] (host memory); out[k].status reports each series' own error.
+ * Returns the first error met, DD_OK if every search succeeded. */
+DD_API dd_status_t dd_find_discord_batched(int32_t count, const float* const* T_dev, const int64_t* m, const int32_t* n,
+                                    const dd_options_t* opt, dd_result_t* out, void* stream);
+
+/* Exhaustive nearest-neighbour profile (no abandon): nn2_dev[i] = squared
+ * distance from subsequence i to its nearest non-self match, i in [0, N),
+ * computed with the plan's precision (tensor-core forms: the FP32 Gram value,
+ * within the per-row bound, not rescored).  nn2_dev: N floats on the device.
+ * Enqueued on `stream`, not waited for.  Errors: DD_EINVAL, DD_ECUDA. */
+DD_API dd_status_t dd_nn_profile(dd_plan_t plan, const float* T_dev, float* nn2_dev, void* stream);
+
+/* Exhaustive nearest-neighbour distances of selected rows: rows_dev[k]
+ * (device int32, 0 <= row < N, k < count) -> nn2_dev[k] (device float).
+ * Enqueued on `stream`.  Errors: DD_EINVAL, DD_ECUDA. */
+DD_API dd_status_t dd_nn_rows(dd_plan_t plan, const float* T_dev, const int32_t* rows_dev, int32_t count, float* nn2_dev,
+                       void* stream);
+
+/* Runs only the preparation stage of Algorithm 2 (Eq. 2 normalisation,
+ * prefix sums, window statistics, PAA/SAX words, Freq, Cand, Index_Word) on
+ * `stream` and waits.  Errors: DD_EINVAL, DD_ENONFINITE, DD_ECUDA. */
+DD_API dd_status_t dd_prep(dd_plan_t plan, const float* T_dev, void* stream);
+
+/* Device views of the preparation arrays of the last call on the plan. */
+DD_API dd_status_t dd_plan_view(dd_plan_t plan, dd_view_t* view);
+
+/* Number of this library's kernels launched by the plan's last call. */
+DD_API int64_t dd_plan_last_launches(dd_plan_t plan);
+
+/* Static text for a status code. */
+DD_API const char* dd_status_string(dd_status_t status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DD_H_ */

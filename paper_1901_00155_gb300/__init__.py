@@ -1,0 +1,240 @@
+"""GB300-native time-series discord discovery (PhiDD / HOTSAX, arXiv:1901.00155).
+
+Python binding of the C ABI in include/dd.h.  PyTorch supplies device memory
+and streams; every step of the search runs in the library's sm_103a kernels.
+
+    import torch, paper_1901_00155_gb300 as dd
+    plan = dd.Plan(m=1 << 20, n=256)                 # FP32 form
+    res = plan.find_discord(T_cuda)                  # -> DiscordResult(index, nn_distance, ...)
+
+The package never falls back to the CPU: if libdd.so or a CUDA device is
+missing, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+
+from . import _lib
+
+__all__ = ["Plan", "DiscordResult", "DDError", "find_discord", "find_discord_batched", "PRECISIONS"]
+
+PRECISIONS = {"fp32": _lib.DD_FP32, "tc_fp16": _lib.DD_TC_FP16, "tc_bf16": _lib.DD_TC_BF16}
+
+
+class DDError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        lib = _lib.load()
+        msg = lib.dd_status_string(int(status)).decode()
+        super().__init__(f"{what}: {msg} (status {status})" if what else f"{msg} (status {status})")
+        self.status = int(status)
+
+
+@dataclass
+class DiscordResult:
+    index: int
+    nn_distance: float
+    exact: bool
+    computed_pairs: int
+    candidates: int
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_ptr(stream=None):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _check(st: int, what: str):
+    if st != _lib.DD_OK:
+        raise DDError(st, what)
+
+
+def _options(precision="fp32", paa_w=4, alphabet=4, early_abandon=True, paa_mode=0, phase1_max=4096,
+             refine_k=512) -> _lib.Options:
+    o = _lib.Options()
+    _lib.load().dd_options_default(ctypes.byref(o))
+    o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    o.paa_w = paa_w
+    o.alphabet = alphabet
+    o.early_abandon = 1 if early_abandon else 0
+    o.paa_mode = paa_mode
+    o.phase1_max = phase1_max
+    o.refine_k = refine_k
+    return o
+
+
+def _as_result(r: _lib.Result) -> DiscordResult:
+    return DiscordResult(int(r.index), float(r.nn_distance), bool(r.exact), int(r.computed_pairs), int(r.candidates))
+
+
+def _check_series(T, m):
+    torch = _torch()
+    if not isinstance(T, torch.Tensor) or not T.is_cuda or T.dtype != torch.float32 or not T.is_contiguous():
+        raise TypeError("T must be a contiguous float32 CUDA tensor")
+    if T.numel() != m:
+        raise ValueError(f"series has {T.numel()} points, plan expects {m}")
+
+
+class _DevArray:
+    """Exposes a device pointer through __cuda_array_interface__ (zero copy)."""
+
+    def __init__(self, ptr, shape, typestr):
+        self.__cuda_array_interface__ = {"data": (int(ptr), False), "shape": tuple(shape), "typestr": typestr,
+                                         "version": 3, "strides": None, "stream": None}
+
+
+class Plan:
+    """A device plan for series of length ``m`` and subsequence length ``n``."""
+
+    def __init__(self, m: int, n: int, precision="fp32", workspace=None, **opts):
+        self._lib = _lib.load()
+        self.m, self.n = int(m), int(n)
+        self.N = self.m - self.n + 1
+        self.options = _options(precision, **opts)
+        self._ptr = ctypes.c_void_p()
+        ws_ptr, ws_bytes = None, 0
+        if workspace is not None:
+            ws_ptr, ws_bytes = ctypes.c_void_p(workspace.data_ptr()), workspace.numel() * workspace.element_size()
+            self._ws = workspace
+        _check(self._lib.dd_plan_create(ctypes.byref(self._ptr), self.m, self.n, ctypes.byref(self.options), ws_ptr,
+                                        ws_bytes), "dd_plan_create")
+
+    @staticmethod
+    def footprint(m: int, n: int, precision="fp32", **opts) -> int:
+        o = _options(precision, **opts)
+        return int(_lib.load().dd_plan_footprint(int(m), int(n), ctypes.byref(o)))
+
+    def close(self):
+        if getattr(self, "_ptr", None) and self._ptr.value:
+            self._lib.dd_plan_destroy(self._ptr)
+            self._ptr = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def find_discord(self, T, stream=None) -> DiscordResult:
+        _check_series(T, self.m)
+        r = _lib.Result()
+        _check(self._lib.dd_find_discord(self._ptr, ctypes.c_void_p(T.data_ptr()), ctypes.byref(r),
+                                         _stream_ptr(stream)), "dd_find_discord")
+        return _as_result(r)
+
+    def find_discord_async(self, T, out_dev, stream=None):
+        """Enqueue the search; out_dev: a CUDA uint8 tensor of >= 40 bytes receiving a dd_result_t."""
+        _check_series(T, self.m)
+        _check(self._lib.dd_find_discord_async(self._ptr, ctypes.c_void_p(T.data_ptr()),
+                                               ctypes.c_void_p(out_dev.data_ptr()), _stream_ptr(stream)),
+               "dd_find_discord_async")
+
+    @staticmethod
+    def decode_result(buf) -> DiscordResult:
+        """Decode a dd_result_t from a host uint8 tensor / bytes."""
+        raw = bytes(buf.cpu().numpy().tobytes()) if hasattr(buf, "cpu") else bytes(buf)
+        r = _lib.Result.from_buffer_copy(raw[: ctypes.sizeof(_lib.Result)])
+        if r.status != _lib.DD_OK:
+            raise DDError(r.status, "dd_find_discord_async")
+        return _as_result(r)
+
+    def find_discord_host(self, T_host, stream=None) -> DiscordResult:
+        """End-to-end: T_host is a host float32 array (numpy or CPU tensor, pinned or not)."""
+        import numpy as np
+        if hasattr(T_host, "numpy"):
+            if T_host.is_cuda:
+                raise TypeError("find_discord_host takes host memory")
+            ptr, numel = T_host.data_ptr(), T_host.numel()
+            if T_host.dtype != _torch().float32 or not T_host.is_contiguous():
+                raise TypeError("T_host must be contiguous float32")
+        else:
+            arr = np.ascontiguousarray(T_host, dtype=np.float32)
+            T_host = arr
+            ptr, numel = arr.ctypes.data, arr.size
+        if numel != self.m:
+            raise ValueError(f"series has {numel} points, plan expects {self.m}")
+        r = _lib.Result()
+        _check(self._lib.dd_find_discord_host(self._ptr, ctypes.c_void_p(ptr), ctypes.byref(r), _stream_ptr(stream)),
+               "dd_find_discord_host")
+        return _as_result(r)
+
+    def nn_profile(self, T, out=None, stream=None):
+        """Exhaustive squared nearest-neighbour distances of every row (CUDA float32[N])."""
+        torch = _torch()
+        _check_series(T, self.m)
+        if out is None:
+            out = torch.empty(self.N, dtype=torch.float32, device=T.device)
+        _check(self._lib.dd_nn_profile(self._ptr, ctypes.c_void_p(T.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                       _stream_ptr(stream)), "dd_nn_profile")
+        return out
+
+    def nn_rows(self, T, rows, out=None, stream=None):
+        """Exhaustive squared nearest-neighbour distances of the given rows (int32 CUDA tensor)."""
+        torch = _torch()
+        _check_series(T, self.m)
+        if rows.dtype != torch.int32 or not rows.is_cuda or not rows.is_contiguous():
+            raise TypeError("rows must be a contiguous int32 CUDA tensor")
+        if out is None:
+            out = torch.empty(rows.numel(), dtype=torch.float32, device=T.device)
+        _check(self._lib.dd_nn_rows(self._ptr, ctypes.c_void_p(T.data_ptr()), ctypes.c_void_p(rows.data_ptr()),
+                                    rows.numel(), ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)), "dd_nn_rows")
+        return out
+
+    def prep(self, T, stream=None) -> dict:
+        """Run only the preparation stage; returns zero-copy CUDA views of its arrays."""
+        torch = _torch()
+        _check_series(T, self.m)
+        _check(self._lib.dd_prep(self._ptr, ctypes.c_void_p(T.data_ptr()), _stream_ptr(stream)), "dd_prep")
+        v = _lib.View()
+        _check(self._lib.dd_plan_view(self._ptr, ctypes.byref(v)), "dd_plan_view")
+        m, N, D = int(v.m), int(v.N), int(v.dict_size)
+
+        def t(ptr, shape, typestr):
+            return torch.as_tensor(_DevArray(ptr, shape, typestr), device=T.device)
+
+        return {"stats": t(v.stats, (8,), "<f8"), "P1": t(v.P1, (m + 1,), "<f8"), "P2": t(v.P2, (m + 1,), "<f8"),
+                "mu_w": t(v.mu_w, (N,), "<f8"), "c_w": t(v.c_w, (N,), "<f8"), "code": t(v.code, (N,), "<i4"),
+                "freq_hist": t(v.freq_hist, (D,), "<i4"), "order": t(v.order, (N,), "<i4"),
+                "word_start": t(v.word_start, (D,), "<i4"), "ncand": t(v.ncand, (1,), "<i4"),
+                "t32": t(v.t32, (m,), "<f4")}
+
+    def last_launches(self) -> int:
+        return int(self._lib.dd_plan_last_launches(self._ptr))
+
+
+def find_discord(T, n: int, precision="fp32", stream=None, **opts) -> DiscordResult:
+    """One-shot search (creates and destroys a plan)."""
+    with Plan(T.numel(), n, precision, **opts) as p:
+        return p.find_discord(T, stream)
+
+
+def find_discord_batched(series, ns, precision="fp32", stream=None, **opts):
+    """Independent searches over CUDA float32 tensors of possibly different lengths."""
+    lib = _lib.load()
+    k = len(series)
+    ptrs = (ctypes.c_void_p * k)(*[ctypes.c_void_p(s.data_ptr()) for s in series])
+    ms = (ctypes.c_int64 * k)(*[s.numel() for s in series])
+    nn = (ctypes.c_int32 * k)(*[int(x) for x in ns])
+    out = (_lib.Result * k)()
+    for s in series:
+        _check_series(s, s.numel())
+    o = _options(precision, **opts)
+    st = lib.dd_find_discord_batched(k, ptrs, ms, nn, ctypes.byref(o), out, _stream_ptr(stream))
+    results = []
+    for r in out:
+        results.append(_as_result(r) if r.status == _lib.DD_OK else DDError(r.status, "batched item"))
+    if st != _lib.DD_OK and all(isinstance(r, DDError) for r in results):
+        raise DDError(st, "dd_find_discord_batched")
+    return results

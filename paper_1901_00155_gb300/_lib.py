@@ -1,0 +1,81 @@
+"""ctypes binding of libdd.so (include/dd.h).  Argument marshalling only:
+every step of the search runs in the library's CUDA kernels.  There is no CPU
+fallback -- if the library is missing or cannot be loaded this module raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libdd.so")
+
+DD_OK, DD_EINVAL, DD_ENOMEM, DD_ENONFINITE, DD_ETIMEOUT, DD_ECUDA, DD_EBUSY, DD_ENOTSUP = range(8)
+DD_FP32, DD_TC_FP16, DD_TC_BF16 = 0, 1, 2
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int32), ("paa_w", ctypes.c_int32), ("alphabet", ctypes.c_int32),
+                ("early_abandon", ctypes.c_int32), ("paa_mode", ctypes.c_int32), ("phase1_max", ctypes.c_int32),
+                ("refine_k", ctypes.c_int32), ("reserved", ctypes.c_int32 * 9)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("index", ctypes.c_int64), ("nn_distance", ctypes.c_double), ("status", ctypes.c_int32),
+                ("exact", ctypes.c_int32), ("computed_pairs", ctypes.c_int64), ("candidates", ctypes.c_int64)]
+
+
+class View(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int64), ("N", ctypes.c_int64), ("n", ctypes.c_int32), ("dict_size", ctypes.c_int32),
+                ("stats", ctypes.c_void_p), ("P1", ctypes.c_void_p), ("P2", ctypes.c_void_p),
+                ("mu_w", ctypes.c_void_p), ("c_w", ctypes.c_void_p), ("code", ctypes.c_void_p),
+                ("freq_hist", ctypes.c_void_p), ("order", ctypes.c_void_p), ("word_start", ctypes.c_void_p),
+                ("ncand", ctypes.c_void_p), ("t32", ctypes.c_void_p)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+# exported symbol -> (argtypes, restype); every function include/dd.h declares
+SIGNATURES = {
+    "dd_options_default": ([ctypes.POINTER(Options)], None),
+    "dd_plan_footprint": ([ctypes.c_int64, ctypes.c_int32, ctypes.POINTER(Options)], ctypes.c_size_t),
+    "dd_plan_create": ([ctypes.POINTER(ctypes.c_void_p), ctypes.c_int64, ctypes.c_int32, ctypes.POINTER(Options),
+                        ctypes.c_void_p, ctypes.c_size_t], ctypes.c_int),
+    "dd_plan_destroy": ([ctypes.c_void_p], None),
+    "dd_find_discord": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(Result), ctypes.c_void_p], ctypes.c_int),
+    "dd_find_discord_async": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
+    "dd_find_discord_host": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(Result), ctypes.c_void_p],
+                             ctypes.c_int),
+    "dd_find_discord_batched": ([ctypes.c_int32, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_int64),
+                                 ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(Options), ctypes.POINTER(Result),
+                                 ctypes.c_void_p], ctypes.c_int),
+    "dd_nn_profile": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
+    "dd_nn_rows": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
+                    ctypes.c_void_p], ctypes.c_int),
+    "dd_prep": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
+    "dd_plan_view": ([ctypes.c_void_p, ctypes.POINTER(View)], ctypes.c_int),
+    "dd_plan_last_launches": ([ctypes.c_void_p], ctypes.c_int64),
+    "dd_status_string": ([ctypes.c_int], ctypes.c_char_p),
+}
+
+
+def load(build_if_missing: bool = True):
+    """Load libdd.so (building it first if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if build_if_missing:
+            from . import build as _build
+            _build.build()
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"libdd.so not found at {LIB_PATH}; build it with python -m paper_1901_00155_gb300.build")
+        lib = ctypes.CDLL(LIB_PATH)
+        for name, (args, res) in SIGNATURES.items():
+            f = getattr(lib, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = lib
+        return lib

@@ -1,0 +1,361 @@
+// api.cu -- the C ABI of libdd.so (declared in include/dd.h): plans, their
+// device workspace, and the entry points that enqueue preparation + search.
+#include <cstring>
+#include <new>
+
+#include "dd_internal.cuh"
+
+using dd::Ctrl;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+constexpr int kPad = 64;  // zero elements after the series copies
+
+struct Carver {
+    char* base;
+    size_t off = 0;
+    template <class T>
+    T* take(size_t count) {
+        off = (off + kAlign - 1) / kAlign * kAlign;
+        T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+        off += count * sizeof(T);
+        return p;
+    }
+};
+
+bool valid_options(const dd_options_t& o) {
+    if (o.precision != DD_FP32 && o.precision != DD_TC_FP16 && o.precision != DD_TC_BF16) return false;
+    if (o.paa_w < 1 || o.alphabet < 2 || o.alphabet > dd::kMaxAlphabet) return false;
+    double dict = 1.0;
+    for (int i = 0; i < o.paa_w; i++) dict *= o.alphabet;
+    if (dict > dd::kMaxDict) return false;
+    if (o.early_abandon != 0 && o.early_abandon != 1) return false;
+    if (o.paa_mode != 0 && o.paa_mode != 1) return false;
+    if (o.phase1_max < 0 || o.refine_k < 0) return false;
+    for (int i = 0; i < 9; i++)
+        if (o.reserved[i] != 0) return false;
+    return true;
+}
+
+bool valid_sizes(int64_t m, int32_t n) {
+    if (n < 1 || m < 1 || (int64_t)n > m) return false;
+    const int64_t N = m - n + 1;
+    if (N < 2 * (int64_t)n) return false;
+    if (m > (int64_t)0x7fffffff - 4096) return false;  // int32 row / column indices
+    return true;
+}
+
+// Words never have more PAA segments than a subsequence has points.
+void clamp_word(dd_options_t& o, int32_t n) {
+    if (o.paa_w > n) o.paa_w = n;
+}
+
+int dict_size(const dd_options_t& o) {
+    int d = 1;
+    for (int i = 0; i < o.paa_w; i++) d *= o.alphabet;
+    return d;
+}
+
+// Lays the plan's arrays out in `base` (or only measures when base == null).
+size_t carve(dd_plan_s* p, char* base) {
+    Carver c{base};
+    const int64_t m = p->m, N = p->N;
+    const int D = p->D;
+    const int nscan = (int)((m + dd::kScanElems - 1) / dd::kScanElems);
+    const int nh = (int)((N + dd::kHistRows - 1) / dd::kHistRows);
+    const int nblk = (int)((N + dd::kCompactRows - 1) / dd::kCompactRows);
+    p->ctrl = c.take<Ctrl>(1);
+    p->stats = c.take<double>(8);
+    p->part = c.take<double>(3 * dd::kStatBlocks);
+    p->beta = c.take<double>(dd::kMaxAlphabet);
+    p->Tbuf = c.take<float>(m + kPad);
+    p->t64 = c.take<double>(m + kPad);
+    p->t32 = c.take<float>(m + kPad);
+    p->P1 = c.take<double>(m + 1);
+    p->P2 = c.take<double>(m + 1);
+    p->bsum = c.take<double>(4 * (size_t)nscan);
+    p->mu_w = c.take<double>(N);
+    p->c_w = c.take<double>(N);
+    p->code = c.take<int32_t>(N);
+    p->hist = c.take<int32_t>(D);
+    p->blockcnt = c.take<int32_t>((size_t)nh * D);
+    p->word_start = c.take<int32_t>(D);
+    p->order = c.take<int32_t>(N);
+    p->pos_of = c.take<int32_t>(N);
+    p->rmin = c.take<uint32_t>(N);
+    for (int k = 0; k < 4; k++) p->list[k] = c.take<int32_t>(N);
+    p->flag = c.take<uint8_t>(N);
+    p->blk = c.take<int32_t>(nblk + 1);
+    p->res_dev = c.take<dd_result_t>(1);
+    p->seq_rows = c.take<int32_t>(N);
+    return (c.off + kAlign - 1) / kAlign * kAlign;
+}
+
+__global__ void k_iota(int32_t* a, int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) a[i] = (int32_t)i;
+}
+
+dd_status_t from_cuda(cudaError_t e) {
+    if (e == cudaSuccess) return DD_OK;
+    if (e == cudaErrorMemoryAllocation) return DD_ENOMEM;
+    return DD_ECUDA;
+}
+
+struct BusyGuard {
+    dd_plan_s* p;
+    bool ok;
+    explicit BusyGuard(dd_plan_s* q) : p(q) {
+        int expected = 0;
+        ok = p->busy.compare_exchange_strong(expected, 1);
+    }
+    ~BusyGuard() {
+        if (ok) p->busy.store(0);
+    }
+};
+
+dd_status_t search_sync(dd_plan_s* p, const float* T_dev, dd_result_t* out, cudaStream_t s) {
+    cudaError_t e = dd::launch_search(p, T_dev, p->res_dev, s);
+    if (e != cudaSuccess) return from_cuda(e);
+    e = cudaMemcpyAsync(p->res_host, p->res_dev, sizeof(dd_result_t), cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return from_cuda(e);
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return from_cuda(e);
+    *out = *p->res_host;
+    return (dd_status_t)out->status;
+}
+
+}  // namespace
+
+extern "C" {
+
+void dd_options_default(dd_options_t* opt) {
+    if (!opt) return;
+    std::memset(opt, 0, sizeof(*opt));
+    opt->precision = DD_FP32;
+    opt->paa_w = 4;
+    opt->alphabet = 4;
+    opt->early_abandon = 1;
+    opt->paa_mode = 0;
+    opt->phase1_max = 4096;
+    opt->refine_k = 512;
+}
+
+size_t dd_plan_footprint(int64_t m, int32_t n, const dd_options_t* opt) {
+    dd_options_t o;
+    if (opt)
+        o = *opt;
+    else
+        dd_options_default(&o);
+    if (!valid_options(o) || !valid_sizes(m, n)) return 0;
+    clamp_word(o, n);
+    dd_plan_s tmp;
+    tmp.m = m;
+    tmp.n = n;
+    tmp.N = m - n + 1;
+    tmp.opt = o;
+    tmp.D = dict_size(o);
+    return carve(&tmp, nullptr);
+}
+
+dd_status_t dd_plan_create(dd_plan_t* plan, int64_t m, int32_t n, const dd_options_t* opt, void* workspace,
+                           size_t workspace_bytes) {
+    if (!plan) return DD_EINVAL;
+    *plan = nullptr;
+    dd_options_t o;
+    if (opt)
+        o = *opt;
+    else
+        dd_options_default(&o);
+    if (!valid_options(o) || !valid_sizes(m, n)) return DD_EINVAL;
+    clamp_word(o, n);
+    if (o.precision != DD_FP32) return DD_ENOTSUP;
+    if (workspace && (reinterpret_cast<uintptr_t>(workspace) % kAlign) != 0) return DD_EINVAL;
+    dd_plan_s* p = new (std::nothrow) dd_plan_s();
+    if (!p) return DD_ENOMEM;
+    p->m = m;
+    p->n = n;
+    p->N = m - n + 1;
+    p->opt = o;
+    p->D = dict_size(o);
+    cudaError_t e = cudaGetDevice(&p->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&p->sm_count, cudaDevAttrMultiProcessorCount, p->device);
+    if (e != cudaSuccess) {
+        delete p;
+        return from_cuda(e);
+    }
+    const size_t need = carve(p, nullptr);
+    p->ws_bytes = need;
+    if (workspace) {
+        if (workspace_bytes < need) {
+            delete p;
+            return DD_ENOMEM;
+        }
+        p->ws = workspace;
+        p->own_ws = false;
+    } else {
+        e = cudaMalloc(&p->ws, need);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            delete p;
+            return DD_ENOMEM;
+        }
+        p->own_ws = true;
+    }
+    carve(p, static_cast<char*>(p->ws));
+    e = cudaMallocHost(reinterpret_cast<void**>(&p->res_host), sizeof(dd_result_t));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        if (p->own_ws) cudaFree(p->ws);
+        delete p;
+        return DD_ENOMEM;
+    }
+    dd::host_breakpoints(o.alphabet, p->beta_host);
+    e = cudaMemcpy(p->beta, p->beta_host, sizeof(double) * (o.alphabet - 1), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(p->t64 + p->m, 0, sizeof(double) * kPad);
+    if (e == cudaSuccess) e = cudaMemset(p->t32 + p->m, 0, sizeof(float) * kPad);
+    if (e == cudaSuccess) {
+        k_iota<<<(unsigned)((p->N + 255) / 256), 256>>>(p->seq_rows, p->N);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        cudaFreeHost(p->res_host);
+        if (p->own_ws) cudaFree(p->ws);
+        delete p;
+        return from_cuda(e);
+    }
+    *plan = p;
+    return DD_OK;
+}
+
+void dd_plan_destroy(dd_plan_t p) {
+    if (!p) return;
+    cudaDeviceSynchronize();
+    if (p->res_host) cudaFreeHost(p->res_host);
+    if (p->own_ws && p->ws) cudaFree(p->ws);
+    delete p;
+}
+
+dd_status_t dd_find_discord(dd_plan_t p, const float* T_dev, dd_result_t* out, void* stream) {
+    if (!p || !T_dev || !out) return DD_EINVAL;
+    BusyGuard g(p);
+    if (!g.ok) return DD_EBUSY;
+    return search_sync(p, T_dev, out, static_cast<cudaStream_t>(stream));
+}
+
+dd_status_t dd_find_discord_async(dd_plan_t p, const float* T_dev, dd_result_t* out_dev, void* stream) {
+    if (!p || !T_dev || !out_dev) return DD_EINVAL;
+    BusyGuard g(p);
+    if (!g.ok) return DD_EBUSY;
+    return from_cuda(dd::launch_search(p, T_dev, out_dev, static_cast<cudaStream_t>(stream)));
+}
+
+dd_status_t dd_find_discord_host(dd_plan_t p, const float* T_host, dd_result_t* out, void* stream) {
+    if (!p || !T_host || !out) return DD_EINVAL;
+    BusyGuard g(p);
+    if (!g.ok) return DD_EBUSY;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemcpyAsync(p->Tbuf, T_host, sizeof(float) * p->m, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return from_cuda(e);
+    return search_sync(p, p->Tbuf, out, s);
+}
+
+dd_status_t dd_find_discord_batched(int32_t count, const float* const* T_dev, const int64_t* m, const int32_t* n,
+                                    const dd_options_t* opt, dd_result_t* out, void* stream) {
+    if (count < 0 || (count > 0 && (!T_dev || !m || !n || !out))) return DD_EINVAL;
+    dd_status_t first = DD_OK;
+    dd_plan_t plan = nullptr;
+    int64_t pm = -1;
+    int32_t pn = -1;
+    for (int32_t k = 0; k < count; k++) {
+        dd_status_t st = DD_OK;
+        if (!plan || pm != m[k] || pn != n[k]) {
+            dd_plan_destroy(plan);
+            plan = nullptr;
+            st = dd_plan_create(&plan, m[k], n[k], opt, nullptr, 0);
+            pm = m[k];
+            pn = n[k];
+        }
+        if (st == DD_OK) st = dd_find_discord(plan, T_dev[k], &out[k], stream);
+        if (st != DD_OK) {
+            std::memset(&out[k], 0, sizeof(dd_result_t));
+            out[k].index = -1;
+            out[k].status = st;
+            if (first == DD_OK) first = st;
+        }
+    }
+    dd_plan_destroy(plan);
+    return first;
+}
+
+dd_status_t dd_nn_profile(dd_plan_t p, const float* T_dev, float* nn2_dev, void* stream) {
+    if (!p || !T_dev || !nn2_dev) return DD_EINVAL;
+    BusyGuard g(p);
+    if (!g.ok) return DD_EBUSY;
+    return from_cuda(dd::launch_profile(p, T_dev, nullptr, 0, nn2_dev, static_cast<cudaStream_t>(stream)));
+}
+
+dd_status_t dd_nn_rows(dd_plan_t p, const float* T_dev, const int32_t* rows_dev, int32_t count, float* nn2_dev,
+                       void* stream) {
+    if (!p || !T_dev || !rows_dev || !nn2_dev || count < 0) return DD_EINVAL;
+    if (count == 0) return DD_OK;
+    BusyGuard g(p);
+    if (!g.ok) return DD_EBUSY;
+    return from_cuda(dd::launch_profile(p, T_dev, rows_dev, count, nn2_dev, static_cast<cudaStream_t>(stream)));
+}
+
+dd_status_t dd_prep(dd_plan_t p, const float* T_dev, void* stream) {
+    if (!p || !T_dev) return DD_EINVAL;
+    BusyGuard g(p);
+    if (!g.ok) return DD_EBUSY;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    p->launches = 0;
+    cudaError_t e = cudaMemsetAsync(p->ctrl, 0, sizeof(Ctrl), s);
+    if (e == cudaSuccess) e = dd::launch_prep(p, T_dev, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return from_cuda(e);
+    int nonfinite = 0;
+    e = cudaMemcpy(&nonfinite, &p->ctrl->nonfinite, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return from_cuda(e);
+    return nonfinite ? DD_ENONFINITE : DD_OK;
+}
+
+dd_status_t dd_plan_view(dd_plan_t p, dd_view_t* v) {
+    if (!p || !v) return DD_EINVAL;
+    v->m = p->m;
+    v->N = p->N;
+    v->n = p->n;
+    v->dict_size = p->D;
+    v->stats = p->stats;
+    v->P1 = p->P1;
+    v->P2 = p->P2;
+    v->mu_w = p->mu_w;
+    v->c_w = p->c_w;
+    v->code = p->code;
+    v->freq_hist = p->hist;
+    v->order = p->order;
+    v->word_start = p->word_start;
+    v->ncand = &p->ctrl->ncand;
+    v->t32 = p->t32;
+    return DD_OK;
+}
+
+int64_t dd_plan_last_launches(dd_plan_t p) { return p ? p->launches : -1; }
+
+const char* dd_status_string(dd_status_t s) {
+    switch (s) {
+        case DD_OK: return "ok";
+        case DD_EINVAL: return "invalid argument";
+        case DD_ENOMEM: return "out of memory";
+        case DD_ENONFINITE: return "series holds NaN or Inf";
+        case DD_ETIMEOUT: return "device-side wait timed out";
+        case DD_ECUDA: return "CUDA error";
+        case DD_EBUSY: return "plan busy";
+        case DD_ENOTSUP: return "not supported";
+    }
+    return "unknown status";
+}
+
+}  // extern "C"

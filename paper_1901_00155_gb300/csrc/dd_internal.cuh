@@ -1,0 +1,171 @@
+// dd_internal.cuh -- plan layout, device control block and kernel entry points
+// shared by the CUDA translation units of libdd.so.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+#include <vector>
+
+#include "../../include/dd.h"
+
+namespace dd {
+
+// ---------------------------------------------------------------- constants
+constexpr int kMaxAlphabet = 64;
+constexpr int kMaxDict = 4096;           // alphabet^paa_w limit (word index fits one smem sort)
+constexpr int kStatBlocks = 1024;        // partial-sum blocks of the Eq. 2 statistics
+constexpr int kScanElems = 4096;         // elements per block of the FP64 prefix scan
+constexpr int kHistRows = 4096;          // rows per block of the word histogram / scatter
+constexpr int kCompactRows = 2048;       // list entries per block of the compaction
+constexpr int kTopkBins = 4096;          // bins of the top-k radix select (float bits >> 19)
+constexpr int kMaxLaunchSlots = 512;     // work counters per search
+constexpr int kMaxListSlots = 256;       // list counts per search
+
+// FP32 direct-difference tile kernel
+constexpr int kF32BM = 128;  // rows per tile
+constexpr int kF32BN = 128;  // columns per tile
+constexpr int kF32BK = 32;   // k-chunk
+constexpr int kF32Threads = 256;
+
+// Device control block: zeroed once at the start of every search (one memset),
+// so every counter below is written by exactly one search.
+struct Ctrl {
+    unsigned long long key;       // argmax key: float bits(nn^2) << 32 | (0xffffffff - i)
+    unsigned long long pairs;     // distance pairs computed
+    unsigned int bsf;             // best-so-far nn^2 (float bits, non-negative floats order as uints)
+    int nonfinite;                // T held NaN/Inf
+    int degenerate;               // sigma == 0
+    int ncand;                    // |Cand|
+    int n1;                       // rows run in phase 1
+    int n2;                       // rows in phase 2 (N - n1)
+    int ncomplete;                // rows that completed a full scan
+    int err;                      // device-side error code (0 = none)
+    unsigned int topk_thr;        // top-k threshold (float bits)
+    int pad_[3];
+    int cnt[kMaxListSlots];       // list counts written by compactions
+    int work[kMaxLaunchSlots];    // dynamic-schedule work counters, one per launch
+    int topk_hist[kTopkBins];     // radix-select histogram
+};
+
+// A list of rows (orig indices).  Row r of the list is base[off + r] with
+// off = *off_dev (or 0) and the count *cnt_dev.
+struct ListRef {
+    const int32_t* base;
+    const int32_t* off_dev;  // may be null
+    const int32_t* cnt_dev;
+};
+
+// Column schedule of one wave.
+struct ColSpec {
+    int mode;        // 0 = global order, 1 = same-word (bucket) neighbourhood
+    int v_lo, v_hi;  // mode 0: virtual columns [v_lo, v_hi); virtual v -> order position N-1-v
+    int local_cols;  // mode 1: columns of the row tile's own word scanned
+};
+
+struct PrepArrays {
+    const float* T;
+    int64_t m, N;
+    int n;
+    int w, A, D, paa_mode;
+    double* stats;      // [8]
+    double* part;       // [2*kStatBlocks]
+    double* t64;        // [m + pad]
+    float* t32;         // [m + pad]
+    double* P1;         // [m+1]
+    double* P2;         // [m+1]
+    double* bsum;       // [4 * nscan]
+    double* mu_w;       // [N]
+    double* c_w;        // [N]
+    const double* beta; // [A-1] breakpoints
+    int32_t* code;      // [N]
+    int32_t* hist;      // [D]
+    int32_t* blockcnt;  // [nhist * D]
+    int32_t* word_start;// [D]
+    int32_t* order;     // [N]
+    int32_t* pos_of;    // [N]
+    int phase1_max;
+    Ctrl* ctrl;
+};
+
+struct ScanArgs {
+    const float* t32;
+    int N, n;
+    ListRef rows;
+    const int32_t* order;
+    const int32_t* pos_of;
+    const int32_t* code;
+    const int32_t* hist;
+    const int32_t* word_start;
+    ColSpec col;
+    uint32_t* rmin;           // per orig row: float bits of the running minimum
+    const Ctrl* ctrl_ro;      // bsf, flags
+    Ctrl* ctrl;
+    int abandon;
+    int work_slot;
+    int min_seg_tiles;
+    int target_items;
+};
+
+}  // namespace dd
+
+// Plan: everything a search needs, carved out of one device workspace.
+struct dd_plan_s {
+    int64_t m = 0, N = 0;
+    int32_t n = 0;
+    dd_options_t opt{};
+    int device = 0;
+    int sm_count = 0;
+    int D = 0;
+    size_t ws_bytes = 0;
+    void* ws = nullptr;
+    bool own_ws = false;
+    std::atomic<int> busy{0};
+    int64_t launches = 0;
+
+    // arrays (device)
+    dd::Ctrl* ctrl = nullptr;
+    double* stats = nullptr;
+    double* part = nullptr;
+    double* beta = nullptr;
+    float* Tbuf = nullptr;
+    double* t64 = nullptr;
+    float* t32 = nullptr;
+    double* P1 = nullptr;
+    double* P2 = nullptr;
+    double* bsum = nullptr;
+    double* mu_w = nullptr;
+    double* c_w = nullptr;
+    int32_t* code = nullptr;
+    int32_t* hist = nullptr;
+    int32_t* blockcnt = nullptr;
+    int32_t* word_start = nullptr;
+    int32_t* order = nullptr;
+    int32_t* pos_of = nullptr;
+    uint32_t* rmin = nullptr;
+    int32_t* list[4] = {nullptr, nullptr, nullptr, nullptr};
+    uint8_t* flag = nullptr;
+    int32_t* blk = nullptr;
+    dd_result_t* res_dev = nullptr;
+    dd_result_t* res_host = nullptr;  // pinned
+    int32_t* seq_rows = nullptr;      // 0..N-1
+
+    double beta_host[dd::kMaxAlphabet];
+};
+
+namespace dd {
+
+// prep.cu
+cudaError_t launch_prep(dd_plan_s* p, const float* T, cudaStream_t s);
+// search.cu
+cudaError_t launch_search(dd_plan_s* p, const float* T, dd_result_t* out_dev, cudaStream_t s);
+cudaError_t launch_profile(dd_plan_s* p, const float* T, const int32_t* rows, int count, float* nn2,
+                           cudaStream_t s);
+// scan_fp32.cu
+cudaError_t launch_scan_fp32(const ScanArgs& a, int grid, cudaStream_t s);
+int scan_fp32_grid(const dd_plan_s* p);
+
+void host_breakpoints(int A, double* beta);
+
+}  // namespace dd

@@ -1,0 +1,500 @@
+// prep.cu -- preparation stage of PhiDD (Algorithm 2, before the search):
+//   Eq. 2   z-normalisation of the whole series (FP64 mean and population sigma)
+//           and the FP32 / FP64 normalised copies,
+//           FP64 exclusive prefix sums P1 = sum t^, P2 = sum t^^2,
+//   Eq. 5   per-row statistics of the subsequence matrix (mean mu_i, centred
+//           sum of squares c_i) from the prefix sums,
+//   Eq. 3/4/9  PAA -> SAX word code per row,
+//   Eq. 8/7/10 word histogram (Freq), candidate set (Cand = rarest words) and
+//           the word index (Index_Word) as one row order: words by ascending
+//           frequency, rows ascending within a word (stable counting sort).
+#include <cmath>
+
+#include "dd_internal.cuh"
+
+namespace dd {
+namespace {
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ double warp_max_d(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Block-wide sum of one double per thread; result valid in thread 0.
+template <int NT>
+__device__ double block_sum_d(double v, double* sh) {
+    v = warp_sum_d(v);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (wid == 0) {
+        r = (lane < NT / 32) ? sh[lane] : 0.0;
+        r = warp_sum_d(r);
+    }
+    __syncthreads();
+    return r;
+}
+
+template <int NT>
+__device__ double block_max_d(double v, double* sh) {
+    v = warp_max_d(v);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (wid == 0) {
+        r = (lane < NT / 32) ? sh[lane] : 0.0;
+        r = warp_max_d(r);
+    }
+    __syncthreads();
+    return r;
+}
+
+// ---- Eq. 2, pass 1: per-block sums of T, min/max, finiteness ----------------
+__global__ void __launch_bounds__(256) k_stats_sum(const float* __restrict__ T, int64_t m, double* part,
+                                                   Ctrl* ctrl) {
+    __shared__ double sh[32];
+    double s = 0.0, mx = -INFINITY, mn = INFINITY;
+    int bad = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+        float v = T[i];
+        if (!isfinite(v)) bad = 1;
+        s += (double)v;
+        mx = fmax(mx, (double)v);
+        mn = fmin(mn, (double)v);
+    }
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicExch(&ctrl->nonfinite, 1);
+    double bs = block_sum_d<256>(s, sh);
+    double bmx = block_max_d<256>(mx, sh);
+    double bmn = -block_max_d<256>(-mn, sh);
+    if (threadIdx.x == 0) {
+        part[blockIdx.x] = bs;
+        part[kStatBlocks + blockIdx.x] = bmx;
+        part[2 * kStatBlocks + blockIdx.x] = bmn;
+    }
+}
+
+// mu = (1/m) sum t ; fixed-order reduction over the block partials.
+__global__ void __launch_bounds__(256) k_stats_mu(const double* part, int nb, int64_t m, double* stats) {
+    __shared__ double sh[32];
+    double s = 0.0, mx = -INFINITY, mn = INFINITY;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+        s += part[b];
+        mx = fmax(mx, part[kStatBlocks + b]);
+        mn = fmin(mn, part[2 * kStatBlocks + b]);
+    }
+    double bs = block_sum_d<256>(s, sh);
+    double bmx = block_max_d<256>(mx, sh);
+    double bmn = -block_max_d<256>(-mn, sh);
+    if (threadIdx.x == 0) {
+        stats[0] = bs / (double)m;
+        stats[4] = bmx;
+        stats[5] = bmn;
+    }
+}
+
+// ---- Eq. 2, pass 2: sum of squared deviations (two-pass variance) ------------
+__global__ void __launch_bounds__(256) k_stats_var(const float* __restrict__ T, int64_t m, const double* stats,
+                                                   double* part) {
+    __shared__ double sh[32];
+    const double mu = stats[0];
+    double s = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+        double d = (double)T[i] - mu;
+        s += d * d;
+    }
+    double bs = block_sum_d<256>(s, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = bs;
+}
+
+__global__ void __launch_bounds__(256) k_stats_sigma(const double* part, int nb, int64_t m, double* stats,
+                                                     Ctrl* ctrl) {
+    __shared__ double sh[32];
+    double s = 0.0;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) s += part[b];
+    double bs = block_sum_d<256>(s, sh);
+    if (threadIdx.x == 0) {
+        double sigma = sqrt(bs / (double)m);
+        stats[1] = sigma;
+        double mu = stats[0];
+        // max |t^| over the series
+        double a = fmax(fabs(stats[4] - mu), fabs(stats[5] - mu));
+        stats[2] = sigma > 0.0 ? a / sigma : 0.0;
+        if (!(sigma > 0.0)) ctrl->degenerate = 1;
+    }
+}
+
+// ---- Eq. 2 normalisation + FP64 prefix scan (3 passes) -----------------------
+// Block b covers elements [b*kScanElems, (b+1)*kScanElems); 1024 threads x 4.
+__global__ void __launch_bounds__(1024) k_norm_blocks(const float* __restrict__ T, int64_t m,
+                                                      const double* stats, double* __restrict__ t64,
+                                                      float* __restrict__ t32, double* bsum, int nscan) {
+    __shared__ double sh[32];
+    const double mu = stats[0], sigma = stats[1];
+    const int64_t base = (int64_t)blockIdx.x * kScanElems + 4 * threadIdx.x;
+    double s1 = 0.0, s2 = 0.0;
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+        int64_t i = base + q;
+        if (i < m) {
+            double v = sigma > 0.0 ? ((double)T[i] - mu) / sigma : 0.0;
+            t64[i] = v;
+            t32[i] = (float)v;
+            s1 += v;
+            s2 += v * v;
+        }
+    }
+    double b1 = block_sum_d<1024>(s1, sh);
+    double b2 = block_sum_d<1024>(s2, sh);
+    if (threadIdx.x == 0) {
+        bsum[blockIdx.x] = b1;
+        bsum[nscan + blockIdx.x] = b2;
+    }
+}
+
+// Exclusive scan of the block totals (one block; sequential runs per thread).
+__global__ void __launch_bounds__(1024) k_norm_scan_totals(double* bsum, int nscan) {
+    __shared__ double r1[1024], r2[1024];
+    const int per = (nscan + 1023) / 1024;
+    const int lo = threadIdx.x * per, hi = min(nscan, lo + per);
+    double a1 = 0.0, a2 = 0.0;
+    for (int b = lo; b < hi; b++) {
+        a1 += bsum[b];
+        a2 += bsum[nscan + b];
+    }
+    r1[threadIdx.x] = a1;
+    r2[threadIdx.x] = a2;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double c1 = 0.0, c2 = 0.0;
+        for (int t = 0; t < 1024; t++) {
+            double x1 = r1[t], x2 = r2[t];
+            r1[t] = c1;
+            r2[t] = c2;
+            c1 += x1;
+            c2 += x2;
+        }
+    }
+    __syncthreads();
+    double c1 = r1[threadIdx.x], c2 = r2[threadIdx.x];
+    for (int b = lo; b < hi; b++) {
+        double x1 = bsum[b], x2 = bsum[nscan + b];
+        bsum[2 * nscan + b] = c1;
+        bsum[3 * nscan + b] = c2;
+        c1 += x1;
+        c2 += x2;
+    }
+}
+
+// Exclusive block scan of two doubles per thread (1024 threads).
+__device__ void block_exscan2(double& a, double& b, double* sh1, double* sh2) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    double ia = a, ib = b;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        double ua = __shfl_up_sync(0xffffffffu, ia, o);
+        double ub = __shfl_up_sync(0xffffffffu, ib, o);
+        if (lane >= o) {
+            ia += ua;
+            ib += ub;
+        }
+    }
+    if (lane == 31) {
+        sh1[wid] = ia;
+        sh2[wid] = ib;
+    }
+    __syncthreads();
+    if (wid == 0) {
+        double wa = sh1[lane], wb = sh2[lane];
+        double sa = wa, sb = wb;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            double ua = __shfl_up_sync(0xffffffffu, sa, o);
+            double ub = __shfl_up_sync(0xffffffffu, sb, o);
+            if (lane >= o) {
+                sa += ua;
+                sb += ub;
+            }
+        }
+        sh1[lane] = sa - wa;
+        sh2[lane] = sb - wb;
+    }
+    __syncthreads();
+    a = sh1[wid] + (ia - a);
+    b = sh2[wid] + (ib - b);
+}
+
+__global__ void __launch_bounds__(1024) k_norm_prefix(const double* __restrict__ t64, int64_t m,
+                                                      const double* bsum, int nscan, double* __restrict__ P1,
+                                                      double* __restrict__ P2) {
+    __shared__ double sh1[32], sh2[32];
+    const int64_t base = (int64_t)blockIdx.x * kScanElems + 4 * threadIdx.x;
+    double v[4];
+    double s1 = 0.0, s2 = 0.0;
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+        int64_t i = base + q;
+        v[q] = (i < m) ? t64[i] : 0.0;
+        s1 += v[q];
+        s2 += v[q] * v[q];
+    }
+    double e1 = s1, e2 = s2;
+    block_exscan2(e1, e2, sh1, sh2);
+    double c1 = bsum[2 * nscan + blockIdx.x] + e1;
+    double c2 = bsum[3 * nscan + blockIdx.x] + e2;
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+        int64_t i = base + q;
+        c1 += v[q];
+        c2 += v[q] * v[q];
+        if (i < m) {
+            P1[i + 1] = c1;
+            P2[i + 1] = c2;
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        P1[0] = 0.0;
+        P2[0] = 0.0;
+    }
+}
+
+// ---- Eq. 5 rows: mean and centred sum of squares from the prefix sums -------
+__global__ void __launch_bounds__(256) k_window_stats(const double* __restrict__ P1, const double* __restrict__ P2,
+                                                      int64_t N, int n, double* __restrict__ mu_w,
+                                                      double* __restrict__ c_w) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const double S1 = P1[i + n] - P1[i];
+    const double S2 = P2[i + n] - P2[i];
+    const double mu = S1 / (double)n;
+    double c = S2 - S1 * mu;
+    // Within the rounding of the prefix sums a constant row has c == 0.
+    const double noise = 64.0 * 1.1102230246251565e-16 * (fabs(P2[i + n]) + fabs(P2[i]));
+    if (c <= noise) c = 0.0;
+    mu_w[i] = mu;
+    c_w[i] = c;
+}
+
+// ---- Eq. 3 (PAA) + Eq. 4 (SAX letters) + Eq. 9 (word code) -----------------
+// Segment s of a row covers [floor(s n / w), floor((s+1) n / w)).
+__global__ void __launch_bounds__(256) k_sax(const double* __restrict__ P1, const double* __restrict__ mu_w,
+                                             const double* __restrict__ c_w, int64_t N, int n, int w, int A,
+                                             int paa_mode, const double* __restrict__ beta,
+                                             int32_t* __restrict__ code) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const double mu = mu_w[i];
+    const double c = c_w[i];
+    const double sd = sqrt(c / (double)n);
+    int32_t h = 0;
+    for (int s = 0; s < w; s++) {
+        const int a = (int)(((int64_t)s * n) / w), b = (int)(((int64_t)(s + 1) * n) / w);
+        const double seg = (P1[i + b] - P1[i + a]) / (double)(b - a);
+        double v;
+        if (paa_mode == 0)
+            v = (c > 0.0) ? (seg - mu) / sd : 0.0;
+        else
+            v = seg;
+        int letter = 0;
+        while (letter < A - 1 && v >= beta[letter]) letter++;
+        h = h * A + letter;
+    }
+    code[i] = h;
+}
+
+// ---- Eq. 8: word histogram, one block-local count per word -----------------
+__global__ void __launch_bounds__(1024) k_word_hist(const int32_t* __restrict__ code, int64_t N, int D,
+                                                    int32_t* __restrict__ hist, int32_t* __restrict__ blockcnt) {
+    extern __shared__ int32_t sh_cnt[];
+    for (int h = threadIdx.x; h < D; h += blockDim.x) sh_cnt[h] = 0;
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * kHistRows;
+    for (int r = threadIdx.x; r < kHistRows; r += blockDim.x) {
+        int64_t i = base + r;
+        if (i < N) atomicAdd(&sh_cnt[code[i]], 1);
+    }
+    __syncthreads();
+    for (int h = threadIdx.x; h < D; h += blockDim.x) {
+        int c = sh_cnt[h];
+        blockcnt[(int64_t)blockIdx.x * D + h] = c;
+        if (c) atomicAdd(&hist[h], c);
+    }
+}
+
+// ---- Eq. 7 / Eq. 10 plan: words ordered by (frequency, word), offsets,
+// |Cand|, and each block's base offset per word (column scan). One block.
+__global__ void __launch_bounds__(1024) k_word_plan(const int32_t* __restrict__ hist, int D, int nblk,
+                                                    int32_t* __restrict__ blockcnt, int32_t* __restrict__ word_start,
+                                                    int phase1_max, int64_t N, Ctrl* ctrl) {
+    __shared__ unsigned long long keys[kMaxDict];
+    __shared__ int sh_min;
+    int P = 1;
+    while (P < D) P <<= 1;
+    if (threadIdx.x == 0) sh_min = 0x7fffffff;
+    __syncthreads();
+    for (int h = threadIdx.x; h < P; h += blockDim.x) {
+        if (h < D) {
+            int c = hist[h];
+            if (c > 0) atomicMin(&sh_min, c);
+            unsigned long long f = c > 0 ? (unsigned long long)c : 0xffffffffull;
+            keys[h] = (f << 32) | (unsigned long long)h;
+        } else {
+            keys[h] = ~0ull;
+        }
+    }
+    __syncthreads();
+    // bitonic sort ascending
+    for (int k = 2; k <= P; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int t = threadIdx.x; t < P; t += blockDim.x) {
+                int ixj = t ^ j;
+                if (ixj > t) {
+                    unsigned long long a = keys[t], b = keys[ixj];
+                    bool up = ((t & k) == 0);
+                    if ((a > b) == up) {
+                        keys[t] = b;
+                        keys[ixj] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    if (threadIdx.x == 0) {
+        int run = 0, ncand = 0;
+        const int fmin = sh_min;
+        for (int r = 0; r < D; r++) {
+            int h = (int)(keys[r] & 0xffffffffull);
+            int c = hist[h];
+            word_start[h] = run;
+            run += c;
+            if (c == fmin) ncand += c;
+        }
+        ctrl->ncand = ncand;
+        int n1 = ncand < phase1_max ? ncand : phase1_max;
+        ctrl->n1 = n1;
+        ctrl->n2 = (int)(N - n1);
+    }
+    __syncthreads();
+    for (int h = threadIdx.x; h < D; h += blockDim.x) {
+        int run = word_start[h];
+        for (int b = 0; b < nblk; b++) {
+            int64_t ix = (int64_t)b * D + h;
+            int c = blockcnt[ix];
+            blockcnt[ix] = run;
+            run += c;
+        }
+    }
+}
+
+// ---- Eq. 10: stable scatter of rows into word order ------------------------
+// Block b handles rows [b*kHistRows, (b+1)*kHistRows); warp w a contiguous
+// slice of it; ranks inside a round of 32 rows come from __match_any_sync.
+__global__ void k_word_scatter(const int32_t* __restrict__ code, int64_t N, int D,
+                               const int32_t* __restrict__ blockbase, int32_t* __restrict__ order,
+                               int32_t* __restrict__ pos_of) {
+    extern __shared__ int32_t sh_wc[];  // [nwarps][D]
+    const int nw = blockDim.x >> 5;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int x = threadIdx.x; x < nw * D; x += blockDim.x) sh_wc[x] = 0;
+    __syncthreads();
+    const int per = kHistRows / nw;
+    const int64_t base = (int64_t)blockIdx.x * kHistRows + (int64_t)wid * per;
+    int32_t* wc = sh_wc + wid * D;
+    for (int r = lane; r < per; r += 32) {
+        int64_t i = base + r;
+        if (i < N) atomicAdd(&wc[code[i]], 1);
+    }
+    __syncthreads();
+    for (int h = threadIdx.x; h < D; h += blockDim.x) {
+        int run = blockbase[(int64_t)blockIdx.x * D + h];
+        for (int q = 0; q < nw; q++) {
+            int c = sh_wc[q * D + h];
+            sh_wc[q * D + h] = run;
+            run += c;
+        }
+    }
+    __syncthreads();
+    const unsigned lt = (1u << lane) - 1u;
+    for (int r0 = 0; r0 < per; r0 += 32) {
+        int64_t i = base + r0 + lane;
+        bool ok = (r0 + lane < per) && (i < N);
+        int h = ok ? code[i] : -1 - lane;  // unique dummy keys for idle lanes
+        unsigned peers = __match_any_sync(0xffffffffu, h);
+        int rank = __popc(peers & lt);
+        int b = ok ? wc[h] : 0;
+        __syncwarp();
+        if (ok) {
+            int pos = b + rank;
+            order[pos] = (int32_t)i;
+            pos_of[i] = pos;
+            if (rank == 0) wc[h] = b + __popc(peers);
+        }
+        __syncwarp();
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_prep(dd_plan_s* p, const float* T, cudaStream_t s) {
+    const int64_t m = p->m, N = p->N;
+    const int n = p->n;
+    const int D = p->D;
+    int nb = (int)((m + 2047) / 2048);
+    if (nb > kStatBlocks) nb = kStatBlocks;
+    if (nb < 1) nb = 1;
+    k_stats_sum<<<nb, 256, 0, s>>>(T, m, p->part, p->ctrl);
+    k_stats_mu<<<1, 256, 0, s>>>(p->part, nb, m, p->stats);
+    k_stats_var<<<nb, 256, 0, s>>>(T, m, p->stats, p->part);
+    k_stats_sigma<<<1, 256, 0, s>>>(p->part, nb, m, p->stats, p->ctrl);
+    const int nscan = (int)((m + kScanElems - 1) / kScanElems);
+    k_norm_blocks<<<nscan, 1024, 0, s>>>(T, m, p->stats, p->t64, p->t32, p->bsum, nscan);
+    k_norm_scan_totals<<<1, 1024, 0, s>>>(p->bsum, nscan);
+    k_norm_prefix<<<nscan, 1024, 0, s>>>(p->t64, m, p->bsum, nscan, p->P1, p->P2);
+    const int gN = (int)((N + 255) / 256);
+    k_window_stats<<<gN, 256, 0, s>>>(p->P1, p->P2, N, n, p->mu_w, p->c_w);
+    k_sax<<<gN, 256, 0, s>>>(p->P1, p->mu_w, p->c_w, N, n, p->opt.paa_w, p->opt.alphabet, p->opt.paa_mode, p->beta,
+                             p->code);
+    const int nh = (int)((N + kHistRows - 1) / kHistRows);
+    cudaMemsetAsync(p->hist, 0, sizeof(int32_t) * D, s);
+    k_word_hist<<<nh, 1024, sizeof(int32_t) * D, s>>>(p->code, N, D, p->hist, p->blockcnt);
+    k_word_plan<<<1, 1024, 0, s>>>(p->hist, D, nh, p->blockcnt, p->word_start, p->opt.phase1_max, N, p->ctrl);
+    int nw = (48 * 1024 / 4) / D;
+    if (nw > 32) nw = 32;
+    if (nw < 1) nw = 1;
+    while (kHistRows % nw) nw--;
+    k_word_scatter<<<nh, nw * 32, sizeof(int32_t) * nw * D, s>>>(p->code, N, D, p->blockcnt, p->order, p->pos_of);
+    p->launches += 12;
+    return cudaGetLastError();
+}
+
+// Breakpoints of the SAX alphabet (text after Eq. 4): Phi(beta_j) = j / A for
+// the standard normal CDF Phi.  Newton iterations on Phi(x) - p from x = 0
+// for the lower half; the upper half by symmetry, the median exactly 0.
+void host_breakpoints(int A, double* beta) {
+    const double inv_sqrt2pi = 0.39894228040143267794;
+    for (int j = 1; 2 * j < A; j++) {
+        const double p = (double)j / (double)A;
+        double x = 0.0;
+        for (int it = 0; it < 100; it++) {
+            const double cdf = 0.5 * std::erfc(-x * 0.70710678118654752440);
+            const double pdf = inv_sqrt2pi * std::exp(-0.5 * x * x);
+            const double step = (cdf - p) / pdf;
+            x -= step;
+            if (std::fabs(step) < 1e-17) break;
+        }
+        beta[j - 1] = x;
+        beta[A - j - 1] = -x;
+    }
+    if (A % 2 == 0) beta[A / 2 - 1] = 0.0;
+}
+
+}  // namespace dd

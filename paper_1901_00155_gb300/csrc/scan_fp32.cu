@@ -1,0 +1,259 @@
+// scan_fp32.cu -- distance tiles in the plain FP32 form (Eq. 1 squared,
+// direct differences sum_k (x_k - y_k)^2 on the CUDA cores), the inner loops
+// of Algorithms 3 and 4 with early abandon against the best-so-far.
+//
+// One work item = a tile of 128 rows of a row list x a segment of a wave's
+// columns.  The CTA walks the segment's 128-column tiles in order; after each
+// tile it publishes the rows' running minima (atomicMin on float bits) and,
+// when abandoning, stops as soon as every row of the tile has a distance
+// strictly below the best-so-far (such a row cannot be the discord).
+// Work items are handed out dynamically through an atomic counter (the
+// GPU counterpart of the paper's dynamic OpenMP schedule).
+//
+// Tile arithmetic: 256 threads, each an 8x8 register micro-tile of
+// (row, column) pairs; k is staged through shared memory in chunks of 32 with
+// cp.async double buffering; rows and columns are gathered by index, each
+// being n consecutive values of the normalised series t^ (FP32).
+#include "dd_internal.cuh"
+
+namespace dd {
+namespace {
+
+constexpr int BM = kF32BM, BN = kF32BN, BK = kF32BK, NT = kF32Threads;
+constexpr int SROW = BM + 4;  // floats per k-row of a transposed tile (keeps 16-B alignment)
+
+struct __align__(16) F32Smem {
+    float a[2][BK][SROW];
+    float b[2][BK][SROW];
+    int row[BM];
+    int col[BN];
+    float rmin[BM];
+    float last[BM];
+    int item;
+    unsigned bsf;
+    int nvalid_rows;
+    int pad;
+};
+
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem, bool pred) {
+    unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    int sz = pred ? 4 : 0;
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(sa), "l"(gmem), "r"(sz) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// Stage k-chunk [k0, k0+BK) of the tile's rows and columns (transposed).
+__device__ __forceinline__ void stage_chunk(F32Smem& sm, int buf, const float* __restrict__ t32, int k0, int n) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int k = k0 + lane;
+    const bool kin = k < n;
+#pragma unroll 4
+    for (int q = 0; q < BM / 8; q++) {
+        const int r = warp + 8 * q;
+        const int ri = sm.row[r];
+        const bool ok = kin && ri >= 0;
+        cp_async4(&sm.a[buf][lane][r], ok ? (const void*)(t32 + ri + k) : (const void*)t32, ok);
+    }
+#pragma unroll 4
+    for (int q = 0; q < BN / 8; q++) {
+        const int c = warp + 8 * q;
+        const int cj = sm.col[c];
+        const bool ok = kin && cj >= 0;
+        cp_async4(&sm.b[buf][lane][c], ok ? (const void*)(t32 + cj + k) : (const void*)t32, ok);
+    }
+}
+
+__global__ void __launch_bounds__(NT, 2) k_scan_fp32(ScanArgs a) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    F32Smem& sm = *reinterpret_cast<F32Smem*>(smraw);
+    const Ctrl* ctrl = a.ctrl_ro;
+    if (ctrl->nonfinite || ctrl->degenerate) return;
+    const int cnt = *a.rows.cnt_dev;
+    const int off = a.rows.off_dev ? *a.rows.off_dev : 0;
+    const int RT = (cnt + BM - 1) / BM;
+    if (RT <= 0) return;
+    int V;
+    if (a.col.mode == 0) {
+        const int hi = a.col.v_hi < a.N ? a.col.v_hi : a.N;
+        V = hi - a.col.v_lo;
+    } else {
+        V = a.col.local_cols;
+    }
+    if (V <= 0) return;
+    const int CT = (V + BN - 1) / BN;
+    int nseg = (a.target_items + RT - 1) / RT;
+    int maxseg = CT / (a.min_seg_tiles > 0 ? a.min_seg_tiles : 1);
+    if (maxseg < 1) maxseg = 1;
+    if (nseg > maxseg) nseg = maxseg;
+    if (nseg < 1) nseg = 1;
+    const long long items = (long long)RT * nseg;
+
+    const int tid = threadIdx.x;
+    const int tx = tid & 15, ty = tid >> 4;
+    const int n = a.n;
+    const int nk = (n + BK - 1) / BK;
+    unsigned long long pairs = 0;
+
+    for (;;) {
+        if (tid == 0) sm.item = atomicAdd(&a.ctrl->work[a.work_slot], 1);
+        __syncthreads();
+        const int item = sm.item;
+        if (item >= items) break;
+        const int rt = item / nseg, sg = item % nseg;
+        const int ct0 = (int)(((long long)sg * CT) / nseg), ct1 = (int)(((long long)(sg + 1) * CT) / nseg);
+
+        if (tid < BM) {
+            const int r = rt * BM + tid;
+            const int ri = r < cnt ? a.rows.base[off + r] : -1;
+            sm.row[tid] = ri;
+            const float v = ri >= 0 ? __uint_as_float(a.rmin[ri]) : INFINITY;
+            sm.rmin[tid] = v;
+            sm.last[tid] = v;
+        }
+        __syncthreads();
+        // same-word neighbourhood of the tile's first row (mode 1)
+        int bs = 0, bsz = 1, startoff = 0, L = V;
+        if (a.col.mode == 1) {
+            const int r0 = sm.row[0];
+            const int h = a.code[r0];
+            bs = a.word_start[h];
+            bsz = a.hist[h];
+            const int p0 = a.pos_of[r0];
+            startoff = (p0 - bs + bsz / 2) % bsz;
+            L = a.col.local_cols < bsz ? a.col.local_cols : bsz;
+        }
+        const int nvr = __syncthreads_count(tid < BM && sm.row[tid] >= 0);
+
+        for (int ct = ct0; ct < ct1; ct++) {
+            if (a.abandon) {
+                bool alive = false;
+                if (tid < BM) {
+                    const int ri = sm.row[tid];
+                    if (ri >= 0) {
+                        const float g = __uint_as_float(*((volatile const unsigned*)(a.rmin + ri)));
+                        const float bsf = __uint_as_float(*((volatile const unsigned*)&ctrl->bsf));
+                        const float mn = fminf(sm.rmin[tid], g);
+                        alive = !(mn < bsf);
+                    }
+                }
+                if (!__syncthreads_or(alive)) break;
+            }
+            int valid_col = 0;
+            if (tid < BN) {
+                int cj = -1;
+                if (a.col.mode == 0) {
+                    const int v = a.col.v_lo + ct * BN + tid;
+                    if (v < a.col.v_lo + V) cj = a.order[a.N - 1 - v];
+                } else {
+                    const int v = ct * BN + tid;
+                    if (v < L) {
+                        int p = startoff + v;
+                        p = p % bsz;
+                        cj = a.order[bs + p];
+                    }
+                }
+                sm.col[tid] = cj;
+                valid_col = cj >= 0;
+            }
+            const int nvc = __syncthreads_count(valid_col);
+            if (nvc == 0) continue;
+            pairs += (unsigned long long)nvr * (unsigned long long)nvc;
+
+            float acc[8][8];
+#pragma unroll
+            for (int i = 0; i < 8; i++)
+#pragma unroll
+                for (int j = 0; j < 8; j++) acc[i][j] = 0.f;
+
+            stage_chunk(sm, 0, a.t32, 0, n);
+            cp_async_commit();
+            for (int kc = 0; kc < nk; kc++) {
+                const int buf = kc & 1;
+                if (kc + 1 < nk) {
+                    stage_chunk(sm, buf ^ 1, a.t32, (kc + 1) * BK, n);
+                    cp_async_commit();
+                    cp_async_wait<1>();
+                } else {
+                    cp_async_wait<0>();
+                }
+                __syncthreads();
+#pragma unroll 8
+                for (int kk = 0; kk < BK; kk++) {
+                    const float4 a0 = *reinterpret_cast<const float4*>(&sm.a[buf][kk][ty * 4]);
+                    const float4 a1 = *reinterpret_cast<const float4*>(&sm.a[buf][kk][64 + ty * 4]);
+                    const float4 b0 = *reinterpret_cast<const float4*>(&sm.b[buf][kk][tx * 4]);
+                    const float4 b1 = *reinterpret_cast<const float4*>(&sm.b[buf][kk][64 + tx * 4]);
+                    const float x[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+                    const float y[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+                    for (int i = 0; i < 8; i++)
+#pragma unroll
+                        for (int j = 0; j < 8; j++) {
+                            const float d = x[i] - y[j];
+                            acc[i][j] = fmaf(d, d, acc[i][j]);
+                        }
+                }
+                __syncthreads();
+            }
+            // exclusion zone |i - j| < n, row minima over the 128 columns
+            int cjr[8];
+#pragma unroll
+            for (int j = 0; j < 8; j++) cjr[j] = sm.col[j < 4 ? tx * 4 + j : 64 + tx * 4 + (j - 4)];
+#pragma unroll
+            for (int i = 0; i < 8; i++) {
+                const int r = i < 4 ? ty * 4 + i : 64 + ty * 4 + (i - 4);
+                const int ri = sm.row[r];
+                float mn = INFINITY;
+#pragma unroll
+                for (int j = 0; j < 8; j++) {
+                    const int d = ri - cjr[j];
+                    const bool ok = cjr[j] >= 0 && (d >= n || d <= -n);
+                    mn = ok ? fminf(mn, acc[i][j]) : mn;
+                }
+                mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, 1));
+                mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, 2));
+                mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, 4));
+                mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, 8));
+                if (tx == 0 && mn < sm.rmin[r]) sm.rmin[r] = mn;
+            }
+            __syncthreads();
+            if (a.abandon && tid < BM) {
+                const int ri = sm.row[tid];
+                const float v = sm.rmin[tid];
+                if (ri >= 0 && v < sm.last[tid]) {
+                    atomicMin(a.rmin + ri, __float_as_uint(v));
+                    sm.last[tid] = v;
+                }
+            }
+        }
+        if (tid < BM) {
+            const int ri = sm.row[tid];
+            const float v = sm.rmin[tid];
+            if (ri >= 0 && v < sm.last[tid]) atomicMin(a.rmin + ri, __float_as_uint(v));
+        }
+        __syncthreads();
+    }
+    if (tid == 0 && pairs) atomicAdd(&a.ctrl->pairs, pairs);
+}
+
+}  // namespace
+
+int scan_fp32_grid(const dd_plan_s* p) { return p->sm_count * 2; }
+
+cudaError_t launch_scan_fp32(const ScanArgs& a, int grid, cudaStream_t s) {
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(k_scan_fp32, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)sizeof(F32Smem));
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    k_scan_fp32<<<grid, NT, sizeof(F32Smem), s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace dd

@@ -1,0 +1,393 @@
+// search.cu -- the search stage of PhiDD (Algorithm 2) on the device:
+//   PotentialDiscord (Algorithm 3) over the Cand rows, then RefineDiscord
+//   (Algorithm 4) over the other rows, as waves of distance tiles with
+//   stream compaction of the surviving rows between waves, and the final
+//   argmax (Algorithm 1's best-so-far update, ties -> smallest index).
+//
+// Everything is enqueued on one stream with all counts kept on the device,
+// so a search needs no host round trip and can be captured in a CUDA graph.
+#include "dd_internal.cuh"
+
+namespace dd {
+namespace {
+
+__global__ void k_set_int(int* p, int v) { *p = v; }
+
+__device__ __forceinline__ bool is_alive(uint32_t rbits, uint32_t bsf_bits) {
+    // Row is alive unless one of its distances fell strictly below the
+    // best-so-far; non-negative floats order like their bit patterns.
+    return rbits >= bsf_bits;
+}
+
+// Compaction pass 1: predicate per list entry + per-block counts.
+// pred 0: alive against the best-so-far; pred 1: alive and rmin >= top-k threshold.
+__global__ void __launch_bounds__(256) k_compact_flags(ListRef in, const uint32_t* __restrict__ rmin,
+                                                       const Ctrl* ctrl, int pred, uint8_t* __restrict__ flag,
+                                                       int* __restrict__ blk) {
+    __shared__ int sh;
+    if (threadIdx.x == 0) sh = 0;
+    __syncthreads();
+    const int cnt = *in.cnt_dev;
+    const int off = in.off_dev ? *in.off_dev : 0;
+    const uint32_t bsf = ctrl->bsf;
+    const uint32_t thr = pred == 1 ? ctrl->topk_thr : 0u;
+    int local = 0;
+    const int base = blockIdx.x * kCompactRows + threadIdx.x * 8;
+#pragma unroll
+    for (int q = 0; q < 8; q++) {
+        const int r = base + q;
+        if (r < cnt) {
+            const int i = in.base[off + r];
+            const uint32_t b = rmin[i];
+            const bool keep = is_alive(b, bsf) && b >= thr;
+            flag[r] = keep;
+            local += keep;
+        }
+    }
+    if (local) atomicAdd(&sh, local);
+    __syncthreads();
+    if (threadIdx.x == 0) blk[blockIdx.x] = sh;
+}
+
+// Compaction pass 2: exclusive scan of the block counts (one block).
+__global__ void __launch_bounds__(1024) k_compact_scan(int* blk, int nblk, int* cnt_out) {
+    __shared__ int part[1024];
+    const int per = (nblk + 1023) / 1024;
+    const int lo = threadIdx.x * per, hi = min(nblk, lo + per);
+    int s = 0;
+    for (int b = lo; b < hi; b++) s += blk[b];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int run = 0;
+        for (int t = 0; t < 1024; t++) {
+            int x = part[t];
+            part[t] = run;
+            run += x;
+        }
+        *cnt_out = run;
+    }
+    __syncthreads();
+    int run = part[threadIdx.x];
+    for (int b = lo; b < hi; b++) {
+        int x = blk[b];
+        blk[b] = run;
+        run += x;
+    }
+}
+
+// Compaction pass 3: order-preserving scatter of the kept entries.
+__global__ void __launch_bounds__(256) k_compact_scatter(ListRef in, const uint8_t* __restrict__ flag,
+                                                         const int* __restrict__ blk, int32_t* __restrict__ out) {
+    __shared__ int wsum[8];
+    const int cnt = *in.cnt_dev;
+    const int off = in.off_dev ? *in.off_dev : 0;
+    const int base = blockIdx.x * kCompactRows + threadIdx.x * 8;
+    if (blockIdx.x * kCompactRows >= cnt) return;
+    int f[8], local = 0;
+#pragma unroll
+    for (int q = 0; q < 8; q++) {
+        const int r = base + q;
+        f[q] = (r < cnt) ? flag[r] : 0;
+        local += f[q];
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int incl = local;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int u = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += u;
+    }
+    if (lane == 31) wsum[wid] = incl;
+    __syncthreads();
+    int wbase = 0;
+    for (int q = 0; q < wid; q++) wbase += wsum[q];
+    int pos = blk[blockIdx.x] + wbase + incl - local;
+#pragma unroll
+    for (int q = 0; q < 8; q++) {
+        if (f[q]) out[pos++] = in.base[off + base + q];
+    }
+}
+
+// Top-k radix select, pass 1: histogram of (float bits >> 19) of the rows'
+// running minima (alive rows only).
+__global__ void __launch_bounds__(256) k_topk_hist(ListRef in, const uint32_t* __restrict__ rmin, Ctrl* ctrl) {
+    __shared__ int h[kTopkBins];
+    for (int b = threadIdx.x; b < kTopkBins; b += blockDim.x) h[b] = 0;
+    __syncthreads();
+    const int cnt = *in.cnt_dev;
+    const int off = in.off_dev ? *in.off_dev : 0;
+    const uint32_t bsf = ctrl->bsf;
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < cnt; r += gridDim.x * blockDim.x) {
+        const uint32_t b = rmin[in.base[off + r]];
+        if (is_alive(b, bsf)) atomicAdd(&h[b >> 19], 1);
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < kTopkBins; b += blockDim.x)
+        if (h[b]) atomicAdd(&ctrl->topk_hist[b], h[b]);
+}
+
+// Top-k pass 2: the threshold bin (from the top) whose cumulative count reaches k.
+__global__ void k_topk_thr(Ctrl* ctrl, int k) {
+    if (threadIdx.x != 0) return;
+    int run = 0;
+    int b = kTopkBins - 1;
+    for (; b > 0; b--) {
+        run += ctrl->topk_hist[b];
+        if (run >= k) break;
+    }
+    ctrl->topk_thr = (uint32_t)b << 19;
+}
+
+// Rows alive after the last wave have scanned every column: their running
+// minimum is their nearest-neighbour distance.  Best-so-far and argmax key.
+__global__ void __launch_bounds__(256) k_complete(ListRef in, const uint32_t* __restrict__ rmin, Ctrl* ctrl) {
+    const int cnt = *in.cnt_dev;
+    const int off = in.off_dev ? *in.off_dev : 0;
+    const uint32_t bsf = ctrl->bsf;
+    unsigned long long best = 0;
+    uint32_t bmax = 0;
+    int done = 0;
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < cnt; r += gridDim.x * blockDim.x) {
+        const int i = in.base[off + r];
+        const uint32_t b = rmin[i];
+        if (!is_alive(b, bsf)) continue;
+        const unsigned long long key = ((unsigned long long)b << 32) | (unsigned long long)(0xffffffffu - (uint32_t)i);
+        best = key > best ? key : best;
+        bmax = b > bmax ? b : bmax;
+        done++;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        unsigned long long ok = __shfl_xor_sync(0xffffffffu, best, o);
+        best = ok > best ? ok : best;
+        uint32_t ob = __shfl_xor_sync(0xffffffffu, bmax, o);
+        bmax = ob > bmax ? ob : bmax;
+        done += __shfl_xor_sync(0xffffffffu, done, o);
+    }
+    if ((threadIdx.x & 31) == 0 && done) {
+        atomicMax(&ctrl->key, best);
+        atomicMax(&ctrl->bsf, bmax);
+        atomicAdd(&ctrl->ncomplete, done);
+    }
+}
+
+__global__ void k_finalize(const Ctrl* ctrl, dd_result_t* out) {
+    if (threadIdx.x != 0) return;
+    dd_result_t r;
+    r.exact = 0;
+    r.computed_pairs = (int64_t)ctrl->pairs;
+    r.candidates = ctrl->ncomplete;
+    if (ctrl->nonfinite) {
+        r.status = DD_ENONFINITE;
+        r.index = -1;
+        r.nn_distance = 0.0;
+    } else if (ctrl->degenerate) {
+        // sigma == 0: the normalised series is identically zero, every
+        // distance is 0 and the first subsequence wins the tie.
+        r.status = DD_OK;
+        r.index = 0;
+        r.nn_distance = 0.0;
+    } else if (ctrl->key == 0ull) {
+        r.status = DD_ECUDA;
+        r.index = -1;
+        r.nn_distance = 0.0;
+    } else {
+        r.status = DD_OK;
+        r.index = (int64_t)(0xffffffffu - (uint32_t)(ctrl->key & 0xffffffffull));
+        r.nn_distance = sqrt((double)__uint_as_float((uint32_t)(ctrl->key >> 32)));
+    }
+    *out = r;
+}
+
+// nn2[k] = running minimum of rows[k] (exhaustive profile output).
+__global__ void k_gather_min(const int32_t* __restrict__ rows, int count, const uint32_t* __restrict__ rmin,
+                             float* __restrict__ nn2) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < count) nn2[k] = __uint_as_float(rmin[rows[k]]);
+}
+
+__global__ void k_check_rows(const int32_t* __restrict__ rows, int count, int64_t N, Ctrl* ctrl) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < count && (rows[k] < 0 || rows[k] >= N)) atomicExch(&ctrl->err, DD_EINVAL);
+}
+
+// ---------------------------------------------------------------------------
+// Host-side sequencing (no synchronisation; counts stay on the device).
+struct Seq {
+    dd_plan_s* p;
+    cudaStream_t s;
+    int work_slot = 0;
+    int cnt_slot = 0;
+    cudaError_t err = cudaSuccess;
+
+    void check() {
+        if (err == cudaSuccess) err = cudaGetLastError();
+    }
+    int* cnt_ptr(int slot) { return &p->ctrl->cnt[slot]; }
+
+    void scan(ListRef rows, ColSpec col, int abandon) {
+        ScanArgs a{};
+        a.t32 = p->t32;
+        a.N = (int)p->N;
+        a.n = p->n;
+        a.rows = rows;
+        a.order = p->order;
+        a.pos_of = p->pos_of;
+        a.code = p->code;
+        a.hist = p->hist;
+        a.word_start = p->word_start;
+        a.col = col;
+        a.rmin = p->rmin;
+        a.ctrl_ro = p->ctrl;
+        a.ctrl = p->ctrl;
+        a.abandon = abandon;
+        a.work_slot = work_slot++;
+        a.min_seg_tiles = 4;
+        const int grid = scan_fp32_grid(p);
+        a.target_items = grid * 2;
+        if (work_slot > kMaxLaunchSlots) {
+            err = cudaErrorInvalidValue;
+            return;
+        }
+        cudaError_t e = launch_scan_fp32(a, grid, s);
+        if (err == cudaSuccess) err = e;
+        p->launches++;
+    }
+
+    // Order-preserving compaction of `in` into `out`; returns the new list.
+    ListRef compact(ListRef in, int32_t* out, int pred) {
+        const int nblk = (int)((p->N + kCompactRows - 1) / kCompactRows);
+        const int slot = cnt_slot++;
+        if (cnt_slot > kMaxListSlots) {
+            err = cudaErrorInvalidValue;
+            return in;
+        }
+        k_compact_flags<<<nblk, 256, 0, s>>>(in, p->rmin, p->ctrl, pred, p->flag, p->blk);
+        k_compact_scan<<<1, 1024, 0, s>>>(p->blk, nblk, cnt_ptr(slot));
+        k_compact_scatter<<<nblk, 256, 0, s>>>(in, p->flag, p->blk, out);
+        p->launches += 3;
+        check();
+        return ListRef{out, nullptr, cnt_ptr(slot)};
+    }
+
+    void complete(ListRef in) {
+        const int g = (int)((p->N + 1023) / 1024);
+        k_complete<<<g < 1024 ? g : 1024, 256, 0, s>>>(in, p->rmin, p->ctrl);
+        p->launches++;
+        check();
+    }
+
+    // Full scan of every column for the rows of `in`, in waves of geometrically
+    // growing column chunks with compaction in between; survivors complete.
+    void scan_full(ListRef in, int32_t* bufA, int32_t* bufB, int first_tiles, int factor) {
+        const int N = (int)p->N;
+        const int BN = kF32BN;
+        ListRef cur = in;
+        int32_t* bufs[2] = {bufA, bufB};
+        int which = 0;
+        long long lo = 0, chunk = first_tiles;
+        while (lo * BN < N) {
+            long long hi = lo + chunk;
+            ColSpec c{0, (int)(lo * BN), (int)(hi * BN < N ? hi * BN : N), 0};
+            scan(cur, c, 1);
+            lo = hi;
+            chunk *= factor;
+            if (lo * BN < N) {
+                cur = compact(cur, bufs[which], 0);
+                which ^= 1;
+            }
+        }
+        complete(cur);
+    }
+};
+
+}  // namespace
+
+cudaError_t launch_search(dd_plan_s* p, const float* T, dd_result_t* out_dev, cudaStream_t s) {
+    p->launches = 0;
+    cudaError_t e = cudaMemsetAsync(p->ctrl, 0, sizeof(Ctrl), s);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(p->rmin, 0x7f, sizeof(uint32_t) * p->N, s);
+    if (e != cudaSuccess) return e;
+    e = launch_prep(p, T, s);
+    if (e != cudaSuccess) return e;
+
+    Seq q{p, s};
+    const dd_options_t& o = p->opt;
+    const bool abandon = o.early_abandon != 0;
+    if (!abandon) {
+        // every row scans every column; the argmax runs over all rows
+        k_set_int<<<1, 1, 0, s>>>(q.cnt_ptr(q.cnt_slot), (int)p->N);
+        ListRef all{p->seq_rows, nullptr, q.cnt_ptr(q.cnt_slot++)};
+        q.scan(all, ColSpec{0, 0, (int)p->N, 0}, 0);
+        q.complete(all);
+        p->launches++;
+    } else {
+        // Algorithm 3 (PotentialDiscord): the rarest-word rows, full scans.
+        ListRef p1{p->order, nullptr, &p->ctrl->n1};
+        q.scan_full(p1, p->list[0], p->list[1], 64, 4);
+        // Algorithm 4 (RefineDiscord) over the remaining rows.  Wave 0: each
+        // row tile scans the rows that share its SAX word (Index_Word first).
+        ListRef p2{p->order, &p->ctrl->n1, &p->ctrl->n2};
+        q.scan(p2, ColSpec{1, 0, 0, 2048}, 1);
+        ListRef surv = q.compact(p2, p->list[0], 0);
+        // Raise the best-so-far: full scans of the survivors with the largest
+        // running minima (the likeliest discords) first.
+        if (o.refine_k > 0) {
+            k_topk_hist<<<2 * p->sm_count, 256, 0, s>>>(surv, p->rmin, p->ctrl);
+            k_topk_thr<<<1, 32, 0, s>>>(p->ctrl, o.refine_k);
+            p->launches += 2;
+            ListRef top = q.compact(surv, p->list[2], 1);
+            q.scan_full(top, p->list[1], p->list[3], 64, 4);
+        }
+        // every other survivor: global waves, then completion
+        {
+            const int N = (int)p->N;
+            const int BN = kF32BN;
+            ListRef cur = q.compact(surv, p->list[1], 0);
+            int32_t* bufs[2] = {p->list[2], p->list[1]};
+            int which = 0;
+            long long lo = 0, chunk = 8;
+            while (lo * BN < N) {
+                long long hi = lo + chunk;
+                ColSpec c{0, (int)(lo * BN), (int)(hi * BN < N ? hi * BN : N), 0};
+                q.scan(cur, c, 1);
+                lo = hi;
+                chunk *= 4;
+                if (lo * BN < N) {
+                    cur = q.compact(cur, bufs[which], 0);
+                    which ^= 1;
+                }
+            }
+            q.complete(cur);
+        }
+    }
+    k_finalize<<<1, 32, 0, s>>>(p->ctrl, out_dev);
+    p->launches++;
+    q.check();
+    return q.err;
+}
+
+cudaError_t launch_profile(dd_plan_s* p, const float* T, const int32_t* rows, int count, float* nn2,
+                           cudaStream_t s) {
+    p->launches = 0;
+    cudaError_t e = cudaMemsetAsync(p->ctrl, 0, sizeof(Ctrl), s);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(p->rmin, 0x7f, sizeof(uint32_t) * p->N, s);
+    if (e != cudaSuccess) return e;
+    e = launch_prep(p, T, s);
+    if (e != cudaSuccess) return e;
+    Seq q{p, s};
+    const int32_t* r = rows ? rows : p->seq_rows;
+    const int c = rows ? count : (int)p->N;
+    k_set_int<<<1, 1, 0, s>>>(q.cnt_ptr(0), c);
+    q.cnt_slot = 1;
+    q.scan(ListRef{r, nullptr, q.cnt_ptr(0)}, ColSpec{0, 0, (int)p->N, 0}, 0);
+    k_gather_min<<<(c + 255) / 256, 256, 0, s>>>(r, c, p->rmin, nn2);
+    p->launches += 2;
+    q.check();
+    return q.err;
+}
+
+}  // namespace dd

@@ -1,0 +1,78 @@
+"""The C-ABI library builds, loads and exports every symbol include/dd.h
+declares; host-only entry points (no device work) behave as documented."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1901_00155_gb300 import _lib
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "dd.h")).read()
+    return sorted(set(re.findall(r"DD_API\s+[\w\s\*]+?\b(dd_\w+)\s*\(", src)))
+
+
+def test_header_declares_functions():
+    names = _declared()
+    assert "dd_find_discord" in names and "dd_plan_create" in names
+    assert len(names) >= 14
+
+
+def test_library_exports_every_declared_symbol():
+    lib = _lib.load()
+    for name in _declared():
+        assert hasattr(lib, name), name
+        assert name in _lib.SIGNATURES, f"binding lacks {name}"
+    assert set(_lib.SIGNATURES) == set(_declared())
+
+
+def test_struct_layouts():
+    assert ctypes.sizeof(_lib.Options) == 64
+    assert ctypes.sizeof(_lib.Result) == 40
+    assert ctypes.sizeof(_lib.View) == 24 + 11 * 8
+
+
+def test_options_default_and_footprint():
+    lib = _lib.load()
+    o = _lib.Options()
+    lib.dd_options_default(ctypes.byref(o))
+    assert (o.precision, o.paa_w, o.alphabet, o.early_abandon, o.paa_mode) == (0, 4, 4, 1, 0)
+    fp = lib.dd_plan_footprint(1 << 20, 256, ctypes.byref(o))
+    assert 32 << 20 < fp < 1 << 30
+    assert lib.dd_plan_footprint(1000, 400, ctypes.byref(o)) == 0  # N < 2n
+    assert lib.dd_plan_footprint(1000, 0, ctypes.byref(o)) == 0
+    o.alphabet = 1
+    assert lib.dd_plan_footprint(1 << 16, 64, ctypes.byref(o)) == 0
+    lib.dd_options_default(ctypes.byref(o))
+    o.reserved[3] = 1
+    assert lib.dd_plan_footprint(1 << 16, 64, ctypes.byref(o)) == 0
+
+
+def test_status_strings():
+    lib = _lib.load()
+    assert lib.dd_status_string(0) == b"ok"
+    assert b"NaN" in lib.dd_status_string(3)
+    assert lib.dd_status_string(99) == b"unknown status"
+
+
+def test_plan_create_rejects_bad_sizes_without_device_work():
+    lib = _lib.load()
+    p = ctypes.c_void_p()
+    assert lib.dd_plan_create(ctypes.byref(p), 100, 40, None, None, 0) == _lib.DD_EINVAL
+    assert lib.dd_plan_create(None, 100, 4, None, None, 0) == _lib.DD_EINVAL
+    assert p.value is None
+    assert lib.dd_find_discord(None, None, None, None) == _lib.DD_EINVAL
+
+
+def test_product_path_does_not_import_oracle():
+    pkg = os.path.join(ROOT, "paper_1901_00155_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                txt = open(os.path.join(dirpath, f)).read()
+                assert "import oracle" not in txt and "from oracle" not in txt, f
+                assert "dd_oracle" not in txt, f

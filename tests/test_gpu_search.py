@@ -1,0 +1,189 @@
+"""Discord search on the GPU (C ABI) against the FP64 oracle.
+
+FP32 form (tolerance from the required accuracy of the plain FP32 path):
+  * index: identical to the oracle's, or -- where the oracle's distances tie
+    within the tolerance -- a row whose oracle nn distance is within RTOL of
+    the oracle's maximum;
+  * nn_distance within RTOL (relative) of the oracle's.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1901_00155_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+RTOL = 1e-4
+
+
+def _dd():
+    import paper_1901_00155_gb300 as dd
+    return dd
+
+
+def _search(T, n, **opts):
+    dd = _dd()
+    with dd.Plan(T.size, n, **opts) as p:
+        r = p.find_discord(torch.from_numpy(np.ascontiguousarray(T)).cuda())
+    return r
+
+
+def _check_against(T, n, r, i_ref, d2_ref):
+    d_ref = math.sqrt(d2_ref)
+    assert r.nn_distance == pytest.approx(d_ref, rel=RTOL, abs=1e-6), (r, i_ref, d_ref)
+    if r.index != i_ref:
+        nn, _ = oracle.nn_rows(T, n, [r.index])
+        assert math.sqrt(nn[0]) == pytest.approx(d_ref, rel=RTOL, abs=1e-6), (r, i_ref, d_ref)
+
+
+def test_small_random_sweep():
+    rng = np.random.default_rng(77)
+    for trial in range(60):
+        n = int(rng.choice([1, 2, 3, 8, 16, 33, 64, 100]))
+        m = int(rng.integers(3 * n - 1, 3 * n + 700))
+        T = synth.random_small(rng, m)
+        r = _search(T, n)
+        i_ref, d2_ref = oracle.discord_brute(T, n)
+        _check_against(T, n, r, i_ref, d2_ref)
+
+
+def test_small_workload_exact():
+    spec = synth.workload_small()
+    T, _ = synth.make_series(spec)
+    r = _search(T, spec.n)
+    i_ref, d2_ref = oracle.discord_brute(T, spec.n)
+    assert r.index == i_ref
+    assert r.nn_distance == pytest.approx(math.sqrt(d2_ref), rel=RTOL)
+
+
+@pytest.mark.parametrize("spec", synth.workloads_medium(), ids=lambda s: s.name())
+def test_medium_workloads_vs_hotsax(spec):
+    T, _ = synth.make_series(spec)
+    r = _search(T, spec.n)
+    i_ref, d2_ref, _ = oracle.hotsax(T, spec.n)
+    _check_against(T, spec.n, r, i_ref, d2_ref)
+
+
+def test_large_workload_sampled():
+    """m = 2^20, n = 256: the GPU's discord distance equals the oracle's
+    brute-force distance of that row, and no sampled row has a larger one."""
+    spec = synth.workload_large(0)
+    T, _ = synth.make_series(spec)
+    r = _search(T, spec.n)
+    nn, _ = oracle.nn_rows(T, spec.n, [r.index])
+    assert r.nn_distance == pytest.approx(math.sqrt(nn[0]), rel=RTOL)
+    rng = np.random.default_rng(1)
+    rows = rng.integers(0, T.size - spec.n + 1, size=24)
+    nns, _ = oracle.nn_rows(T, spec.n, rows)
+    assert np.all(np.sqrt(nns) <= r.nn_distance * (1 + RTOL))
+
+
+@pytest.mark.parametrize("n,m", [(16, 3000), (64, 64 * 3 - 1), (128, 128 * 3 + 77), (1, 50)])
+def test_profile_matches_oracle(n, m):
+    dd = _dd()
+    rng = np.random.default_rng(n + m)
+    T = np.cumsum(rng.standard_normal(m)).astype(np.float32)
+    with dd.Plan(m, n) as p:
+        prof = p.nn_profile(torch.from_numpy(T).cuda()).cpu().numpy()
+    ref = oracle.nn_profile(T, n)
+    np.testing.assert_allclose(prof, ref, rtol=RTOL, atol=1e-5 * max(1.0, ref.max()))
+
+
+def test_nn_rows_matches_oracle():
+    dd = _dd()
+    rng = np.random.default_rng(5)
+    T = np.cumsum(rng.standard_normal(20000)).astype(np.float32)
+    n = 96
+    rows = np.array([0, 1, 777, 5000, 19904, 12345, 12345], dtype=np.int32)
+    with dd.Plan(T.size, n) as p:
+        got = p.nn_rows(torch.from_numpy(T).cuda(), torch.from_numpy(rows).cuda()).cpu().numpy()
+    ref, _ = oracle.nn_rows(T, n, rows)
+    np.testing.assert_allclose(got, ref, rtol=RTOL, atol=1e-6)
+
+
+def test_exhaustive_equals_abandon():
+    rng = np.random.default_rng(9)
+    for _ in range(4):
+        T = np.cumsum(rng.standard_normal(6000)).astype(np.float32)
+        a = _search(T, 50)
+        b = _search(T, 50, early_abandon=False)
+        assert a.index == b.index
+        assert a.nn_distance == b.nn_distance
+        assert b.computed_pairs > a.computed_pairs
+
+
+def test_ordering_options_do_not_change_result():
+    rng = np.random.default_rng(10)
+    T = np.cumsum(rng.standard_normal(9000)).astype(np.float32)
+    base = _search(T, 64)
+    for opts in [dict(paa_mode=1), dict(alphabet=3, paa_w=5), dict(refine_k=0), dict(phase1_max=0),
+                 dict(phase1_max=1, refine_k=1)]:
+        r = _search(T, 64, **opts)
+        assert (r.index, r.nn_distance) == (base.index, base.nn_distance), opts
+
+
+def test_constant_series():
+    r = _search(np.full(1000, 3.5, np.float32), 10)
+    assert r.index == 0 and r.nn_distance == 0.0
+
+
+def test_periodic_ties_pick_smallest_index():
+    # every window has an exact copy except those holding the spike
+    unit = np.array([0, 3, 1, 4, 1, 5, 9, 2], dtype=np.float32)
+    T = np.tile(unit, 50)
+    T[203] += 1.0
+    n = 6
+    r = _search(T, n)
+    i_ref, d2_ref = oracle.discord_brute(T, n)
+    assert i_ref == 203 - n + 1
+    assert r.index == i_ref
+    assert r.nn_distance == pytest.approx(math.sqrt(d2_ref), rel=RTOL)
+
+
+def test_errors():
+    dd = _dd()
+    with pytest.raises(dd.DDError) as e:
+        dd.Plan(100, 40)
+    assert e.value.status == 1
+    T = np.cumsum(np.random.default_rng(0).standard_normal(500)).astype(np.float32)
+    T[17] = np.nan
+    with dd.Plan(T.size, 8) as p:
+        with pytest.raises(dd.DDError) as e:
+            p.find_discord(torch.from_numpy(T).cuda())
+    assert e.value.status == 3
+
+
+def test_host_entry_point_and_async():
+    dd = _dd()
+    spec = synth.workload_small()
+    T, _ = synth.make_series(spec)
+    with dd.Plan(T.size, spec.n) as p:
+        r1 = p.find_discord(torch.from_numpy(T).cuda())
+        r2 = p.find_discord_host(T)
+        r3 = p.find_discord_host(torch.from_numpy(T).pin_memory())
+        buf = torch.zeros(64, dtype=torch.uint8, device="cuda")
+        p.find_discord_async(torch.from_numpy(T).cuda(), buf)
+        torch.cuda.synchronize()
+        r4 = dd.Plan.decode_result(buf)
+    for r in (r2, r3, r4):
+        assert (r.index, r.nn_distance) == (r1.index, r1.nn_distance)
+
+
+def test_batched_uneven():
+    dd = _dd()
+    rng = np.random.default_rng(21)
+    series, ns, refs = [], [], []
+    for k in range(6):
+        n = int(rng.choice([16, 32, 64]))
+        m = int(rng.integers(3 * n + 10, 4000))
+        T = synth.random_small(rng, m, "rw")
+        series.append(torch.from_numpy(T).cuda())
+        ns.append(n)
+        refs.append((T, n) + oracle.discord_brute(T, n))
+    out = dd.find_discord_batched(series, ns)
+    for r, (T, n, i_ref, d2_ref) in zip(out, refs):
+        _check_against(T, n, r, i_ref, d2_ref)
