@@ -1,0 +1,346 @@
+#!/usr/bin/env python3
+"""Benchmark: time-to-discord and pair-distances/s on one GB300.
+
+Workload: a float32 random walk of m = 2^20 points with five injected
+anomalies (seed 0), subsequence length n = 256 -- the size of the paper's
+SCD-1M experiments (Section 4), synthetic because the SCD series are not
+available.  One step = one full discord search (Algorithm 2: preparation,
+PotentialDiscord, RefineDiscord, argmax) through the C ABI with the series
+resident on the device.
+
+value  = brute-force-equivalent unordered non-self pairs per second,
+         P_u / time-to-discord with P_u = (N-n)(N-n+1)/2;
+e2e    = the same metric through dd_find_discord_host (pinned host series,
+         H2D copy and result D2H inside the timed region);
+roofline = the distance-tile kernel, algorithmic work / its CUDA-event time
+         against the GB300 peak of the pipe that bounds it.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+       [--precision fp32|tc_fp16|tc_bf16|all]
+Under torchrun each rank runs an independent replica (the search does not
+exchange data between GPUs); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "pair-distances/s & time-to-discord (m=2^20,n=256), TC vs FP32; serve p99 ms"
+UNIT = "pair-distances/s"
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}, \
+            "fallback"
+
+
+def _pairs_unordered(N: int, n: int) -> int:
+    k = N - n
+    return k * (k + 1) // 2 if k > 0 else 0
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev_index: int):
+        self.dev = dev_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc is not None:
+            time.sleep(0.2)
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                self.out = ""
+
+    def summary(self, busy_floor_mhz: float = 0.0):
+        rows = []
+        for line in (self.out or "").splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for _, _, fl in rows for k, v in enumerate(fl) if v.lower() == "active"})
+        loaded = [r[0] for r in rows if r[0] >= busy_floor_mhz] or [r[0] for r in rows]
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": max(r[1] for r in rows), "reasons": reasons,
+                "samples": len(rows)}
+
+
+def _kernel_traffic(precision: str):
+    """dram bytes per launch of the distance kernel from the committed ncu
+    summary, or None if the kernel source changed since it was taken."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+    except Exception:
+        return None
+    ent = d.get(precision)
+    if not ent:
+        return None
+    src = os.path.join(ROOT, "paper_1901_00155_gb300", "csrc", ent["source"])
+    try:
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    except Exception:
+        return None
+    return ent["dram_bytes_per_launch"] if h == ent.get("source_sha256_16") else None
+
+
+def _reference_arm(args, rank: int):
+    """The FP64 oracle (CPU HOTSAX, Algorithms 2-4) on the host cores, each step a
+    bounded prefix sample of the benchmark workload."""
+    if rank != 0:
+        return
+    import oracle
+    from paper_1901_00155_gb300 import synth
+    spec = synth.workload_large(0)
+    T, _ = synth.make_series(spec)
+    m_s = 1 << 16
+    Ts = T[:m_s].copy()
+    N_s = m_s - spec.n + 1
+    oracle.build()
+    times = []
+    for k in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        oracle.hotsax(Ts, spec.n)
+        dt = time.perf_counter() - t0
+        if k >= args.warmup:
+            times.append(dt)
+    t = statistics.mean(times)
+    value = _pairs_unordered(N_s, spec.n) / t
+    sample = f"first {m_s} points of the m=2^20 n=256 random walk (CPU HOTSAX, FP64), per step"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"rw m={m_s} n={spec.n} (prefix of the m=2^20 benchmark series)",
+                       "m": m_s, "n": spec.n},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def _cpu_baseline():
+    import oracle
+    from paper_1901_00155_gb300 import synth
+    spec = synth.workload_large(0)
+    T, _ = synth.make_series(spec)
+    m_s = 1 << 17
+    Ts = T[:m_s].copy()
+    oracle.build()
+    t0 = time.perf_counter()
+    oracle.hotsax(Ts, spec.n)
+    dt = time.perf_counter() - t0
+    N_s = m_s - spec.n + 1
+    return {"value": _pairs_unordered(N_s, spec.n) / dt, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+            "sample": f"CPU HOTSAX (FP64 oracle) on the first {m_s} points of the workload series, n={spec.n}: "
+                      f"{dt:.2f} s"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="best", choices=["best", "all", "fp32", "tc_fp16", "tc_bf16"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="large", choices=["large", "medium"],
+                    help="large: m=2^20 n=256 (the benchmark); medium: m=262144 n=256 (profiling captures)")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        _reference_arm(args, rank)
+        return
+
+    import torch
+    import torch.distributed as dist
+
+    import paper_1901_00155_gb300 as dd
+    from paper_1901_00155_gb300 import synth
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def max_over_ranks(x: float) -> float:
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    spec = synth.workload_large(0) if args.workload == "large" else synth.workloads_medium()[2]
+    T, _ = synth.make_series(spec)
+    m, n = spec.m, spec.n
+    N = m - n + 1
+    P_u = _pairs_unordered(N, n)
+    Td = torch.from_numpy(T).to(dev)
+    Th = torch.from_numpy(T).pin_memory()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 126 MB L2
+    peaks, peak_src = _peaks()
+
+    supported = []
+    for prec in ("tc_fp16", "tc_bf16", "fp32"):
+        try:
+            dd.Plan(m, n, prec).close()
+            supported.append(prec)
+        except dd.DDError:
+            pass
+    if args.precision == "best":
+        forms = [supported[0]]
+    elif args.precision == "all":
+        forms = supported
+    else:
+        forms = [args.precision]
+
+    results = {}
+    clocks_all = None
+    for prec in forms:
+        plan = dd.Plan(m, n, prec)
+        plan.set_profiling(True)
+        for _ in range(args.warmup):
+            plan.find_discord(Td)
+        torch.cuda.synchronize()
+        stream = torch.cuda.current_stream()
+        step_ms, dist_ms, pairs, launches, dlaunch = [], 0.0, 0, 0, 0
+        res = None
+        barrier()
+        torch.cuda.synchronize()
+        with ClockSampler(local) as cs:
+            for _ in range(args.steps):
+                flush.fill_(1)  # evict the series and workspace from L2 (not timed)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                res = plan.find_discord(Td)
+                e1.record(stream)
+                e1.synchronize()
+                step_ms.append(e0.elapsed_time(e1))
+                pr = plan.profile()
+                dist_ms += pr["dist_ms"]
+                pairs += pr["computed_pairs"]
+                dlaunch += pr["dist_launches"]
+                launches += plan.last_launches()
+        torch.cuda.synchronize()
+        barrier()
+        clocks = cs.summary(busy_floor_mhz=600.0)
+        if clocks_all is None:
+            clocks_all = clocks
+        ms = max_over_ranks(sum(step_ms) / len(step_ms))
+        # end to end: pinned host series -> H2D -> search -> result D2H (synchronous API)
+        e2e_ms = []
+        for _ in range(max(3, args.steps // 2)):
+            flush.fill_(1)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            plan.find_discord_host(Th)
+            e2e_ms.append((time.perf_counter() - t0) * 1e3)
+        e2e = max_over_ranks(statistics.mean(e2e_ms))
+        # roofline of the distance-tile kernel
+        if prec == "fp32":
+            work = 2.0 * n * pairs  # one FP32 subtract + one FFMA per element of each pair
+            achieved = work / (dist_ms * 1e-3) / 1e12 if dist_ms > 0 else 0.0
+            peak = SM_COUNT * FP32_LANES_PER_SM * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+            roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tinstr/s",
+                    "frac": achieved / peak if peak else None, "traffic": _kernel_traffic(prec),
+                    "kernel": "k_scan_fp32", "peak_source": "derived: 152 SM x 128 FP32 lanes x max SM clock",
+                    "launches_per_step": dlaunch / args.steps}
+        else:
+            work = 2.0 * plan_nkpad(n) * pairs
+            achieved = work / (dist_ms * 1e-3) / 1e12 if dist_ms > 0 else 0.0
+            peak = float(peaks.get("bf16_tflops", 1900.0))
+            roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "frac": achieved / peak if peak else None, "traffic": _kernel_traffic(prec),
+                    "kernel": "k_scan_tc", "peak_source": f"{peak_src} bf16 dense burst (fp16 rate equal)",
+                    "launches_per_step": dlaunch / args.steps}
+        results[prec] = {"time_to_discord_ms": ms, "value": P_u / (ms * 1e-3) * world,
+                         "e2e_ms": e2e, "e2e_value": P_u / (e2e * 1e-3) * world, "index": res.index,
+                         "nn_distance": res.nn_distance, "computed_pairs_per_step": pairs // args.steps,
+                         "kernel_launches_per_step": launches / args.steps, "roofline": roof,
+                         "dist_kernel_ms_per_step": dist_ms / args.steps}
+        plan.close()
+
+    head = results[forms[0]]
+    if rank == 0:
+        cpu = None if args.no_cpu_baseline else _cpu_baseline()
+        line = {"metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": head["time_to_discord_ms"], "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32" if forms[0] == "fp32" else "f16xf16->f32+f64",
+                "data": "synthetic",
+                "config": {"workload": f"{spec.kind} m={m} n={n}, {len(spec.anomalies)} anomalies, seed {spec.seed} "
+                                       f"(synthetic stand-in for SCD-1M)",
+                           "m": m, "n": n, "precision": forms[0], "parallelism": f"replicas x{world}",
+                           "l2": "flushed between steps (256 MiB write)"},
+                "time_to_discord_ms": head["time_to_discord_ms"],
+                "roofline": head["roofline"], "cpu_baseline": cpu,
+                "e2e": {"value": head["e2e_value"], "unit": UNIT, "h2d_bytes_per_step": 4 * m,
+                        "d2h_bytes_per_step": 40, "ms_per_step": head["e2e_ms"]},
+                "clocks": clocks_all, "gpu_launches": int(round(head["kernel_launches_per_step"] * args.steps)),
+                "forms": {k: {kk: vv for kk, vv in v.items() if kk != "roofline"} | {"roofline_frac": v["roofline"]["frac"]}
+                          for k, v in results.items()},
+                "discord": {"index": head["index"], "nn_distance": head["nn_distance"]}}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def plan_nkpad(n: int) -> int:
+    return ((n + 63) // 64) * 64
+
+
+if __name__ == "__main__":
+    main()

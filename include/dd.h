@@ -81,7 +81,11 @@ typedef struct {
     int32_t phase1_max;    /* at most this many Cand rows run in phase 1 (default 4096) */
     int32_t refine_k;      /* rows with the largest first-wave upper bounds that get a full scan
                               before the other survivors, to raise the best-so-far (default 512) */
-    int32_t reserved[9];   /* must be zero */
+    int32_t local_cols;    /* first wave: every row scans the rows of nearest window mean, this many
+                              on each side of its tile (default 128) */
+    int32_t word_cols;     /* same-word wave: survivors scan this many rows sharing their SAX word
+                              (Index_Word, Eq. 10) before their full scans; 0 = skip (default 512) */
+    int32_t reserved[7];   /* must be zero */
 } dd_options_t;
 
 typedef struct {
@@ -185,6 +189,22 @@ DD_API dd_status_t dd_plan_view(dd_plan_t plan, dd_view_t* view);
 
 /* Number of this library's kernels launched by the plan's last call. */
 DD_API int64_t dd_plan_last_launches(dd_plan_t plan);
+
+/* Per-call measurements of the distance kernels (tracing).  When enabled
+ * with dd_plan_set_profiling(plan, 1), the synchronous calls record CUDA
+ * events on their stream around every distance-tile launch and fill this
+ * struct after the call; asynchronous calls leave it untouched. */
+typedef struct {
+    int32_t dist_launches;      /* distance-tile kernel launches in the last call */
+    int32_t precision;          /* dd_precision_t of those launches */
+    double dist_ms;             /* sum of their durations (CUDA events, same stream) */
+    int64_t computed_pairs;     /* (row, column) pairs they evaluated */
+    double call_ms;             /* whole call: first to last kernel (CUDA events) */
+    int64_t reserved[4];
+} dd_profile_t;
+
+DD_API dd_status_t dd_plan_set_profiling(dd_plan_t plan, int32_t enable);
+DD_API dd_status_t dd_plan_get_profile(dd_plan_t plan, dd_profile_t* out);
 
 /* Static text for a status code. */
 DD_API const char* dd_status_string(dd_status_t status);

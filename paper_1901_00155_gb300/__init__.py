@@ -56,7 +56,7 @@ def _check(st: int, what: str):
 
 
 def _options(precision="fp32", paa_w=4, alphabet=4, early_abandon=True, paa_mode=0, phase1_max=4096,
-             refine_k=512) -> _lib.Options:
+             refine_k=512, local_cols=128, word_cols=512) -> _lib.Options:
     o = _lib.Options()
     _lib.load().dd_options_default(ctypes.byref(o))
     o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
@@ -66,6 +66,8 @@ def _options(precision="fp32", paa_w=4, alphabet=4, early_abandon=True, paa_mode
     o.paa_mode = paa_mode
     o.phase1_max = phase1_max
     o.refine_k = refine_k
+    o.local_cols = local_cols
+    o.word_cols = word_cols
     return o
 
 
@@ -212,6 +214,16 @@ class Plan:
 
     def last_launches(self) -> int:
         return int(self._lib.dd_plan_last_launches(self._ptr))
+
+    def set_profiling(self, enable: bool = True):
+        _check(self._lib.dd_plan_set_profiling(self._ptr, 1 if enable else 0), "dd_plan_set_profiling")
+
+    def profile(self) -> dict:
+        """Distance-kernel measurements of the last synchronous call (needs set_profiling)."""
+        pr = _lib.Profile()
+        _check(self._lib.dd_plan_get_profile(self._ptr, ctypes.byref(pr)), "dd_plan_get_profile")
+        return {"dist_launches": int(pr.dist_launches), "precision": int(pr.precision), "dist_ms": float(pr.dist_ms),
+                "computed_pairs": int(pr.computed_pairs), "call_ms": float(pr.call_ms)}
 
 
 def find_discord(T, n: int, precision="fp32", stream=None, **opts) -> DiscordResult:

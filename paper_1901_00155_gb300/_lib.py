@@ -18,7 +18,8 @@ DD_FP32, DD_TC_FP16, DD_TC_BF16 = 0, 1, 2
 class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("paa_w", ctypes.c_int32), ("alphabet", ctypes.c_int32),
                 ("early_abandon", ctypes.c_int32), ("paa_mode", ctypes.c_int32), ("phase1_max", ctypes.c_int32),
-                ("refine_k", ctypes.c_int32), ("reserved", ctypes.c_int32 * 9)]
+                ("refine_k", ctypes.c_int32), ("local_cols", ctypes.c_int32), ("word_cols", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 7)]
 
 
 class Result(ctypes.Structure):
@@ -32,6 +33,11 @@ class View(ctypes.Structure):
                 ("mu_w", ctypes.c_void_p), ("c_w", ctypes.c_void_p), ("code", ctypes.c_void_p),
                 ("freq_hist", ctypes.c_void_p), ("order", ctypes.c_void_p), ("word_start", ctypes.c_void_p),
                 ("ncand", ctypes.c_void_p), ("t32", ctypes.c_void_p)]
+
+
+class Profile(ctypes.Structure):
+    _fields_ = [("dist_launches", ctypes.c_int32), ("precision", ctypes.c_int32), ("dist_ms", ctypes.c_double),
+                ("computed_pairs", ctypes.c_int64), ("call_ms", ctypes.c_double), ("reserved", ctypes.c_int64 * 4)]
 
 
 _lock = threading.Lock()
@@ -58,6 +64,8 @@ SIGNATURES = {
     "dd_plan_view": ([ctypes.c_void_p, ctypes.POINTER(View)], ctypes.c_int),
     "dd_plan_last_launches": ([ctypes.c_void_p], ctypes.c_int64),
     "dd_status_string": ([ctypes.c_int], ctypes.c_char_p),
+    "dd_plan_set_profiling": ([ctypes.c_void_p, ctypes.c_int32], ctypes.c_int),
+    "dd_plan_get_profile": ([ctypes.c_void_p, ctypes.POINTER(Profile)], ctypes.c_int),
 }
 
 

@@ -32,8 +32,8 @@ bool valid_options(const dd_options_t& o) {
     if (dict > dd::kMaxDict) return false;
     if (o.early_abandon != 0 && o.early_abandon != 1) return false;
     if (o.paa_mode != 0 && o.paa_mode != 1) return false;
-    if (o.phase1_max < 0 || o.refine_k < 0) return false;
-    for (int i = 0; i < 9; i++)
+    if (o.phase1_max < 0 || o.refine_k < 0 || o.local_cols < 0 || o.word_cols < 0) return false;
+    for (int i = 0; i < 7; i++)
         if (o.reserved[i] != 0) return false;
     return true;
 }
@@ -89,6 +89,13 @@ size_t carve(dd_plan_s* p, char* base) {
     p->blk = c.take<int32_t>(nblk + 1);
     p->res_dev = c.take<dd_result_t>(1);
     p->seq_rows = c.take<int32_t>(N);
+    p->mubin = c.take<int32_t>(N);
+    p->hist_mu = c.take<int32_t>(dd::kMuBins);
+    p->blockcnt_mu = c.take<int32_t>((size_t)nh * dd::kMuBins);
+    p->binstart = c.take<int32_t>(dd::kMuBins + 1);
+    p->sig = c.take<int32_t>(N);
+    p->sigpos = c.take<int32_t>(N);
+    p->ranges = c.take<int4>(N / 128 + 2);
     return (c.off + kAlign - 1) / kAlign * kAlign;
 }
 
@@ -115,7 +122,31 @@ struct BusyGuard {
     }
 };
 
+void prof_begin(dd_plan_s* p, cudaStream_t s) {
+    p->ev_used = 0;
+    if (p->profiling) cudaEventRecord(p->call_ev[0], s);
+}
+
+// Reads back the events of a finished synchronous call.
+void prof_end(dd_plan_s* p, cudaStream_t s, int64_t pairs) {
+    if (!p->profiling) return;
+    cudaEventRecord(p->call_ev[1], s);
+    cudaEventSynchronize(p->call_ev[1]);
+    dd_profile_t r{};
+    r.precision = p->opt.precision;
+    r.dist_launches = p->ev_used / 2;
+    for (int k = 0; k + 1 < p->ev_used; k += 2) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, p->ev[k], p->ev[k + 1]) == cudaSuccess) r.dist_ms += ms;
+    }
+    float call = 0.f;
+    if (cudaEventElapsedTime(&call, p->call_ev[0], p->call_ev[1]) == cudaSuccess) r.call_ms = call;
+    r.computed_pairs = pairs;
+    p->prof = r;
+}
+
 dd_status_t search_sync(dd_plan_s* p, const float* T_dev, dd_result_t* out, cudaStream_t s) {
+    prof_begin(p, s);
     cudaError_t e = dd::launch_search(p, T_dev, p->res_dev, s);
     if (e != cudaSuccess) return from_cuda(e);
     e = cudaMemcpyAsync(p->res_host, p->res_dev, sizeof(dd_result_t), cudaMemcpyDeviceToHost, s);
@@ -123,8 +154,22 @@ dd_status_t search_sync(dd_plan_s* p, const float* T_dev, dd_result_t* out, cuda
     e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return from_cuda(e);
     *out = *p->res_host;
+    prof_end(p, s, out->computed_pairs);
     return (dd_status_t)out->status;
 }
+
+}  // namespace
+
+namespace dd {
+void prof_mark(dd_plan_s* p, cudaStream_t s, bool start) {
+    if (!p->profiling) return;
+    if (p->ev_used >= (int)p->ev.size()) return;  // pool exhausted: later launches untimed
+    (void)start;
+    cudaEventRecord(p->ev[p->ev_used++], s);
+}
+}  // namespace dd
+
+namespace {
 
 }  // namespace
 
@@ -140,6 +185,8 @@ void dd_options_default(dd_options_t* opt) {
     opt->paa_mode = 0;
     opt->phase1_max = 4096;
     opt->refine_k = 512;
+    opt->local_cols = 128;
+    opt->word_cols = 512;
 }
 
 size_t dd_plan_footprint(int64_t m, int32_t n, const dd_options_t* opt) {
@@ -233,6 +280,9 @@ dd_status_t dd_plan_create(dd_plan_t* plan, int64_t m, int32_t n, const dd_optio
 void dd_plan_destroy(dd_plan_t p) {
     if (!p) return;
     cudaDeviceSynchronize();
+    for (cudaEvent_t e : p->ev) cudaEventDestroy(e);
+    for (cudaEvent_t e : p->call_ev)
+        if (e) cudaEventDestroy(e);
     if (p->res_host) cudaFreeHost(p->res_host);
     if (p->own_ws && p->ws) cudaFree(p->ws);
     delete p;
@@ -343,6 +393,25 @@ dd_status_t dd_plan_view(dd_plan_t p, dd_view_t* v) {
 }
 
 int64_t dd_plan_last_launches(dd_plan_t p) { return p ? p->launches : -1; }
+
+dd_status_t dd_plan_set_profiling(dd_plan_t p, int32_t enable) {
+    if (!p) return DD_EINVAL;
+    if (enable && p->ev.empty()) {
+        p->ev.resize(256);
+        for (auto& e : p->ev)
+            if (cudaEventCreate(&e) != cudaSuccess) return DD_ECUDA;
+        for (auto& e : p->call_ev)
+            if (cudaEventCreate(&e) != cudaSuccess) return DD_ECUDA;
+    }
+    p->profiling = enable != 0;
+    return DD_OK;
+}
+
+dd_status_t dd_plan_get_profile(dd_plan_t p, dd_profile_t* out) {
+    if (!p || !out) return DD_EINVAL;
+    *out = p->prof;
+    return DD_OK;
+}
 
 const char* dd_status_string(dd_status_t s) {
     switch (s) {

@@ -20,6 +20,7 @@ constexpr int kScanElems = 4096;         // elements per block of the FP64 prefi
 constexpr int kHistRows = 4096;          // rows per block of the word histogram / scatter
 constexpr int kCompactRows = 2048;       // list entries per block of the compaction
 constexpr int kTopkBins = 4096;          // bins of the top-k radix select (float bits >> 19)
+constexpr int kMuBins = 4096;            // bins of the mean-bucketed row order
 constexpr int kMaxLaunchSlots = 512;     // work counters per search
 constexpr int kMaxListSlots = 256;       // list counts per search
 
@@ -43,7 +44,9 @@ struct Ctrl {
     int ncomplete;                // rows that completed a full scan
     int err;                      // device-side error code (0 = none)
     unsigned int topk_thr;        // top-k threshold (float bits)
-    int pad_[3];
+    int fmin;                     // smallest non-zero word frequency (Cand words)
+    int pad_[2];
+    int smax[64];                 // largest per-tile segment count of each tile-range launch
     int cnt[kMaxListSlots];       // list counts written by compactions
     int work[kMaxLaunchSlots];    // dynamic-schedule work counters, one per launch
     int topk_hist[kTopkBins];     // radix-select histogram
@@ -58,10 +61,17 @@ struct ListRef {
 };
 
 // Column schedule of one wave.
+//   mode 0: every row tile scans virtual columns [v_lo, v_hi) of the word
+//           order, read backwards (virtual v -> position N-1-v);
+//   mode 1: each row tile scans `local_cols` rows that share the SAX word of
+//           its first row (Index_Word neighbourhood), starting half a word away;
+//   mode 2: each row tile scans its own range of the mean-bucketed order
+//           (ranges[t] = (L, H, C, segments)) in segments of seg_cols
+//           columns, alternating right / left of C, nearest first.
 struct ColSpec {
-    int mode;        // 0 = global order, 1 = same-word (bucket) neighbourhood
-    int v_lo, v_hi;  // mode 0: virtual columns [v_lo, v_hi); virtual v -> order position N-1-v
-    int local_cols;  // mode 1: columns of the row tile's own word scanned
+    int mode;
+    int v_lo, v_hi;
+    int local_cols;
 };
 
 struct PrepArrays {
@@ -99,6 +109,10 @@ struct ScanArgs {
     const int32_t* hist;
     const int32_t* word_start;
     ColSpec col;
+    const int32_t* sig;       // mean-bucketed order (mode 2)
+    const int4* ranges;       // per row tile (mode 2)
+    const int* smax;          // largest segment count over the tiles (mode 2)
+    int seg_cols;             // columns per segment (mode 2)
     uint32_t* rmin;           // per orig row: float bits of the running minimum
     const Ctrl* ctrl_ro;      // bsf, flags
     Ctrl* ctrl;
@@ -150,8 +164,22 @@ struct dd_plan_s {
     dd_result_t* res_dev = nullptr;
     dd_result_t* res_host = nullptr;  // pinned
     int32_t* seq_rows = nullptr;      // 0..N-1
+    int32_t* mubin = nullptr;         // [N] mean bin of each row
+    int32_t* hist_mu = nullptr;       // [kMuBins]
+    int32_t* blockcnt_mu = nullptr;   // [nh * kMuBins]
+    int32_t* binstart = nullptr;      // [kMuBins + 1]
+    int32_t* sig = nullptr;           // [N] rows in mean-bucketed order
+    int32_t* sigpos = nullptr;        // [N] position of each row in sig
+    int4* ranges = nullptr;           // [N/128 + 1] per-tile column range (L, H, C, segments)
 
     double beta_host[dd::kMaxAlphabet];
+
+    // tracing (dd_plan_set_profiling)
+    bool profiling = false;
+    std::vector<cudaEvent_t> ev;   // pool: pairs (start, stop) around distance launches
+    int ev_used = 0;
+    cudaEvent_t call_ev[2] = {nullptr, nullptr};
+    dd_profile_t prof{};
 };
 
 namespace dd {
@@ -164,6 +192,8 @@ cudaError_t launch_profile(dd_plan_s* p, const float* T, const int32_t* rows, in
                            cudaStream_t s);
 // scan_fp32.cu
 cudaError_t launch_scan_fp32(const ScanArgs& a, int grid, cudaStream_t s);
+// api.cu: event pair around a distance launch when profiling (start=true before, false after)
+void prof_mark(dd_plan_s* p, cudaStream_t s, bool start);
 int scan_fp32_grid(const dd_plan_s* p);
 
 void host_breakpoints(int A, double* beta);

@@ -379,6 +379,7 @@ __global__ void __launch_bounds__(1024) k_word_plan(const int32_t* __restrict__ 
             if (c == fmin) ncand += c;
         }
         ctrl->ncand = ncand;
+        ctrl->fmin = fmin;
         int n1 = ncand < phase1_max ? ncand : phase1_max;
         ctrl->n1 = n1;
         ctrl->n2 = (int)(N - n1);
@@ -442,6 +443,67 @@ __global__ void k_word_scatter(const int32_t* __restrict__ code, int64_t N, int 
     }
 }
 
+// ---- mean-bucketed row order --------------------------------------------------
+// Rows binned by their mean mu_i over [min t^, max t^] (kMuBins equal bins).
+// For globally normalised subsequences d^2(i, j) >= n (mu_i - mu_j)^2, so the
+// rows whose distance to row i can be below R lie in the bins within
+// sqrt(R / n) of mu_i: a contiguous range of this order.
+__global__ void __launch_bounds__(256) k_mu_bins(const double* __restrict__ mu_w, int64_t N, const double* stats,
+                                                 int32_t* __restrict__ bin, double* stats_out) {
+    const double mu = stats[0], sigma = stats[1];
+    const double lo = sigma > 0.0 ? (stats[5] - mu) / sigma : 0.0;
+    const double hi = sigma > 0.0 ? (stats[4] - mu) / sigma : 0.0;
+    const double w = (hi - lo) / (double)kMuBins;
+    const double invw = w > 0.0 ? 1.0 / w : 0.0;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0) {
+        stats_out[6] = lo;
+        stats_out[7] = w;
+    }
+    if (i >= N) return;
+    double b = floor((mu_w[i] - lo) * invw);
+    int bi = b < 0.0 ? 0 : (b >= (double)kMuBins ? kMuBins - 1 : (int)b);
+    bin[i] = bi;
+}
+
+// Bin order plan: bin offsets (exclusive scan in bin order) and each block's
+// base offset per bin (column scan of the block counts).  One block.
+__global__ void __launch_bounds__(1024) k_bin_plan(const int32_t* __restrict__ hist, int D, int nblk,
+                                                   int32_t* __restrict__ blockcnt, int32_t* __restrict__ binstart) {
+    __shared__ int32_t part[1024];
+    const int per = (D + 1023) / 1024;
+    const int lo = threadIdx.x * per, hi = min(D, lo + per);
+    int s = 0;
+    for (int h = lo; h < hi; h++) s += hist[h];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int run = 0;
+        for (int t = 0; t < 1024; t++) {
+            int x = part[t];
+            part[t] = run;
+            run += x;
+        }
+        binstart[D] = run;
+    }
+    __syncthreads();
+    int run = part[threadIdx.x];
+    for (int h = lo; h < hi; h++) {
+        binstart[h] = run;
+        run += hist[h];
+    }
+    __syncthreads();
+    for (int h = threadIdx.x; h < D; h += blockDim.x) {
+        int r = binstart[h];
+        for (int b = 0; b < nblk; b++) {
+            int64_t ix = (int64_t)b * D + h;
+            int c = blockcnt[ix];
+            blockcnt[ix] = r;
+            r += c;
+        }
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_prep(dd_plan_s* p, const float* T, cudaStream_t s) {
@@ -472,7 +534,17 @@ cudaError_t launch_prep(dd_plan_s* p, const float* T, cudaStream_t s) {
     if (nw < 1) nw = 1;
     while (kHistRows % nw) nw--;
     k_word_scatter<<<nh, nw * 32, sizeof(int32_t) * nw * D, s>>>(p->code, N, D, p->blockcnt, p->order, p->pos_of);
-    p->launches += 12;
+    // mean-bucketed order (sig) with bin offsets
+    k_mu_bins<<<gN, 256, 0, s>>>(p->mu_w, N, p->stats, p->mubin, p->stats);
+    cudaMemsetAsync(p->hist_mu, 0, sizeof(int32_t) * kMuBins, s);
+    k_word_hist<<<nh, 1024, sizeof(int32_t) * kMuBins, s>>>(p->mubin, N, kMuBins, p->hist_mu, p->blockcnt_mu);
+    k_bin_plan<<<1, 1024, 0, s>>>(p->hist_mu, kMuBins, nh, p->blockcnt_mu, p->binstart);
+    int nw2 = (48 * 1024 / 4) / kMuBins;
+    if (nw2 < 1) nw2 = 1;
+    while (kHistRows % nw2) nw2--;
+    k_word_scatter<<<nh, nw2 * 32, sizeof(int32_t) * nw2 * kMuBins, s>>>(p->mubin, N, kMuBins, p->blockcnt_mu, p->sig,
+                                                                        p->sigpos);
+    p->launches += 16;
     return cudaGetLastError();
 }
 

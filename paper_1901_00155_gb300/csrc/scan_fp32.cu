@@ -76,21 +76,30 @@ __global__ void __launch_bounds__(NT, 2) k_scan_fp32(ScanArgs a) {
     const int off = a.rows.off_dev ? *a.rows.off_dev : 0;
     const int RT = (cnt + BM - 1) / BM;
     if (RT <= 0) return;
-    int V;
-    if (a.col.mode == 0) {
-        const int hi = a.col.v_hi < a.N ? a.col.v_hi : a.N;
-        V = hi - a.col.v_lo;
+    const int mode = a.col.mode;
+    // work decomposition
+    long long items;
+    int nseg = 1, CT = 0, V = 0;
+    if (mode == 2) {
+        const int smax = *a.smax;
+        if (smax <= 0) return;
+        items = (long long)RT * smax;
     } else {
-        V = a.col.local_cols;
+        if (mode == 0) {
+            const int hi = a.col.v_hi < a.N ? a.col.v_hi : a.N;
+            V = hi - a.col.v_lo;
+        } else {
+            V = a.col.local_cols;
+        }
+        if (V <= 0) return;
+        CT = (V + BN - 1) / BN;
+        nseg = (a.target_items + RT - 1) / RT;
+        int maxseg = CT / (a.min_seg_tiles > 0 ? a.min_seg_tiles : 1);
+        if (maxseg < 1) maxseg = 1;
+        if (nseg > maxseg) nseg = maxseg;
+        if (nseg < 1) nseg = 1;
+        items = (long long)RT * nseg;
     }
-    if (V <= 0) return;
-    const int CT = (V + BN - 1) / BN;
-    int nseg = (a.target_items + RT - 1) / RT;
-    int maxseg = CT / (a.min_seg_tiles > 0 ? a.min_seg_tiles : 1);
-    if (maxseg < 1) maxseg = 1;
-    if (nseg > maxseg) nseg = maxseg;
-    if (nseg < 1) nseg = 1;
-    const long long items = (long long)RT * nseg;
 
     const int tid = threadIdx.x;
     const int tx = tid & 15, ty = tid >> 4;
@@ -99,12 +108,38 @@ __global__ void __launch_bounds__(NT, 2) k_scan_fp32(ScanArgs a) {
     unsigned long long pairs = 0;
 
     for (;;) {
+        __syncthreads();  // the previous item is done with sm.item and the tiles
         if (tid == 0) sm.item = atomicAdd(&a.ctrl->work[a.work_slot], 1);
         __syncthreads();
         const int item = sm.item;
         if (item >= items) break;
-        const int rt = item / nseg, sg = item % nseg;
-        const int ct0 = (int)(((long long)sg * CT) / nseg), ct1 = (int)(((long long)(sg + 1) * CT) / nseg);
+        // item -> row tile + column tiles
+        int rt, ct0, ct1;
+        int pa = 0, pb = 0, dir = 1;  // mode 2: positions [pa, pb) of sig, walked up (dir 1) or down
+        if (mode == 2) {
+            const int s_rank = item / RT;
+            rt = item % RT;
+            const int4 r = a.ranges[rt];
+            if (s_rank >= r.w) continue;  // uniform: the whole block skips
+            const int side = s_rank & 1, idx = s_rank >> 1;
+            if (side == 0) {
+                pa = r.z + idx * a.seg_cols;
+                pb = min(pa + a.seg_cols, r.y);
+                dir = 1;
+            } else {
+                pb = r.z - idx * a.seg_cols;
+                pa = max(pb - a.seg_cols, r.x);
+                dir = -1;
+            }
+            if (pa >= pb) continue;
+            ct0 = 0;
+            ct1 = (pb - pa + BN - 1) / BN;
+        } else {
+            rt = item / nseg;
+            const int sg = item % nseg;
+            ct0 = (int)(((long long)sg * CT) / nseg);
+            ct1 = (int)(((long long)(sg + 1) * CT) / nseg);
+        }
 
         if (tid < BM) {
             const int r = rt * BM + tid;
@@ -117,7 +152,7 @@ __global__ void __launch_bounds__(NT, 2) k_scan_fp32(ScanArgs a) {
         __syncthreads();
         // same-word neighbourhood of the tile's first row (mode 1)
         int bs = 0, bsz = 1, startoff = 0, L = V;
-        if (a.col.mode == 1) {
+        if (mode == 1) {
             const int r0 = sm.row[0];
             const int h = a.code[r0];
             bs = a.word_start[h];
@@ -145,16 +180,15 @@ __global__ void __launch_bounds__(NT, 2) k_scan_fp32(ScanArgs a) {
             int valid_col = 0;
             if (tid < BN) {
                 int cj = -1;
-                if (a.col.mode == 0) {
+                if (mode == 0) {
                     const int v = a.col.v_lo + ct * BN + tid;
                     if (v < a.col.v_lo + V) cj = a.order[a.N - 1 - v];
-                } else {
+                } else if (mode == 1) {
                     const int v = ct * BN + tid;
-                    if (v < L) {
-                        int p = startoff + v;
-                        p = p % bsz;
-                        cj = a.order[bs + p];
-                    }
+                    if (v < L) cj = a.order[bs + (startoff + v) % bsz];
+                } else {
+                    const int p = dir > 0 ? pa + ct * BN + tid : pb - 1 - ct * BN - tid;
+                    if (p >= pa && p < pb) cj = a.sig[p];
                 }
                 sm.col[tid] = cj;
                 valid_col = cj >= 0;

@@ -20,10 +20,12 @@ __device__ __forceinline__ bool is_alive(uint32_t rbits, uint32_t bsf_bits) {
 }
 
 // Compaction pass 1: predicate per list entry + per-block counts.
-// pred 0: alive against the best-so-far; pred 1: alive and rmin >= top-k threshold.
+// pred 0: alive against the best-so-far; pred 1: alive and rmin >= top-k
+// threshold; pred 2: member of Cand.
 __global__ void __launch_bounds__(256) k_compact_flags(ListRef in, const uint32_t* __restrict__ rmin,
-                                                       const Ctrl* ctrl, int pred, uint8_t* __restrict__ flag,
-                                                       int* __restrict__ blk) {
+                                                       const Ctrl* ctrl, int pred, const int32_t* __restrict__ code,
+                                                       const int32_t* __restrict__ hist, int phase1_max,
+                                                       uint8_t* __restrict__ flag, int* __restrict__ blk) {
     __shared__ int sh;
     if (threadIdx.x == 0) sh = 0;
     __syncthreads();
@@ -38,8 +40,14 @@ __global__ void __launch_bounds__(256) k_compact_flags(ListRef in, const uint32_
         const int r = base + q;
         if (r < cnt) {
             const int i = in.base[off + r];
-            const uint32_t b = rmin[i];
-            const bool keep = is_alive(b, bsf) && b >= thr;
+            bool keep;
+            if (pred == 2) {
+                // Cand (Eq. 7): rows whose word has the smallest frequency
+                keep = hist[code[i]] == ctrl->fmin && ctrl->ncand <= phase1_max;
+            } else {
+                const uint32_t b = rmin[i];
+                keep = is_alive(b, bsf) && b >= thr;
+            }
             flag[r] = keep;
             local += keep;
         }
@@ -172,6 +180,77 @@ __global__ void __launch_bounds__(256) k_complete(ListRef in, const uint32_t* __
     }
 }
 
+// Column range of every 128-row tile of a list in the mean-bucketed order.
+// kind 0 (local): the tile's own positions widened by K on each side.
+// kind 1 (lower bound): for each row, the bins within sqrt(R / n) of its mean,
+// R = its running minimum; d^2 >= n (mu_i - mu_j)^2 means no column outside
+// can lower R.  A row with no finite R gets every column.
+__global__ void __launch_bounds__(128) k_tile_ranges(ListRef L, int kind, int K, int seg_cols,
+                                                     const int32_t* __restrict__ sigpos,
+                                                     const int32_t* __restrict__ mubin,
+                                                     const int32_t* __restrict__ binstart,
+                                                     const uint32_t* __restrict__ rmin, const double* stats, int n,
+                                                     int N, int4* __restrict__ ranges, int* smax) {
+    __shared__ int red[4][4];
+    const int cnt = *L.cnt_dev;
+    const int off = L.off_dev ? *L.off_dev : 0;
+    const int t = blockIdx.x;
+    if (t * 128 >= cnt) return;
+    const int r = t * 128 + threadIdx.x;
+    int lo = 0x7fffffff, hi = -1, qmin = 0x7fffffff, qmax = -1;
+    if (r < cnt) {
+        const int i = L.base[off + r];
+        const int q = sigpos[i];
+        qmin = qmax = q;
+        if (kind == 0) {
+            lo = q - K;
+            hi = q + 1 + K;
+        } else {
+            const float R = __uint_as_float(rmin[i]);
+            const double w = stats[7];
+            if (!(R < 1e30f) || !(w > 0.0)) {
+                lo = 0;
+                hi = N;
+            } else {
+                const double h = sqrt((double)R / (double)n) * (1.0 + 1e-4) + 1e-12;
+                const double kb = ceil(h / w) + 1.0;
+                const int k = kb > (double)kMuBins ? kMuBins : (int)kb;
+                const int b = mubin[i];
+                lo = binstart[b - k < 0 ? 0 : b - k];
+                hi = binstart[b + k + 1 > kMuBins ? kMuBins : b + k + 1];
+            }
+        }
+    }
+    lo = __reduce_min_sync(0xffffffffu, lo);
+    hi = __reduce_max_sync(0xffffffffu, hi);
+    qmin = __reduce_min_sync(0xffffffffu, qmin);
+    qmax = __reduce_max_sync(0xffffffffu, qmax);
+    const int wid = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) {
+        red[0][wid] = lo;
+        red[1][wid] = hi;
+        red[2][wid] = qmin;
+        red[3][wid] = qmax;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w2 = 1; w2 < 4; w2++) {
+            lo = min(lo, red[0][w2]);
+            hi = max(hi, red[1][w2]);
+            qmin = min(qmin, red[2][w2]);
+            qmax = max(qmax, red[3][w2]);
+        }
+        lo = lo < 0 ? 0 : lo;
+        hi = hi > N ? N : hi;
+        int C = (qmin + qmax + 1) / 2;
+        C = C < lo ? lo : (C > hi ? hi : C);
+        const int side = max(hi - C, C - lo);
+        const int nseg = 2 * ((side + seg_cols - 1) / seg_cols);
+        ranges[t] = make_int4(lo, hi, C, nseg);
+        atomicMax(smax, nseg);
+    }
+}
+
 __global__ void k_finalize(const Ctrl* ctrl, dd_result_t* out) {
     if (threadIdx.x != 0) return;
     dd_result_t r;
@@ -214,11 +293,14 @@ __global__ void k_check_rows(const int32_t* __restrict__ rows, int count, int64_
 
 // ---------------------------------------------------------------------------
 // Host-side sequencing (no synchronisation; counts stay on the device).
+constexpr int kSegCols = 512;
+
 struct Seq {
     dd_plan_s* p;
     cudaStream_t s;
     int work_slot = 0;
     int cnt_slot = 0;
+    int smax_slot = 0;
     cudaError_t err = cudaSuccess;
 
     void check() {
@@ -226,7 +308,14 @@ struct Seq {
     }
     int* cnt_ptr(int slot) { return &p->ctrl->cnt[slot]; }
 
-    void scan(ListRef rows, ColSpec col, int abandon) {
+    ListRef constant_list(const int32_t* base, int count) {
+        const int slot = cnt_slot++;
+        k_set_int<<<1, 1, 0, s>>>(cnt_ptr(slot), count);
+        p->launches++;
+        return ListRef{base, nullptr, cnt_ptr(slot)};
+    }
+
+    void scan(ListRef rows, ColSpec col, int abandon, const int* smax = nullptr) {
         ScanArgs a{};
         a.t32 = p->t32;
         a.N = (int)p->N;
@@ -238,6 +327,10 @@ struct Seq {
         a.hist = p->hist;
         a.word_start = p->word_start;
         a.col = col;
+        a.sig = p->sig;
+        a.ranges = p->ranges;
+        a.smax = smax;
+        a.seg_cols = kSegCols;
         a.rmin = p->rmin;
         a.ctrl_ro = p->ctrl;
         a.ctrl = p->ctrl;
@@ -250,9 +343,26 @@ struct Seq {
             err = cudaErrorInvalidValue;
             return;
         }
+        prof_mark(p, s, true);
         cudaError_t e = launch_scan_fp32(a, grid, s);
+        prof_mark(p, s, false);
         if (err == cudaSuccess) err = e;
         p->launches++;
+    }
+
+    // Column ranges of the list's tiles (kind 0: local +-K, kind 1: lower bound).
+    const int* ranges(ListRef rows, int kind, int K) {
+        const int slot = smax_slot++;
+        if (smax_slot > 64) {
+            err = cudaErrorInvalidValue;
+            return nullptr;
+        }
+        const int tiles = (int)((p->N + 127) / 128);
+        k_tile_ranges<<<tiles, 128, 0, s>>>(rows, kind, K, kSegCols, p->sigpos, p->mubin, p->binstart, p->rmin,
+                                            p->stats, p->n, (int)p->N, p->ranges, &p->ctrl->smax[slot]);
+        p->launches++;
+        check();
+        return &p->ctrl->smax[slot];
     }
 
     // Order-preserving compaction of `in` into `out`; returns the new list.
@@ -263,7 +373,8 @@ struct Seq {
             err = cudaErrorInvalidValue;
             return in;
         }
-        k_compact_flags<<<nblk, 256, 0, s>>>(in, p->rmin, p->ctrl, pred, p->flag, p->blk);
+        k_compact_flags<<<nblk, 256, 0, s>>>(in, p->rmin, p->ctrl, pred, p->code, p->hist, p->opt.phase1_max,
+                                             p->flag, p->blk);
         k_compact_scan<<<1, 1024, 0, s>>>(p->blk, nblk, cnt_ptr(slot));
         k_compact_scatter<<<nblk, 256, 0, s>>>(in, p->flag, p->blk, out);
         p->launches += 3;
@@ -278,27 +389,13 @@ struct Seq {
         check();
     }
 
-    // Full scan of every column for the rows of `in`, in waves of geometrically
-    // growing column chunks with compaction in between; survivors complete.
-    void scan_full(ListRef in, int32_t* bufA, int32_t* bufB, int first_tiles, int factor) {
-        const int N = (int)p->N;
-        const int BN = kF32BN;
-        ListRef cur = in;
-        int32_t* bufs[2] = {bufA, bufB};
-        int which = 0;
-        long long lo = 0, chunk = first_tiles;
-        while (lo * BN < N) {
-            long long hi = lo + chunk;
-            ColSpec c{0, (int)(lo * BN), (int)(hi * BN < N ? hi * BN : N), 0};
-            scan(cur, c, 1);
-            lo = hi;
-            chunk *= factor;
-            if (lo * BN < N) {
-                cur = compact(cur, bufs[which], 0);
-                which ^= 1;
-            }
-        }
-        complete(cur);
+    // Full scan of each row of `in`: every column whose lower bound
+    // n (mu_i - mu_j)^2 is below the row's running minimum, nearest mean
+    // first, abandoning against the best-so-far; survivors complete.
+    void full(ListRef in) {
+        const int* sm = ranges(in, 1, 0);
+        scan(in, ColSpec{2, 0, 0, 0}, 1, sm);
+        complete(in);
     }
 };
 
@@ -315,53 +412,40 @@ cudaError_t launch_search(dd_plan_s* p, const float* T, dd_result_t* out_dev, cu
 
     Seq q{p, s};
     const dd_options_t& o = p->opt;
-    const bool abandon = o.early_abandon != 0;
-    if (!abandon) {
+    if (!o.early_abandon) {
         // every row scans every column; the argmax runs over all rows
-        k_set_int<<<1, 1, 0, s>>>(q.cnt_ptr(q.cnt_slot), (int)p->N);
-        ListRef all{p->seq_rows, nullptr, q.cnt_ptr(q.cnt_slot++)};
+        ListRef all = q.constant_list(p->seq_rows, (int)p->N);
         q.scan(all, ColSpec{0, 0, (int)p->N, 0}, 0);
         q.complete(all);
-        p->launches++;
     } else {
-        // Algorithm 3 (PotentialDiscord): the rarest-word rows, full scans.
-        ListRef p1{p->order, nullptr, &p->ctrl->n1};
-        q.scan_full(p1, p->list[0], p->list[1], 64, 4);
-        // Algorithm 4 (RefineDiscord) over the remaining rows.  Wave 0: each
-        // row tile scans the rows that share its SAX word (Index_Word first).
-        ListRef p2{p->order, &p->ctrl->n1, &p->ctrl->n2};
-        q.scan(p2, ColSpec{1, 0, 0, 2048}, 1);
-        ListRef surv = q.compact(p2, p->list[0], 0);
-        // Raise the best-so-far: full scans of the survivors with the largest
-        // running minima (the likeliest discords) first.
+        ListRef all = q.constant_list(p->sig, (int)p->N);
+        // Upper bounds for every row from its nearest-mean neighbourhood.
+        if (o.local_cols > 0) {
+            const int* sm = q.ranges(all, 0, o.local_cols);
+            q.scan(all, ColSpec{2, 0, 0, 0}, 1, sm);
+        }
+        // Algorithm 3 (PotentialDiscord): the Cand rows (rarest SAX words).
+        ListRef cand = q.compact(all, p->list[0], 2);
+        q.full(cand);
+        // Raise the best-so-far further: full scans of the rows with the
+        // largest upper bounds (the likeliest discords) next.
+        ListRef alive = q.compact(all, p->list[1], 0);
         if (o.refine_k > 0) {
-            k_topk_hist<<<2 * p->sm_count, 256, 0, s>>>(surv, p->rmin, p->ctrl);
+            k_topk_hist<<<2 * p->sm_count, 256, 0, s>>>(alive, p->rmin, p->ctrl);
             k_topk_thr<<<1, 32, 0, s>>>(p->ctrl, o.refine_k);
             p->launches += 2;
-            ListRef top = q.compact(surv, p->list[2], 1);
-            q.scan_full(top, p->list[1], p->list[3], 64, 4);
+            ListRef top = q.compact(alive, p->list[2], 1);
+            q.full(top);
         }
-        // every other survivor: global waves, then completion
-        {
-            const int N = (int)p->N;
-            const int BN = kF32BN;
-            ListRef cur = q.compact(surv, p->list[1], 0);
-            int32_t* bufs[2] = {p->list[2], p->list[1]};
-            int which = 0;
-            long long lo = 0, chunk = 8;
-            while (lo * BN < N) {
-                long long hi = lo + chunk;
-                ColSpec c{0, (int)(lo * BN), (int)(hi * BN < N ? hi * BN : N), 0};
-                q.scan(cur, c, 1);
-                lo = hi;
-                chunk *= 4;
-                if (lo * BN < N) {
-                    cur = q.compact(cur, bufs[which], 0);
-                    which ^= 1;
-                }
-            }
-            q.complete(cur);
+        // Algorithm 4 (RefineDiscord) over the remaining rows: rows sharing the
+        // SAX word first (Index_Word), then every column the bound allows.
+        if (o.word_cols > 0) {
+            ListRef words = q.constant_list(p->order, (int)p->N);
+            ListRef wl = q.compact(words, p->list[3], 0);
+            q.scan(wl, ColSpec{1, 0, 0, o.word_cols}, 1);
         }
+        ListRef rest = q.compact(alive, p->list[2], 0);
+        q.full(rest);
     }
     k_finalize<<<1, 32, 0, s>>>(p->ctrl, out_dev);
     p->launches++;
@@ -381,11 +465,10 @@ cudaError_t launch_profile(dd_plan_s* p, const float* T, const int32_t* rows, in
     Seq q{p, s};
     const int32_t* r = rows ? rows : p->seq_rows;
     const int c = rows ? count : (int)p->N;
-    k_set_int<<<1, 1, 0, s>>>(q.cnt_ptr(0), c);
-    q.cnt_slot = 1;
-    q.scan(ListRef{r, nullptr, q.cnt_ptr(0)}, ColSpec{0, 0, (int)p->N, 0}, 0);
+    ListRef L = q.constant_list(r, c);
+    q.scan(L, ColSpec{0, 0, (int)p->N, 0}, 0);
     k_gather_min<<<(c + 255) / 256, 256, 0, s>>>(r, c, p->rmin, nn2);
-    p->launches += 2;
+    p->launches++;
     q.check();
     return q.err;
 }
