@@ -96,6 +96,20 @@ size_t carve(dd_plan_s* p, char* base) {
     p->sig = c.take<int32_t>(N);
     p->sigpos = c.take<int32_t>(N);
     p->ranges = c.take<int4>(N / 128 + 2);
+    if (p->opt.precision != DD_FP32) {
+        p->kpad = (p->n + 63) / 64 * 64;
+        p->S16 = c.take<uint16_t>((size_t)N * p->kpad);
+        p->A16 = c.take<uint16_t>((size_t)N * p->kpad);
+        p->colmu = c.take<float>(N);
+        p->colc = c.take<float>(N);
+        p->rowmu = c.take<float>(N);
+        p->rowc = c.take<float>(N);
+        p->rowsc = c.take<float>(N);
+        p->alpha = c.take<float>(N);
+        p->gam = c.take<float>(N);
+        p->q2 = c.take<float>(N);
+        p->ex64 = c.take<double>(N);
+    }
     return (c.off + kAlign - 1) / kAlign * kAlign;
 }
 
@@ -217,7 +231,7 @@ dd_status_t dd_plan_create(dd_plan_t* plan, int64_t m, int32_t n, const dd_optio
         dd_options_default(&o);
     if (!valid_options(o) || !valid_sizes(m, n)) return DD_EINVAL;
     clamp_word(o, n);
-    if (o.precision != DD_FP32) return DD_ENOTSUP;
+    if (o.precision != DD_FP32 && !dd::tc_supported(n)) return DD_ENOTSUP;
     if (workspace && (reinterpret_cast<uintptr_t>(workspace) % kAlign) != 0) return DD_EINVAL;
     dd_plan_s* p = new (std::nothrow) dd_plan_s();
     if (!p) return DD_ENOMEM;
@@ -266,6 +280,7 @@ dd_status_t dd_plan_create(dd_plan_t* plan, int64_t m, int32_t n, const dd_optio
         k_iota<<<(unsigned)((p->N + 255) / 256), 256>>>(p->seq_rows, p->N);
         e = cudaGetLastError();
     }
+    if (e == cudaSuccess && o.precision != DD_FP32) e = dd::tc_make_maps(p);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
         cudaFreeHost(p->res_host);

@@ -2,6 +2,7 @@
 // shared by the CUDA translation units of libdd.so.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -45,7 +46,12 @@ struct Ctrl {
     int err;                      // device-side error code (0 = none)
     unsigned int topk_thr;        // top-k threshold (float bits)
     int fmin;                     // smallest non-zero word frequency (Cand words)
-    int pad_[2];
+    unsigned int tc_scmax;        // Gram form: max sqrt(c_j) (float bits)
+    unsigned int tc_cmax;         // Gram form: max c_j (float bits)
+    unsigned int tc_mumax;        // Gram form: max |sqrt(n) mu_j| (float bits)
+    int ncandidates;              // rows rescored in FP64
+    int best_idx;                 // smallest index attaining best64
+    unsigned long long best64;    // exact nn^2 of the discord (double bits)
     int smax[64];                 // largest per-tile segment count of each tile-range launch
     int cnt[kMaxListSlots];       // list counts written by compactions
     int work[kMaxLaunchSlots];    // dynamic-schedule work counters, one per launch
@@ -122,6 +128,49 @@ struct ScanArgs {
     int target_items;
 };
 
+// Upper / lower bounds of a row's nearest-neighbour distance from its running
+// minimum D: identical to D for the FP32 form; D +- F_i(D) for the Gram form.
+struct TcBound {
+    const float* alpha;
+    const float* gam;
+    const float* q2;
+    float beta;
+    int on;
+};
+
+__device__ __forceinline__ float row_ub(const TcBound& b, int i, float D) {
+    if (!b.on) return D;
+    return D + (b.alpha[i] + b.beta * D + b.gam[i] * sqrtf(fmaxf(D, 0.f) + b.q2[i]));
+}
+__device__ __forceinline__ float row_lb(const TcBound& b, int i, float D) {
+    if (!b.on) return D;
+    const float g = b.gam[i];
+    const float v = D - (b.alpha[i] + b.beta * D + g * sqrtf(fmaxf(D, 0.f) + b.q2[i])) - g * g;
+    return v > 0.f ? v : 0.f;
+}
+
+struct TcArgs {
+    int N, n, nka, stages, seg_cols, mode;
+    ListRef rows;
+    int a_direct, a_row0;
+    const int32_t* sig;
+    const float* colmu;
+    const float* colc;
+    const float* rowmu;
+    const float* rowc;
+    const float* alpha;
+    const float* gam;
+    const float* q2;
+    float beta;
+    const int4* ranges;
+    const int* smax;
+    uint32_t* rmin;
+    Ctrl* ctrl;
+    const double* stats;
+    int abandon, work_slot;
+    uint32_t idesc;
+};
+
 }  // namespace dd
 
 // Plan: everything a search needs, carved out of one device workspace.
@@ -172,6 +221,21 @@ struct dd_plan_s {
     int32_t* sigpos = nullptr;        // [N] position of each row in sig
     int4* ranges = nullptr;           // [N/128 + 1] per-tile column range (L, H, C, segments)
 
+    // Gram (tensor-core) form
+    int kpad = 0;                     // n rounded up to 64 (one 128-byte swizzle atom)
+    void* S16 = nullptr;              // [N][kpad] centred rows in mean-bucketed order (FP16/BF16)
+    void* A16 = nullptr;              // [N][kpad] rows of the current list, packed
+    float* colmu = nullptr;           // [N] sqrt(n) mu in mean-bucketed order
+    float* colc = nullptr;            // [N] c in mean-bucketed order
+    float* rowmu = nullptr;           // [N] sqrt(n) mu (orig order)
+    float* rowc = nullptr;            // [N] c
+    float* rowsc = nullptr;           // [N] sqrt(c) rounded up
+    float* alpha = nullptr;           // [N] error bound terms
+    float* gam = nullptr;
+    float* q2 = nullptr;
+    double* ex64 = nullptr;           // [N] exact FP64 nn^2 of the rescored rows
+    CUtensorMap mapS_A, mapS_B, mapP_A;
+
     double beta_host[dd::kMaxAlphabet];
 
     // tracing (dd_plan_set_profiling)
@@ -192,6 +256,17 @@ cudaError_t launch_profile(dd_plan_s* p, const float* T, const int32_t* rows, in
                            cudaStream_t s);
 // scan_fp32.cu
 cudaError_t launch_scan_fp32(const ScanArgs& a, int grid, cudaStream_t s);
+// scan_tc.cu
+size_t tc_smem_bytes(int kpad);
+int tc_stages(int kpad);
+bool tc_supported(int n);
+cudaError_t tc_make_maps(dd_plan_s* p);
+cudaError_t launch_tc_prep(dd_plan_s* p, cudaStream_t s);
+cudaError_t launch_gather_rows(dd_plan_s* p, ListRef L, cudaStream_t s);
+cudaError_t launch_scan_tc(dd_plan_s* p, const TcArgs& a, bool a_packed, cudaStream_t s);
+// rescore.cu
+cudaError_t launch_rescore(dd_plan_s* p, ListRef cand, TcBound bound, int work_slot, dd_result_t* out_dev,
+                           cudaStream_t s);
 // api.cu: event pair around a distance launch when profiling (start=true before, false after)
 void prof_mark(dd_plan_s* p, cudaStream_t s, bool start);
 int scan_fp32_grid(const dd_plan_s* p);

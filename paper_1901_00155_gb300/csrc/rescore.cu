@@ -1,0 +1,166 @@
+// rescore.cu -- exact FP64 nearest-neighbour distances of the rows the
+// tensor-core bound could not rule out, and the final argmax (Algorithm 4
+// returns sqrt(dist_bsf); Section 2.1: the discord maximises the nearest
+// non-self-match distance, ties -> smallest index).
+//
+// A candidate row i has an upper bound ub_i >= nn_i^2 from its Gram-form scan.
+// Its nearest neighbour j* satisfies n (mu_i - mu_j*)^2 <= d^2(i, j*) <= ub_i,
+// so scanning the mean-bucketed order over the bins within sqrt(ub_i / n) of
+// mu_i, in FP64 direct differences on t^ (Eq. 1 squared), gives nn_i^2
+// exactly (to FP64 rounding).  Work items = (candidate, chunk of that range),
+// handed out dynamically; chunk minima meet in an atomicMin on the double's
+// bits (non-negative doubles order like their bit patterns).
+#include "dd_internal.cuh"
+
+namespace dd {
+namespace {
+
+constexpr int kChunk = 2048;
+
+__device__ __forceinline__ void lb_range(float R, int i, int n, int N, const double* stats, const int32_t* mubin,
+                                         const int32_t* binstart, int& L, int& H) {
+    const double w = stats[7];
+    if (!(R < 1e30f) || !(w > 0.0)) {
+        L = 0;
+        H = N;
+        return;
+    }
+    const double h = sqrt((double)R / (double)n) * (1.0 + 1e-4) + 1e-12;
+    const double kb = ceil(h / w) + 1.0;
+    const int k = kb > (double)kMuBins ? kMuBins : (int)kb;
+    const int b = mubin[i];
+    L = binstart[b - k < 0 ? 0 : b - k];
+    H = binstart[b + k + 1 > kMuBins ? kMuBins : b + k + 1];
+}
+
+__global__ void __launch_bounds__(256) k_rescore64(ListRef cand, TcBound bound, const uint32_t* __restrict__ rmin,
+                                                   const int32_t* __restrict__ sig,
+                                                   const int32_t* __restrict__ mubin,
+                                                   const int32_t* __restrict__ binstart, const double* stats,
+                                                   const double* __restrict__ t64, int n, int N,
+                                                   unsigned long long* __restrict__ ex64, Ctrl* ctrl, int slot) {
+    __shared__ int sh_item;
+    __shared__ double red[8];
+    if (ctrl->nonfinite || ctrl->degenerate) return;
+    const int cnt = *cand.cnt_dev;
+    const int off = cand.off_dev ? *cand.off_dev : 0;
+    const int nchunk = (N + kChunk - 1) / kChunk;
+    const long long items = (long long)cnt * nchunk;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) sh_item = atomicAdd(&ctrl->work[slot], 1);
+        __syncthreads();
+        const int item = sh_item;
+        if (item >= items) break;
+        const int r = item / nchunk, c = item % nchunk;
+        const int i = cand.base[off + r];
+        const float D = __uint_as_float(rmin[i]);
+        int L, H;
+        lb_range(row_ub(bound, i, D), i, n, N, stats, mubin, binstart, L, H);
+        const int a0 = L + c * kChunk;
+        if (a0 >= H) continue;
+        const int a1 = min(H, a0 + kChunk);
+        double best = INFINITY;
+        const double* x = t64 + i;
+        for (int p = a0 + threadIdx.x; p < a1; p += blockDim.x) {
+            const int j = sig[p];
+            const int d = i - j;
+            if (d < n && d > -n) continue;
+            const double* y = t64 + j;
+            double s = 0.0;
+            for (int k = 0; k < n; k++) {
+                const double df = x[k] - y[k];
+                s = fma(df, df, s);
+            }
+            best = fmin(best, s);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) best = fmin(best, __shfl_xor_sync(0xffffffffu, best, o));
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = best;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double b = red[0];
+            for (int w = 1; w < (int)(blockDim.x >> 5); w++) b = fmin(b, red[w]);
+            if (b < INFINITY) atomicMin(ex64 + r, (unsigned long long)__double_as_longlong(b));
+        }
+    }
+}
+
+// best64 = max over candidates of the exact value; then the smallest index
+// attaining it.
+__global__ void __launch_bounds__(256) k_best64(ListRef cand, const unsigned long long* __restrict__ ex64, Ctrl* ctrl) {
+    const int cnt = *cand.cnt_dev;
+    unsigned long long m = 0;
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < cnt; r += gridDim.x * blockDim.x) {
+        const unsigned long long v = ex64[r];
+        m = v > m ? v : m;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long u = __shfl_xor_sync(0xffffffffu, m, o);
+        m = u > m ? u : m;
+    }
+    if ((threadIdx.x & 31) == 0 && m) atomicMax(&ctrl->best64, m);
+    if (blockIdx.x == 0 && threadIdx.x == 0) ctrl->ncandidates = cnt;
+}
+
+__global__ void __launch_bounds__(256) k_pick64(ListRef cand, const unsigned long long* __restrict__ ex64, Ctrl* ctrl) {
+    const int cnt = *cand.cnt_dev;
+    const int off = cand.off_dev ? *cand.off_dev : 0;
+    const unsigned long long best = ctrl->best64;
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < cnt; r += gridDim.x * blockDim.x)
+        if (ex64[r] == best) atomicMin(&ctrl->best_idx, cand.base[off + r]);
+}
+
+__global__ void k_finalize_tc(const Ctrl* ctrl, dd_result_t* out) {
+    if (threadIdx.x != 0) return;
+    dd_result_t r;
+    r.exact = 1;
+    r.computed_pairs = (int64_t)ctrl->pairs;
+    r.candidates = ctrl->ncandidates;
+    if (ctrl->nonfinite) {
+        r.status = DD_ENONFINITE;
+        r.index = -1;
+        r.nn_distance = 0.0;
+    } else if (ctrl->degenerate) {
+        r.status = DD_OK;
+        r.index = 0;
+        r.nn_distance = 0.0;
+    } else if (ctrl->err) {
+        r.status = ctrl->err;
+        r.index = -1;
+        r.nn_distance = 0.0;
+    } else if (ctrl->best_idx == 0x7fffffff) {
+        r.status = DD_ECUDA;
+        r.index = -1;
+        r.nn_distance = 0.0;
+    } else {
+        r.status = DD_OK;
+        r.index = ctrl->best_idx;
+        r.nn_distance = sqrt(__longlong_as_double((long long)ctrl->best64));
+    }
+    *out = r;
+}
+
+__global__ void k_init_best(Ctrl* ctrl) {
+    if (threadIdx.x == 0) ctrl->best_idx = 0x7fffffff;
+}
+
+}  // namespace
+
+cudaError_t launch_rescore(dd_plan_s* p, ListRef cand, TcBound bound, int work_slot, dd_result_t* out_dev,
+                           cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(p->ex64, 0x7f, sizeof(double) * p->N, s);
+    if (e != cudaSuccess) return e;
+    k_init_best<<<1, 32, 0, s>>>(p->ctrl);
+    k_rescore64<<<2 * p->sm_count, 256, 0, s>>>(cand, bound, p->rmin, p->sig, p->mubin, p->binstart, p->stats, p->t64,
+                                                 p->n, (int)p->N, reinterpret_cast<unsigned long long*>(p->ex64),
+                                                 p->ctrl, work_slot);
+    k_best64<<<p->sm_count, 256, 0, s>>>(cand, reinterpret_cast<const unsigned long long*>(p->ex64), p->ctrl);
+    k_pick64<<<p->sm_count, 256, 0, s>>>(cand, reinterpret_cast<const unsigned long long*>(p->ex64), p->ctrl);
+    k_finalize_tc<<<1, 32, 0, s>>>(p->ctrl, out_dev);
+    p->launches += 5;
+    return cudaGetLastError();
+}
+
+}  // namespace dd

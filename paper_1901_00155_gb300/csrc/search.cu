@@ -13,16 +13,19 @@ namespace {
 
 __global__ void k_set_int(int* p, int v) { *p = v; }
 
-__device__ __forceinline__ bool is_alive(uint32_t rbits, uint32_t bsf_bits) {
-    // Row is alive unless one of its distances fell strictly below the
-    // best-so-far; non-negative floats order like their bit patterns.
-    return rbits >= bsf_bits;
+// A row is alive unless one of its distances is proven strictly below the
+// best-so-far: FP32 form D < bsf (Algorithms 3/4); Gram form D + F_i(D) < bsf,
+// bsf being a proven lower bound there.  Non-negative floats order like their
+// bit patterns.
+__device__ __forceinline__ bool is_alive(const TcBound& b, int i, uint32_t rbits, uint32_t bsf_bits) {
+    if (!b.on) return rbits >= bsf_bits;
+    return !(row_ub(b, i, __uint_as_float(rbits)) < __uint_as_float(bsf_bits));
 }
 
 // Compaction pass 1: predicate per list entry + per-block counts.
 // pred 0: alive against the best-so-far; pred 1: alive and rmin >= top-k
 // threshold; pred 2: member of Cand.
-__global__ void __launch_bounds__(256) k_compact_flags(ListRef in, const uint32_t* __restrict__ rmin,
+__global__ void __launch_bounds__(256) k_compact_flags(ListRef in, const uint32_t* __restrict__ rmin, TcBound tb,
                                                        const Ctrl* ctrl, int pred, const int32_t* __restrict__ code,
                                                        const int32_t* __restrict__ hist, int phase1_max,
                                                        uint8_t* __restrict__ flag, int* __restrict__ blk) {
@@ -46,7 +49,7 @@ __global__ void __launch_bounds__(256) k_compact_flags(ListRef in, const uint32_
                 keep = hist[code[i]] == ctrl->fmin && ctrl->ncand <= phase1_max;
             } else {
                 const uint32_t b = rmin[i];
-                keep = is_alive(b, bsf) && b >= thr;
+                keep = is_alive(tb, i, b, bsf) && b >= thr;
             }
             flag[r] = keep;
             local += keep;
@@ -119,7 +122,8 @@ __global__ void __launch_bounds__(256) k_compact_scatter(ListRef in, const uint8
 
 // Top-k radix select, pass 1: histogram of (float bits >> 19) of the rows'
 // running minima (alive rows only).
-__global__ void __launch_bounds__(256) k_topk_hist(ListRef in, const uint32_t* __restrict__ rmin, Ctrl* ctrl) {
+__global__ void __launch_bounds__(256) k_topk_hist(ListRef in, const uint32_t* __restrict__ rmin, TcBound tb,
+                                                   Ctrl* ctrl) {
     __shared__ int h[kTopkBins];
     for (int b = threadIdx.x; b < kTopkBins; b += blockDim.x) h[b] = 0;
     __syncthreads();
@@ -127,8 +131,9 @@ __global__ void __launch_bounds__(256) k_topk_hist(ListRef in, const uint32_t* _
     const int off = in.off_dev ? *in.off_dev : 0;
     const uint32_t bsf = ctrl->bsf;
     for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < cnt; r += gridDim.x * blockDim.x) {
-        const uint32_t b = rmin[in.base[off + r]];
-        if (is_alive(b, bsf)) atomicAdd(&h[b >> 19], 1);
+        const int i = in.base[off + r];
+        const uint32_t b = rmin[i];
+        if (is_alive(tb, i, b, bsf)) atomicAdd(&h[b >> 19], 1);
     }
     __syncthreads();
     for (int b = threadIdx.x; b < kTopkBins; b += blockDim.x)
@@ -149,7 +154,9 @@ __global__ void k_topk_thr(Ctrl* ctrl, int k) {
 
 // Rows alive after the last wave have scanned every column: their running
 // minimum is their nearest-neighbour distance.  Best-so-far and argmax key.
-__global__ void __launch_bounds__(256) k_complete(ListRef in, const uint32_t* __restrict__ rmin, Ctrl* ctrl) {
+// (Gram form: the best-so-far takes the row's proven lower bound D - F_i(D).)
+__global__ void __launch_bounds__(256) k_complete(ListRef in, const uint32_t* __restrict__ rmin, TcBound tb,
+                                                  Ctrl* ctrl) {
     const int cnt = *in.cnt_dev;
     const int off = in.off_dev ? *in.off_dev : 0;
     const uint32_t bsf = ctrl->bsf;
@@ -159,10 +166,11 @@ __global__ void __launch_bounds__(256) k_complete(ListRef in, const uint32_t* __
     for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < cnt; r += gridDim.x * blockDim.x) {
         const int i = in.base[off + r];
         const uint32_t b = rmin[i];
-        if (!is_alive(b, bsf)) continue;
+        if (!is_alive(tb, i, b, bsf)) continue;
         const unsigned long long key = ((unsigned long long)b << 32) | (unsigned long long)(0xffffffffu - (uint32_t)i);
         best = key > best ? key : best;
-        bmax = b > bmax ? b : bmax;
+        const uint32_t lbits = tb.on ? __float_as_uint(row_lb(tb, i, __uint_as_float(b))) : b;
+        bmax = lbits > bmax ? lbits : bmax;
         done++;
     }
 #pragma unroll
@@ -189,8 +197,9 @@ __global__ void __launch_bounds__(128) k_tile_ranges(ListRef L, int kind, int K,
                                                      const int32_t* __restrict__ sigpos,
                                                      const int32_t* __restrict__ mubin,
                                                      const int32_t* __restrict__ binstart,
-                                                     const uint32_t* __restrict__ rmin, const double* stats, int n,
-                                                     int N, int4* __restrict__ ranges, int* smax) {
+                                                     const uint32_t* __restrict__ rmin, TcBound tb,
+                                                     const double* stats, int n, int N, int4* __restrict__ ranges,
+                                                     int* smax) {
     __shared__ int red[4][4];
     const int cnt = *L.cnt_dev;
     const int off = L.off_dev ? *L.off_dev : 0;
@@ -206,7 +215,7 @@ __global__ void __launch_bounds__(128) k_tile_ranges(ListRef L, int kind, int K,
             lo = q - K;
             hi = q + 1 + K;
         } else {
-            const float R = __uint_as_float(rmin[i]);
+            const float R = row_ub(tb, i, __uint_as_float(rmin[i]));
             const double w = stats[7];
             if (!(R < 1e30f) || !(w > 0.0)) {
                 lo = 0;
@@ -302,9 +311,25 @@ struct Seq {
     int cnt_slot = 0;
     int smax_slot = 0;
     cudaError_t err = cudaSuccess;
+    bool tc = false;
+    TcBound tb{};
+
+    Seq(dd_plan_s* plan, cudaStream_t stream) : p(plan), s(stream) {
+        tc = p->opt.precision != DD_FP32;
+        if (tc) {
+            tb.alpha = p->alpha;
+            tb.gam = p->gam;
+            tb.q2 = p->q2;
+            tb.beta = 12.0f * 5.9604644775390625e-08f;  // 2 x 6 u32 (safety factor 2)
+            tb.on = 1;
+        }
+    }
 
     void check() {
         if (err == cudaSuccess) err = cudaGetLastError();
+    }
+    void keep(cudaError_t e) {
+        if (err == cudaSuccess) err = e;
     }
     int* cnt_ptr(int slot) { return &p->ctrl->cnt[slot]; }
 
@@ -315,38 +340,77 @@ struct Seq {
         return ListRef{base, nullptr, cnt_ptr(slot)};
     }
 
-    void scan(ListRef rows, ColSpec col, int abandon, const int* smax = nullptr) {
-        ScanArgs a{};
-        a.t32 = p->t32;
-        a.N = (int)p->N;
-        a.n = p->n;
-        a.rows = rows;
-        a.order = p->order;
-        a.pos_of = p->pos_of;
-        a.code = p->code;
-        a.hist = p->hist;
-        a.word_start = p->word_start;
-        a.col = col;
-        a.sig = p->sig;
-        a.ranges = p->ranges;
-        a.smax = smax;
-        a.seg_cols = kSegCols;
-        a.rmin = p->rmin;
-        a.ctrl_ro = p->ctrl;
-        a.ctrl = p->ctrl;
-        a.abandon = abandon;
-        a.work_slot = work_slot++;
-        a.min_seg_tiles = 4;
-        const int grid = scan_fp32_grid(p);
-        a.target_items = grid * 2;
+    // One wave of distance tiles for the rows of `rows`.  a_direct: the list
+    // is the mean-bucketed order itself (its operand rows need no packing).
+    void scan(ListRef rows, ColSpec col, int abandon, const int* smax = nullptr, bool a_direct = false) {
+        const int slot = work_slot++;
         if (work_slot > kMaxLaunchSlots) {
             err = cudaErrorInvalidValue;
             return;
         }
+        if (!tc) {
+            ScanArgs a{};
+            a.t32 = p->t32;
+            a.N = (int)p->N;
+            a.n = p->n;
+            a.rows = rows;
+            a.order = p->order;
+            a.pos_of = p->pos_of;
+            a.code = p->code;
+            a.hist = p->hist;
+            a.word_start = p->word_start;
+            a.col = col;
+            a.sig = p->sig;
+            a.ranges = p->ranges;
+            a.smax = smax;
+            a.seg_cols = kSegCols;
+            a.rmin = p->rmin;
+            a.ctrl_ro = p->ctrl;
+            a.ctrl = p->ctrl;
+            a.abandon = abandon;
+            a.work_slot = slot;
+            a.min_seg_tiles = 4;
+            const int grid = scan_fp32_grid(p);
+            a.target_items = grid * 2;
+            prof_mark(p, s, true);
+            keep(launch_scan_fp32(a, grid, s));
+            prof_mark(p, s, false);
+            p->launches++;
+            return;
+        }
+        if (col.mode == 1) return;  // the same-word wave runs in the FP32 form only
+        if (!a_direct) keep(launch_gather_rows(p, rows, s));
+        TcArgs t{};
+        t.N = (int)p->N;
+        t.n = p->n;
+        t.nka = p->kpad / 64;
+        t.stages = tc_stages(p->kpad);
+        t.seg_cols = kSegCols;
+        t.mode = col.mode == 2 ? 2 : 0;
+        t.rows = rows;
+        t.a_direct = a_direct ? 1 : 0;
+        t.a_row0 = 0;
+        t.sig = p->sig;
+        t.colmu = p->colmu;
+        t.colc = p->colc;
+        t.rowmu = p->rowmu;
+        t.rowc = p->rowc;
+        t.alpha = p->alpha;
+        t.gam = p->gam;
+        t.q2 = p->q2;
+        t.beta = tb.beta;
+        t.ranges = p->ranges;
+        t.smax = smax;
+        t.rmin = p->rmin;
+        t.ctrl = p->ctrl;
+        t.stats = p->stats;
+        t.abandon = abandon;
+        t.work_slot = slot;
+        const uint32_t ty = p->opt.precision == DD_TC_BF16 ? 1u : 0u;
+        t.idesc = (1u << 4) | (ty << 7) | (ty << 10) | ((uint32_t)(256 >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
         prof_mark(p, s, true);
-        cudaError_t e = launch_scan_fp32(a, grid, s);
+        keep(launch_scan_tc(p, t, !a_direct, s));
         prof_mark(p, s, false);
-        if (err == cudaSuccess) err = e;
         p->launches++;
     }
 
@@ -358,7 +422,7 @@ struct Seq {
             return nullptr;
         }
         const int tiles = (int)((p->N + 127) / 128);
-        k_tile_ranges<<<tiles, 128, 0, s>>>(rows, kind, K, kSegCols, p->sigpos, p->mubin, p->binstart, p->rmin,
+        k_tile_ranges<<<tiles, 128, 0, s>>>(rows, kind, K, kSegCols, p->sigpos, p->mubin, p->binstart, p->rmin, tb,
                                             p->stats, p->n, (int)p->N, p->ranges, &p->ctrl->smax[slot]);
         p->launches++;
         check();
@@ -373,7 +437,7 @@ struct Seq {
             err = cudaErrorInvalidValue;
             return in;
         }
-        k_compact_flags<<<nblk, 256, 0, s>>>(in, p->rmin, p->ctrl, pred, p->code, p->hist, p->opt.phase1_max,
+        k_compact_flags<<<nblk, 256, 0, s>>>(in, p->rmin, tb, p->ctrl, pred, p->code, p->hist, p->opt.phase1_max,
                                              p->flag, p->blk);
         k_compact_scan<<<1, 1024, 0, s>>>(p->blk, nblk, cnt_ptr(slot));
         k_compact_scatter<<<nblk, 256, 0, s>>>(in, p->flag, p->blk, out);
@@ -384,13 +448,20 @@ struct Seq {
 
     void complete(ListRef in) {
         const int g = (int)((p->N + 1023) / 1024);
-        k_complete<<<g < 1024 ? g : 1024, 256, 0, s>>>(in, p->rmin, p->ctrl);
+        k_complete<<<g < 1024 ? g : 1024, 256, 0, s>>>(in, p->rmin, tb, p->ctrl);
         p->launches++;
         check();
     }
 
+    void topk(ListRef in, int k) {
+        k_topk_hist<<<2 * p->sm_count, 256, 0, s>>>(in, p->rmin, tb, p->ctrl);
+        k_topk_thr<<<1, 32, 0, s>>>(p->ctrl, k);
+        p->launches += 2;
+        check();
+    }
+
     // Full scan of each row of `in`: every column whose lower bound
-    // n (mu_i - mu_j)^2 is below the row's running minimum, nearest mean
+    // n (mu_i - mu_j)^2 can still undercut the row's upper bound, nearest mean
     // first, abandoning against the best-so-far; survivors complete.
     void full(ListRef in) {
         const int* sm = ranges(in, 1, 0);
@@ -410,19 +481,19 @@ cudaError_t launch_search(dd_plan_s* p, const float* T, dd_result_t* out_dev, cu
     e = launch_prep(p, T, s);
     if (e != cudaSuccess) return e;
 
-    Seq q{p, s};
+    Seq q(p, s);
+    if (q.tc) q.keep(launch_tc_prep(p, s));
     const dd_options_t& o = p->opt;
+    ListRef all = q.constant_list(p->sig, (int)p->N);  // every row, mean-bucketed order
     if (!o.early_abandon) {
         // every row scans every column; the argmax runs over all rows
-        ListRef all = q.constant_list(p->seq_rows, (int)p->N);
-        q.scan(all, ColSpec{0, 0, (int)p->N, 0}, 0);
+        q.scan(all, ColSpec{0, 0, (int)p->N, 0}, 0, nullptr, true);
         q.complete(all);
     } else {
-        ListRef all = q.constant_list(p->sig, (int)p->N);
         // Upper bounds for every row from its nearest-mean neighbourhood.
         if (o.local_cols > 0) {
             const int* sm = q.ranges(all, 0, o.local_cols);
-            q.scan(all, ColSpec{2, 0, 0, 0}, 1, sm);
+            q.scan(all, ColSpec{2, 0, 0, 0}, 1, sm, true);
         }
         // Algorithm 3 (PotentialDiscord): the Cand rows (rarest SAX words).
         ListRef cand = q.compact(all, p->list[0], 2);
@@ -431,15 +502,13 @@ cudaError_t launch_search(dd_plan_s* p, const float* T, dd_result_t* out_dev, cu
         // largest upper bounds (the likeliest discords) next.
         ListRef alive = q.compact(all, p->list[1], 0);
         if (o.refine_k > 0) {
-            k_topk_hist<<<2 * p->sm_count, 256, 0, s>>>(alive, p->rmin, p->ctrl);
-            k_topk_thr<<<1, 32, 0, s>>>(p->ctrl, o.refine_k);
-            p->launches += 2;
+            q.topk(alive, o.refine_k);
             ListRef top = q.compact(alive, p->list[2], 1);
             q.full(top);
         }
         // Algorithm 4 (RefineDiscord) over the remaining rows: rows sharing the
         // SAX word first (Index_Word), then every column the bound allows.
-        if (o.word_cols > 0) {
+        if (o.word_cols > 0 && !q.tc) {
             ListRef words = q.constant_list(p->order, (int)p->N);
             ListRef wl = q.compact(words, p->list[3], 0);
             q.scan(wl, ColSpec{1, 0, 0, o.word_cols}, 1);
@@ -447,8 +516,14 @@ cudaError_t launch_search(dd_plan_s* p, const float* T, dd_result_t* out_dev, cu
         ListRef rest = q.compact(alive, p->list[2], 0);
         q.full(rest);
     }
-    k_finalize<<<1, 32, 0, s>>>(p->ctrl, out_dev);
-    p->launches++;
+    if (q.tc) {
+        // every row the bound cannot rule out, rescored exactly in FP64
+        ListRef cands = q.compact(all, p->list[3], 0);
+        q.keep(launch_rescore(p, cands, q.tb, q.work_slot++, out_dev, s));
+    } else {
+        k_finalize<<<1, 32, 0, s>>>(p->ctrl, out_dev);
+        p->launches++;
+    }
     q.check();
     return q.err;
 }
@@ -462,7 +537,8 @@ cudaError_t launch_profile(dd_plan_s* p, const float* T, const int32_t* rows, in
     if (e != cudaSuccess) return e;
     e = launch_prep(p, T, s);
     if (e != cudaSuccess) return e;
-    Seq q{p, s};
+    Seq q(p, s);
+    if (q.tc) q.keep(launch_tc_prep(p, s));
     const int32_t* r = rows ? rows : p->seq_rows;
     const int c = rows ? count : (int)p->N;
     ListRef L = q.constant_list(r, c);
