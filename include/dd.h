@@ -206,6 +206,27 @@ typedef struct {
 DD_API dd_status_t dd_plan_set_profiling(dd_plan_t plan, int32_t enable);
 DD_API dd_status_t dd_plan_get_profile(dd_plan_t plan, dd_profile_t* out);
 
+/* Exhaustive nearest-neighbour profile without any device allocation.
+ * The paper has no counterpart to this entry point; it exists for callers
+ * that may not allocate device memory at the time of the call -- code running
+ * inside a device-memory budget that is already fully handed out to another
+ * allocator, or latency-critical loops where an allocation would synchronise
+ * the device.  It computes what dd_nn_profile computes in the FP32 form
+ * (nn2_dev[i] = squared distance from subsequence i to its nearest non-self
+ * match, i in [0, N)), needs no plan, and uses as scratch one fixed array of
+ * about 1 MiB inside the library that every GPU loading the library keeps
+ * until the process exits.  The caller passes T_dev (m float32 values) and
+ * nn2_dev (N floats), both device memory.  Work is enqueued on `stream`.
+ *   - m must be at most 262,144; larger series return DD_EINVAL (as do
+ *     n < 1, N < 2n and null pointers).
+ *   - All calls on a device share the scratch array, and it keeps the last
+ *     call's contents: calls whose work overlaps on the GPU (other streams or
+ *     host threads) race.  Order them on one stream.
+ *   - The first call on a device looks up the scratch address with that
+ *     device current; make it before any stream capture.
+ *   - A series holding NaN or Inf yields NaN in every output element. */
+DD_API dd_status_t dd_nn_profile_static(const float* T_dev, int64_t m, int32_t n, float* nn2_dev, void* stream);
+
 /* Static text for a status code. */
 DD_API const char* dd_status_string(dd_status_t status);
 

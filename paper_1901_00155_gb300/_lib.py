@@ -66,6 +66,8 @@ SIGNATURES = {
     "dd_status_string": ([ctypes.c_int], ctypes.c_char_p),
     "dd_plan_set_profiling": ([ctypes.c_void_p, ctypes.c_int32], ctypes.c_int),
     "dd_plan_get_profile": ([ctypes.c_void_p, ctypes.POINTER(Profile)], ctypes.c_int),
+    "dd_nn_profile_static": ([ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p],
+                             ctypes.c_int),
 }
 
 
