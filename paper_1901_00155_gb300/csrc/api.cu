@@ -66,7 +66,7 @@ size_t carve(dd_plan_s* p, char* base) {
     const int nh = (int)((N + dd::kHistRows - 1) / dd::kHistRows);
     const int nblk = (int)((N + dd::kCompactRows - 1) / dd::kCompactRows);
     p->ctrl = c.take<Ctrl>(1);
-    p->stats = c.take<double>(8);
+    p->stats = c.take<double>(16);
     p->part = c.take<double>(3 * dd::kStatBlocks);
     p->beta = c.take<double>(dd::kMaxAlphabet);
     p->Tbuf = c.take<float>(m + kPad);

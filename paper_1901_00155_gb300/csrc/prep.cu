@@ -129,6 +129,14 @@ __global__ void __launch_bounds__(256) k_stats_sigma(const double* part, int nb,
         double a = fmax(fabs(stats[4] - mu), fabs(stats[5] - mu));
         stats[2] = sigma > 0.0 ? a / sigma : 0.0;
         if (!(sigma > 0.0)) ctrl->degenerate = 1;
+        stats[8] = sigma > 0.0 ? 1.0 / sigma : 0.0;
+        // mean-bin geometry: bins of width w over [min t^, max t^]
+        const double lo = sigma > 0.0 ? (stats[5] - mu) / sigma : 0.0;
+        const double hi = sigma > 0.0 ? (stats[4] - mu) / sigma : 0.0;
+        const double w = (hi - lo) / (double)kMuBins;
+        stats[6] = lo;
+        stats[7] = w;
+        stats[9] = w > 0.0 ? 1.0 / w : 0.0;
     }
 }
 
@@ -138,14 +146,14 @@ __global__ void __launch_bounds__(1024) k_norm_blocks(const float* __restrict__ 
                                                       const double* stats, double* __restrict__ t64,
                                                       float* __restrict__ t32, double* bsum, int nscan) {
     __shared__ double sh[32];
-    const double mu = stats[0], sigma = stats[1];
+    const double mu = stats[0], inv_sigma = stats[8];
     const int64_t base = (int64_t)blockIdx.x * kScanElems + 4 * threadIdx.x;
     double s1 = 0.0, s2 = 0.0;
 #pragma unroll
     for (int q = 0; q < 4; q++) {
         int64_t i = base + q;
         if (i < m) {
-            double v = sigma > 0.0 ? ((double)T[i] - mu) / sigma : 0.0;
+            double v = ((double)T[i] - mu) * inv_sigma;
             t64[i] = v;
             t32[i] = (float)v;
             s1 += v;
@@ -268,13 +276,13 @@ __global__ void __launch_bounds__(1024) k_norm_prefix(const double* __restrict__
 
 // ---- Eq. 5 rows: mean and centred sum of squares from the prefix sums -------
 __global__ void __launch_bounds__(256) k_window_stats(const double* __restrict__ P1, const double* __restrict__ P2,
-                                                      int64_t N, int n, double* __restrict__ mu_w,
+                                                      int64_t N, int n, double inv_n, double* __restrict__ mu_w,
                                                       double* __restrict__ c_w) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     const double S1 = P1[i + n] - P1[i];
     const double S2 = P2[i + n] - P2[i];
-    const double mu = S1 / (double)n;
+    const double mu = S1 * inv_n;
     double c = S2 - S1 * mu;
     // Within the rounding of the prefix sums a constant row has c == 0.
     const double noise = 64.0 * 1.1102230246251565e-16 * (fabs(P2[i + n]) + fabs(P2[i]));
@@ -284,27 +292,34 @@ __global__ void __launch_bounds__(256) k_window_stats(const double* __restrict__
 }
 
 // ---- Eq. 3 (PAA) + Eq. 4 (SAX letters) + Eq. 9 (word code) -----------------
-// Segment s of a row covers [floor(s n / w), floor((s+1) n / w)).
+// Segment s of a row covers [floor(s n / w), floor((s+1) n / w)), length L_s.
+// The letter test beta <= (seg_sum / L_s - mu) / sd is evaluated as
+// seg_sum - mu L_s >= beta L_s sd (sd > 0, L_s > 0): the same decision
+// without an FP64 division per segment.
 __global__ void __launch_bounds__(256) k_sax(const double* __restrict__ P1, const double* __restrict__ mu_w,
-                                             const double* __restrict__ c_w, int64_t N, int n, int w, int A,
-                                             int paa_mode, const double* __restrict__ beta,
+                                             const double* __restrict__ c_w, int64_t N, int n, double inv_n, int w,
+                                             int A, int paa_mode, const double* __restrict__ beta,
                                              int32_t* __restrict__ code) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     const double mu = mu_w[i];
     const double c = c_w[i];
-    const double sd = sqrt(c / (double)n);
+    const double sd = sqrt(c * inv_n);
     int32_t h = 0;
     for (int s = 0; s < w; s++) {
         const int a = (int)(((int64_t)s * n) / w), b = (int)(((int64_t)(s + 1) * n) / w);
-        const double seg = (P1[i + b] - P1[i + a]) / (double)(b - a);
-        double v;
-        if (paa_mode == 0)
-            v = (c > 0.0) ? (seg - mu) / sd : 0.0;
-        else
-            v = seg;
+        const double len = (double)(b - a);
+        const double seg = P1[i + b] - P1[i + a];
+        double lhs, scale;
+        if (paa_mode == 0) {
+            lhs = (c > 0.0) ? seg - mu * len : 0.0;
+            scale = (c > 0.0) ? len * sd : 1.0;
+        } else {
+            lhs = seg;
+            scale = len;
+        }
         int letter = 0;
-        while (letter < A - 1 && v >= beta[letter]) letter++;
+        while (letter < A - 1 && lhs >= beta[letter] * scale) letter++;
         h = h * A + letter;
     }
     code[i] = h;
@@ -449,58 +464,63 @@ __global__ void k_word_scatter(const int32_t* __restrict__ code, int64_t N, int 
 // rows whose distance to row i can be below R lie in the bins within
 // sqrt(R / n) of mu_i: a contiguous range of this order.
 __global__ void __launch_bounds__(256) k_mu_bins(const double* __restrict__ mu_w, int64_t N, const double* stats,
-                                                 int32_t* __restrict__ bin, double* stats_out) {
-    const double mu = stats[0], sigma = stats[1];
-    const double lo = sigma > 0.0 ? (stats[5] - mu) / sigma : 0.0;
-    const double hi = sigma > 0.0 ? (stats[4] - mu) / sigma : 0.0;
-    const double w = (hi - lo) / (double)kMuBins;
-    const double invw = w > 0.0 ? 1.0 / w : 0.0;
+                                                 int32_t* __restrict__ bin) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i == 0) {
-        stats_out[6] = lo;
-        stats_out[7] = w;
-    }
     if (i >= N) return;
-    double b = floor((mu_w[i] - lo) * invw);
-    int bi = b < 0.0 ? 0 : (b >= (double)kMuBins ? kMuBins - 1 : (int)b);
-    bin[i] = bi;
+    const double b = floor((mu_w[i] - stats[6]) * stats[9]);
+    bin[i] = b < 0.0 ? 0 : (b >= (double)kMuBins ? kMuBins - 1 : (int)b);
 }
 
-// Bin order plan: bin offsets (exclusive scan in bin order) and each block's
-// base offset per bin (column scan of the block counts).  One block.
-__global__ void __launch_bounds__(1024) k_bin_plan(const int32_t* __restrict__ hist, int D, int nblk,
-                                                   int32_t* __restrict__ blockcnt, int32_t* __restrict__ binstart) {
+// Bin order plan, part 1: bin offsets (exclusive scan of the histogram in bin
+// order).  One block; each thread a run of consecutive bins.
+__global__ void __launch_bounds__(1024) k_bin_scan(const int32_t* __restrict__ hist, int D,
+                                                   int32_t* __restrict__ binstart) {
     __shared__ int32_t part[1024];
     const int per = (D + 1023) / 1024;
     const int lo = threadIdx.x * per, hi = min(D, lo + per);
     int s = 0;
     for (int h = lo; h < hi; h++) s += hist[h];
-    part[threadIdx.x] = s;
+    // block exclusive scan of the per-thread sums (warp scans + one pass over warp totals)
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int incl = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += u;
+    }
+    if (lane == 31) part[wid] = incl;
     __syncthreads();
-    if (threadIdx.x == 0) {
-        int run = 0;
-        for (int t = 0; t < 1024; t++) {
-            int x = part[t];
-            part[t] = run;
-            run += x;
+    if (wid == 0) {
+        const int v = part[lane];
+        int c = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int u = __shfl_up_sync(0xffffffffu, c, o);
+            if (lane >= o) c += u;
         }
-        binstart[D] = run;
+        part[lane] = c - v;
+        if (lane == 31) binstart[D] = c;
     }
     __syncthreads();
-    int run = part[threadIdx.x];
+    int run = part[wid] + incl - s;
     for (int h = lo; h < hi; h++) {
         binstart[h] = run;
         run += hist[h];
     }
-    __syncthreads();
-    for (int h = threadIdx.x; h < D; h += blockDim.x) {
-        int r = binstart[h];
-        for (int b = 0; b < nblk; b++) {
-            int64_t ix = (int64_t)b * D + h;
-            int c = blockcnt[ix];
-            blockcnt[ix] = r;
-            r += c;
-        }
+}
+
+// Part 2: each block's base offset per bin (column scan of the block counts),
+// one thread per bin.
+__global__ void __launch_bounds__(256) k_bin_bases(int D, int nblk, const int32_t* __restrict__ binstart,
+                                                   int32_t* __restrict__ blockcnt) {
+    const int h = blockIdx.x * blockDim.x + threadIdx.x;
+    if (h >= D) return;
+    int r = binstart[h];
+    for (int b = 0; b < nblk; b++) {
+        const int64_t ix = (int64_t)b * D + h;
+        const int c = blockcnt[ix];
+        blockcnt[ix] = r;
+        r += c;
     }
 }
 
@@ -522,9 +542,9 @@ cudaError_t launch_prep(dd_plan_s* p, const float* T, cudaStream_t s) {
     k_norm_scan_totals<<<1, 1024, 0, s>>>(p->bsum, nscan);
     k_norm_prefix<<<nscan, 1024, 0, s>>>(p->t64, m, p->bsum, nscan, p->P1, p->P2);
     const int gN = (int)((N + 255) / 256);
-    k_window_stats<<<gN, 256, 0, s>>>(p->P1, p->P2, N, n, p->mu_w, p->c_w);
-    k_sax<<<gN, 256, 0, s>>>(p->P1, p->mu_w, p->c_w, N, n, p->opt.paa_w, p->opt.alphabet, p->opt.paa_mode, p->beta,
-                             p->code);
+    k_window_stats<<<gN, 256, 0, s>>>(p->P1, p->P2, N, n, 1.0 / (double)n, p->mu_w, p->c_w);
+    k_sax<<<gN, 256, 0, s>>>(p->P1, p->mu_w, p->c_w, N, n, 1.0 / (double)n, p->opt.paa_w, p->opt.alphabet,
+                             p->opt.paa_mode, p->beta, p->code);
     const int nh = (int)((N + kHistRows - 1) / kHistRows);
     cudaMemsetAsync(p->hist, 0, sizeof(int32_t) * D, s);
     k_word_hist<<<nh, 1024, sizeof(int32_t) * D, s>>>(p->code, N, D, p->hist, p->blockcnt);
@@ -535,16 +555,17 @@ cudaError_t launch_prep(dd_plan_s* p, const float* T, cudaStream_t s) {
     while (kHistRows % nw) nw--;
     k_word_scatter<<<nh, nw * 32, sizeof(int32_t) * nw * D, s>>>(p->code, N, D, p->blockcnt, p->order, p->pos_of);
     // mean-bucketed order (sig) with bin offsets
-    k_mu_bins<<<gN, 256, 0, s>>>(p->mu_w, N, p->stats, p->mubin, p->stats);
+    k_mu_bins<<<gN, 256, 0, s>>>(p->mu_w, N, p->stats, p->mubin);
     cudaMemsetAsync(p->hist_mu, 0, sizeof(int32_t) * kMuBins, s);
     k_word_hist<<<nh, 1024, sizeof(int32_t) * kMuBins, s>>>(p->mubin, N, kMuBins, p->hist_mu, p->blockcnt_mu);
-    k_bin_plan<<<1, 1024, 0, s>>>(p->hist_mu, kMuBins, nh, p->blockcnt_mu, p->binstart);
+    k_bin_scan<<<1, 1024, 0, s>>>(p->hist_mu, kMuBins, p->binstart);
+    k_bin_bases<<<(kMuBins + 255) / 256, 256, 0, s>>>(kMuBins, nh, p->binstart, p->blockcnt_mu);
     int nw2 = (48 * 1024 / 4) / kMuBins;
     if (nw2 < 1) nw2 = 1;
     while (kHistRows % nw2) nw2--;
     k_word_scatter<<<nh, nw2 * 32, sizeof(int32_t) * nw2 * kMuBins, s>>>(p->mubin, N, kMuBins, p->blockcnt_mu, p->sig,
                                                                         p->sigpos);
-    p->launches += 16;
+    p->launches += 17;
     return cudaGetLastError();
 }
 

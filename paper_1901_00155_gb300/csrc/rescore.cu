@@ -7,15 +7,18 @@
 // Its nearest neighbour j* satisfies n (mu_i - mu_j*)^2 <= d^2(i, j*) <= ub_i,
 // so scanning the mean-bucketed order over the bins within sqrt(ub_i / n) of
 // mu_i, in FP64 direct differences on t^ (Eq. 1 squared), gives nn_i^2
-// exactly (to FP64 rounding).  Work items = (candidate, chunk of that range),
-// handed out dynamically; chunk minima meet in an atomicMin on the double's
-// bits (non-negative doubles order like their bit patterns).
+// exactly (to FP64 rounding).  FP64 is slow on GB300, so each column is first
+// evaluated in FP32 (direct differences on the FP32 copy of t^); a column whose
+// FP32 value exceeds ub_i by more than that value's proven error bound cannot
+// be the nearest neighbour and is skipped.  Work items = (candidate, chunk of
+// the range), handed out dynamically; chunk minima meet in an atomicMin on the
+// double's bits (non-negative doubles order like their bit patterns).
 #include "dd_internal.cuh"
 
 namespace dd {
 namespace {
 
-constexpr int kChunk = 2048;
+constexpr int kChunk = 512;
 
 __device__ __forceinline__ void lb_range(float R, int i, int n, int N, const double* stats, const int32_t* mubin,
                                          const int32_t* binstart, int& L, int& H) {
@@ -37,11 +40,16 @@ __global__ void __launch_bounds__(256) k_rescore64(ListRef cand, TcBound bound, 
                                                    const int32_t* __restrict__ sig,
                                                    const int32_t* __restrict__ mubin,
                                                    const int32_t* __restrict__ binstart, const double* stats,
-                                                   const double* __restrict__ t64, int n, int N,
-                                                   unsigned long long* __restrict__ ex64, Ctrl* ctrl, int slot) {
+                                                   const double* __restrict__ t64, const float* __restrict__ t32,
+                                                   int n, int N, unsigned long long* __restrict__ ex64, Ctrl* ctrl,
+                                                   int slot) {
     __shared__ int sh_item;
     __shared__ double red[8];
     if (ctrl->nonfinite || ctrl->degenerate) return;
+    const float u32 = 5.9604644775390625e-08f;
+    const float nf = (float)n;
+    const float gn32 = nf * u32 / (1.f - nf * u32);
+    const float maxabs = (float)stats[2];
     const int cnt = *cand.cnt_dev;
     const int off = cand.off_dev ? *cand.off_dev : 0;
     const int nchunk = (N + kChunk - 1) / kChunk;
@@ -62,10 +70,23 @@ __global__ void __launch_bounds__(256) k_rescore64(ListRef cand, TcBound bound, 
         const int a1 = min(H, a0 + kChunk);
         double best = INFINITY;
         const double* x = t64 + i;
+        const float* x32 = t32 + i;
+        const float ub = row_ub(bound, i, D);
         for (int p = a0 + threadIdx.x; p < a1; p += blockDim.x) {
             const int j = sig[p];
             const int d = i - j;
             if (d < n && d > -n) continue;
+            // FP32 screen: |s32 - s| <= (gamma_n + 4u) s32 + 8u M sqrt(n s32) + n (6 u M)^2, M = max|t^|,
+            // u = 2^-24 (inputs rounded to FP32, differences, FMA accumulation); doubled for safety.
+            const float* y32 = t32 + j;
+            float s32 = 0.f;
+            for (int k = 0; k < n; k++) {
+                const float df = x32[k] - y32[k];
+                s32 = fmaf(df, df, s32);
+            }
+            const float margin = 2.f * ((gn32 + 4.f * u32) * s32 + 8.f * u32 * maxabs * sqrtf(nf * s32) +
+                                        nf * (6.f * u32 * maxabs) * (6.f * u32 * maxabs)) + 1e-30f;
+            if (s32 - margin > ub) continue;
             const double* y = t64 + j;
             double s = 0.0;
             for (int k = 0; k < n; k++) {
@@ -154,7 +175,7 @@ cudaError_t launch_rescore(dd_plan_s* p, ListRef cand, TcBound bound, int work_s
     if (e != cudaSuccess) return e;
     k_init_best<<<1, 32, 0, s>>>(p->ctrl);
     k_rescore64<<<2 * p->sm_count, 256, 0, s>>>(cand, bound, p->rmin, p->sig, p->mubin, p->binstart, p->stats, p->t64,
-                                                 p->n, (int)p->N, reinterpret_cast<unsigned long long*>(p->ex64),
+                                                 p->t32, p->n, (int)p->N, reinterpret_cast<unsigned long long*>(p->ex64),
                                                  p->ctrl, work_slot);
     k_best64<<<p->sm_count, 256, 0, s>>>(cand, reinterpret_cast<const unsigned long long*>(p->ex64), p->ctrl);
     k_pick64<<<p->sm_count, 256, 0, s>>>(cand, reinterpret_cast<const unsigned long long*>(p->ex64), p->ctrl);

@@ -25,6 +25,7 @@
 // DD_ETIMEOUT in the control block, drains and returns.
 #include <cuda.h>
 #include <cuda_bf16.h>
+#include <cmath>
 #include <cuda_fp16.h>
 
 #include "dd_internal.cuh"
@@ -35,21 +36,34 @@ namespace {
 constexpr int TBM = 128;
 constexpr int TBN = 256;
 constexpr int TKA = 64;  // 16-bit elements per 128-byte swizzle atom
-constexpr int kTcThreads = 192;
 constexpr int kABytesPerAtom = TBM * 128;  // 16 KB
 constexpr int kBBytesPerAtom = TBN * 128;  // 32 KB
 constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s
 
+constexpr int kStageBytes = kABytesPerAtom + kBBytesPerAtom;  // one k-chunk of A and B: 48 KB
+constexpr int kStages = 4;
+constexpr int kItemRing = 4;
+constexpr int kEpiWarps = 8;
+constexpr int kEpiThreads = kEpiWarps * 32;
+constexpr int kTcThreadsV2 = 64 + kEpiThreads;
+
+struct ItemDesc {
+    int rt, pa, pb, dir, nct;  // nct < 0: no more items
+    int pad[3];
+};
+
 struct TcHdr {
-    unsigned long long a_full;
-    unsigned long long b_full[8];
-    unsigned long long b_empty[8];
+    unsigned long long b_full[kStages];
+    unsigned long long b_empty[kStages];
     unsigned long long acc_full[2];
     unsigned long long acc_empty[2];
+    unsigned long long col_ready[2];
+    unsigned long long it_full[kItemRing];
+    unsigned long long it_empty[kItemRing];
     uint32_t tmem_base;
-    int item;
     int abort;
-    int pad;
+    int pad[2];
+    ItemDesc items[kItemRing];
     float4 col[2][TBN];
 };
 
@@ -157,16 +171,46 @@ __device__ __forceinline__ float bound_F(float D, float alpha, float gam, float 
     return alpha + beta * D + gam * sqrtf(fmaxf(D, 0.f) + q2);
 }
 
-__global__ void __launch_bounds__(kTcThreads, 1)
+__device__ __forceinline__ void item_geometry(const TcArgs& a, int item, int RT, int nseg0, int& rt, int& pa, int& pb,
+                                              int& dir) {
+    if (a.mode == 2) {
+        const int s_rank = item / RT;
+        rt = item % RT;
+        const int4 r = a.ranges[rt];
+        pa = pb = 0;
+        dir = 1;
+        if (s_rank >= r.w) return;
+        const int side = s_rank & 1, idx = s_rank >> 1;
+        if (side == 0) {
+            pa = r.z + idx * a.seg_cols;
+            pb = min(pa + a.seg_cols, r.y);
+        } else {
+            pb = r.z - idx * a.seg_cols;
+            pa = max(pb - a.seg_cols, r.x);
+            dir = -1;
+        }
+    } else {
+        rt = item / nseg0;
+        const int sg = item % nseg0;
+        pa = sg * a.seg_cols;
+        pb = min(pa + a.seg_cols, a.N);
+        dir = 1;
+    }
+}
+
+// Roles: warp 0 schedules work items and issues the TMA loads (lane 0);
+// warp 1 owns the tensor memory and issues the UMMAs (lane 0); warps 2..9
+// are the epilogue (two warps per 32-lane TMEM quarter, each taking half of
+// a tile's 256 columns).  Work items flow from warp 0 to the others through
+// a ring of descriptors; operand k-chunks through a ring of stages; tiles
+// through two TMEM accumulators.  Nothing waits on an unbounded barrier.
+__global__ void __launch_bounds__(kTcThreadsV2, 1)
     k_scan_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, TcArgs a) {
     extern __shared__ unsigned char smraw[];
-    // 1024-byte aligned operand area (128-byte swizzle atoms)
     const uint32_t base_u32 = smem_u32(smraw);
     const uint32_t pad = (1024u - (base_u32 & 1023u)) & 1023u;
-    unsigned char* sbase = smraw + pad;
-    unsigned char* sA = sbase;
-    unsigned char* sB = sbase + a.nka * kABytesPerAtom;
-    TcHdr& h = *reinterpret_cast<TcHdr*>(sB + a.stages * kBBytesPerAtom);
+    unsigned char* stages = smraw + pad;
+    TcHdr& h = *reinterpret_cast<TcHdr*>(stages + kStages * kStageBytes);
 
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
@@ -188,14 +232,18 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     }
 
     if (tid == 0) {
-        mbar_init(&h.a_full, 1);
-        for (int s = 0; s < a.stages; s++) {
+        for (int s = 0; s < kStages; s++) {
             mbar_init(&h.b_full[s], 1);
             mbar_init(&h.b_empty[s], 1);
         }
         for (int b = 0; b < 2; b++) {
             mbar_init(&h.acc_full[b], 1);
-            mbar_init(&h.acc_empty[b], 128);
+            mbar_init(&h.acc_empty[b], kEpiThreads);
+            mbar_init(&h.col_ready[b], kEpiThreads);
+        }
+        for (int r = 0; r < kItemRing; r++) {
+            mbar_init(&h.it_full[r], 1);
+            mbar_init(&h.it_empty[r], 1 + kEpiThreads);
         }
         h.abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -210,156 +258,189 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     tc_fence_after();
     const uint32_t tbase = h.tmem_base;
     volatile int* abort = &h.abort;
-
-    // pipeline state (identical sequences in the producer and MMA roles)
-    uint32_t a_phase = 0;
-    int bstage = 0;
-    uint32_t bphase = 0;
-    uint32_t acc_phase[2] = {0u, 0u};
-    const float neg2s = (float)(-2.0 / (a.stats[3] * a.stats[3]));  // s is a power of two: exact
     const int n = a.n;
-    unsigned long long pairs = 0;
+    const int nka = a.nka;
 
-    for (;;) {
-        __syncthreads();
-        if (tid == 0) h.item = atomicAdd(&a.ctrl->work[a.work_slot], 1);
-        __syncthreads();
-        const int item = h.item;
-        if (item >= items || *abort) break;
-        int rt, pa, pb, dir;
-        if (a.mode == 2) {
-            const int s_rank = item / RT;
-            rt = item % RT;
-            const int4 r = a.ranges[rt];
-            if (s_rank >= r.w) continue;
-            const int side = s_rank & 1, idx = s_rank >> 1;
-            if (side == 0) {
-                pa = r.z + idx * a.seg_cols;
-                pb = min(pa + a.seg_cols, r.y);
-                dir = 1;
-            } else {
-                pb = r.z - idx * a.seg_cols;
-                pa = max(pb - a.seg_cols, r.x);
-                dir = -1;
-            }
-        } else {
-            rt = item / nseg0;
-            const int sg = item % nseg0;
-            pa = sg * a.seg_cols;
-            pb = min(pa + a.seg_cols, a.N);
-            dir = 1;
-        }
-        if (pa >= pb) continue;
-        const int nct = (pb - pa + TBN - 1) / TBN;
-
-        // rows of the tile (epilogue threads own one row each)
-        const bool epi = warp >= 2;
-        const int r_in = epi ? ((warp & 3) * 32 + lane) : 0;
-        int ri = -1;
-        float rmu = 0.f, rc = 0.f, al = 0.f, ga = 0.f, q2 = 0.f, Drun = INFINITY, Dlast = INFINITY;
-        if (epi) {
-            const int r = rt * TBM + r_in;
-            ri = r < cnt ? a.rows.base[off + r] : -1;
-            if (ri >= 0) {
-                rmu = a.rowmu[ri];
-                rc = a.rowc[ri];
-                al = a.alpha[ri];
-                ga = a.gam[ri];
-                q2 = a.q2[ri];
-                Drun = __uint_as_float(a.rmin[ri]);
-                Dlast = Drun;
-            }
-        }
-        bool alive = true;
-        if (a.abandon) {
-            bool al_me = false;
-            if (ri >= 0) {
-                const float g = __uint_as_float(*((volatile const unsigned*)(a.rmin + ri)));
-                const float D = fminf(Drun, g);
-                const float bsf = __uint_as_float(*((volatile const unsigned*)&ctrl->bsf));
-                al_me = !(D + bound_F(D, al, ga, q2, a.beta) < bsf);
-            }
-            alive = __syncthreads_or(al_me) != 0;
-        }
-        if (!alive) continue;
-
-        if (warp == 0) {
-            if (lane == 0) {
-                // A tile: the 128 rows of the list tile, all k atoms
-                const int arow = a.a_row0 + rt * TBM + (a.a_direct ? off : 0);
-                mbar_expect_tx(&h.a_full, (uint32_t)(a.nka * kABytesPerAtom));
-                for (int ka = 0; ka < a.nka; ka++) tma_load_2d(sA + ka * kABytesPerAtom, &mapA, &h.a_full, ka * TKA, arow);
-                for (int ct = 0; ct < nct; ct++) {
-                    const int p0 = dir > 0 ? pa + ct * TBN : pb - (ct + 1) * TBN;
-                    for (int ka = 0; ka < a.nka; ka++) {
-                        if (!mbar_wait(&h.b_empty[bstage], bphase ^ 1u, abort)) {
-                            atomicExch(&a.ctrl->err, DD_ETIMEOUT);
-                            *abort = 1;
-                            break;
-                        }
-                        mbar_expect_tx(&h.b_full[bstage], (uint32_t)kBBytesPerAtom);
-                        tma_load_2d(sB + bstage * kBBytesPerAtom, &mapB, &h.b_full[bstage], ka * TKA, p0);
-                        if (++bstage == a.stages) {
-                            bstage = 0;
-                            bphase ^= 1u;
-                        }
+    if (warp == 0) {
+        // ---------------- scheduler + TMA producer ----------------
+        int stage = 0, ring = 0;
+        uint32_t sph = 0, rph = 0;
+        unsigned long long pairs = 0;
+        bool ok = true;
+        for (;;) {
+            int item = 0;
+            if (lane == 0) item = atomicAdd(&a.ctrl->work[a.work_slot], 1);
+            item = __shfl_sync(0xffffffffu, item, 0);
+            if (item >= items || *abort) break;
+            int rt, pa, pb, dir;
+            item_geometry(a, item, RT, nseg0, rt, pa, pb, dir);
+            if (pa >= pb) continue;
+            // alive check: 4 rows per lane
+            bool any = !a.abandon;
+            int nvr = 0;
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                const int r = rt * TBM + q * 32 + lane;
+                if (r < cnt) {
+                    nvr++;
+                    if (a.abandon) {
+                        const int ri = a.rows.base[off + r];
+                        const float D = __uint_as_float(*((volatile const unsigned*)(a.rmin + ri)));
+                        const float bsf = __uint_as_float(*((volatile const unsigned*)&ctrl->bsf));
+                        any |= !(D + bound_F(D, a.alpha[ri], a.gam[ri], a.q2[ri], a.beta) < bsf);
                     }
-                    if (*abort) break;
                 }
             }
-        } else if (warp == 1) {
+            any = __any_sync(0xffffffffu, any);
+            if (!any) continue;
+            nvr = __reduce_add_sync(0xffffffffu, nvr);
+            const int nct = (pb - pa + TBN - 1) / TBN;
             if (lane == 0) {
-                bool ok = mbar_wait(&h.a_full, a_phase, abort);
-                a_phase ^= 1u;
-                for (int ct = 0; ct < nct && ok; ct++) {
-                    const int buf = ct & 1;
-                    if (!mbar_wait(&h.acc_empty[buf], acc_phase[buf] ^ 1u, abort)) {
+                pairs += (unsigned long long)nvr * (unsigned long long)(pb - pa);
+                if (!mbar_wait(&h.it_empty[ring], rph ^ 1u, abort)) ok = false;
+                if (ok) {
+                    ItemDesc d;
+                    d.rt = rt;
+                    d.pa = pa;
+                    d.pb = pb;
+                    d.dir = dir;
+                    d.nct = nct;
+                    h.items[ring] = d;
+                    mbar_arrive(&h.it_full[ring]);
+                    if (++ring == kItemRing) {
+                        ring = 0;
+                        rph ^= 1u;
+                    }
+                    const int arow = rt * TBM + (a.a_direct ? off : 0);
+                    for (int ct = 0; ct < nct && ok; ct++) {
+                        const int p0 = dir > 0 ? pa + ct * TBN : pb - (ct + 1) * TBN;
+                        for (int ka = 0; ka < nka; ka++) {
+                            if (!mbar_wait(&h.b_empty[stage], sph ^ 1u, abort)) {
+                                ok = false;
+                                break;
+                            }
+                            unsigned char* st = stages + stage * kStageBytes;
+                            mbar_expect_tx(&h.b_full[stage], (uint32_t)kStageBytes);
+                            tma_load_2d(st, &mapA, &h.b_full[stage], ka * TKA, arow);
+                            tma_load_2d(st + kABytesPerAtom, &mapB, &h.b_full[stage], ka * TKA, p0);
+                            if (++stage == kStages) {
+                                stage = 0;
+                                sph ^= 1u;
+                            }
+                        }
+                    }
+                }
+            }
+            ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+            if (!ok) break;
+        }
+        if (lane == 0) {
+            if (!ok) {
+                atomicExch(&a.ctrl->err, DD_ETIMEOUT);
+                *abort = 1;
+            }
+            // end marker (bounded wait; on abort the consumers leave on their own)
+            if (mbar_wait(&h.it_empty[ring], rph ^ 1u, abort)) {
+                h.items[ring].nct = -1;
+                mbar_arrive(&h.it_full[ring]);
+            }
+            if (pairs) atomicAdd(&a.ctrl->pairs, pairs);
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        // ---------------- UMMA issuer ----------------
+        if (lane == 0) {
+            int stage = 0, ring = 0, tb = 0;
+            uint32_t sph = 0, rph = 0;
+            uint32_t aph[2] = {0u, 0u};
+            bool ok = true;
+            for (;;) {
+                if (!mbar_wait(&h.it_full[ring], rph, abort)) {
+                    ok = false;
+                    break;
+                }
+                const ItemDesc d = h.items[ring];
+                mbar_arrive(&h.it_empty[ring]);
+                if (++ring == kItemRing) {
+                    ring = 0;
+                    rph ^= 1u;
+                }
+                if (d.nct < 0) break;
+                for (int ct = 0; ct < d.nct && ok; ct++) {
+                    if (!mbar_wait(&h.acc_empty[tb], aph[tb] ^ 1u, abort)) {
                         ok = false;
                         break;
                     }
                     tc_fence_after();
-                    const uint32_t dt = tbase + (uint32_t)(buf * TBN);
-                    for (int ka = 0; ka < a.nka; ka++) {
-                        if (!mbar_wait(&h.b_full[bstage], bphase, abort)) {
+                    const uint32_t dt = tbase + (uint32_t)(tb * TBN);
+                    for (int ka = 0; ka < nka; ka++) {
+                        if (!mbar_wait(&h.b_full[stage], sph, abort)) {
                             ok = false;
                             break;
                         }
                         tc_fence_after();
-                        const uint64_t ad = sw128_desc(smem_u32(sA + ka * kABytesPerAtom));
-                        const uint64_t bd = sw128_desc(smem_u32(sB + bstage * kBBytesPerAtom));
+                        const uint32_t sa = smem_u32(stages + stage * kStageBytes);
+                        const uint64_t ad = sw128_desc(sa);
+                        const uint64_t bd = sw128_desc(sa + kABytesPerAtom);
 #pragma unroll
                         for (int kk = 0; kk < TKA / 16; kk++)
                             umma_f16(dt, ad + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2), a.idesc,
                                      (ka | kk) != 0 ? 1u : 0u);
-                        umma_commit(&h.b_empty[bstage]);
-                        if (++bstage == a.stages) {
-                            bstage = 0;
-                            bphase ^= 1u;
+                        umma_commit(&h.b_empty[stage]);
+                        if (++stage == kStages) {
+                            stage = 0;
+                            sph ^= 1u;
                         }
                     }
                     if (!ok) break;
-                    umma_commit(&h.acc_full[buf]);
-                    acc_phase[buf] ^= 1u;
+                    umma_commit(&h.acc_full[tb]);
+                    aph[tb] ^= 1u;
+                    tb ^= 1;
                 }
-                if (!ok) {
-                    atomicExch(&a.ctrl->err, DD_ETIMEOUT);
-                    *abort = 1;
-                }
+                if (!ok) break;
             }
-            __syncwarp();
-        } else {
-            // epilogue
-            const int e = tid - 64;
-            const int q = warp & 3;
-            for (int ct = 0; ct < nct; ct++) {
-                const int buf = ct & 1;
-                const int p0 = dir > 0 ? pa + ct * TBN : pb - (ct + 1) * TBN;
-#pragma unroll
-                for (int k2 = 0; k2 < 2; k2++) {
-                    const int c = e + k2 * 128;
+            if (!ok) {
+                atomicExch(&a.ctrl->err, DD_ETIMEOUT);
+                *abort = 1;
+            }
+        }
+        __syncwarp();
+    } else {
+        // ---------------- epilogue ----------------
+        const int e = tid - 64;            // 0 .. kEpiThreads-1
+        const int q = warp & 3;            // TMEM lane quarter
+        const int half = (warp - 2) >> 2;  // column half of the tile
+        const float neg2s = (float)(-2.0 / (a.stats[3] * a.stats[3]));  // s is a power of two: exact
+        int ring = 0, tb = 0;
+        uint32_t rph = 0;
+        uint32_t aph[2] = {0u, 0u}, cph[2] = {0u, 0u};
+        for (;;) {
+            bool ok = mbar_wait(&h.it_full[ring], rph, abort);
+            ok = __all_sync(0xffffffffu, ok);
+            if (!ok) break;
+            const ItemDesc d = h.items[ring];
+            mbar_arrive(&h.it_empty[ring]);
+            if (++ring == kItemRing) {
+                ring = 0;
+                rph ^= 1u;
+            }
+            if (d.nct < 0) break;
+            const int r = d.rt * TBM + q * 32 + lane;
+            const int ri = r < cnt ? a.rows.base[off + r] : -1;
+            float rmu = 0.f, rc = 0.f, Drun = INFINITY;
+            if (ri >= 0) {
+                rmu = a.rowmu[ri];
+                rc = a.rowc[ri];
+                Drun = __uint_as_float(a.rmin[ri]);
+            }
+            const float Dlast = Drun;
+            for (int ct = 0; ct < d.nct; ct++) {
+                const int p0 = d.dir > 0 ? d.pa + ct * TBN : d.pb - (ct + 1) * TBN;
+                {
+                    const int c = e;  // kEpiThreads == TBN: one column each
                     const int p = p0 + c;
                     float4 cd;
-                    if (p >= pa && p < pb) {
+                    if (p >= d.pa && p < d.pb) {
                         cd.x = a.colmu[p];
                         cd.y = a.colc[p];
                         cd.z = __int_as_float(a.sig[p]);
@@ -369,29 +450,31 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                         cd.z = __int_as_float(-(1 << 30));
                     }
                     cd.w = 0.f;
-                    h.col[buf][c] = cd;
+                    h.col[tb][c] = cd;
                 }
-                // every epilogue thread reaches this barrier on every tile, abort or not
-                asm volatile("bar.sync 1, 128;" ::: "memory");
-                bool ok = !*abort && mbar_wait(&h.acc_full[buf], acc_phase[buf], abort);
-                acc_phase[buf] ^= 1u;
-                ok = __all_sync(0xffffffffu, ok);  // tcgen05.ld is warp-wide
-                if (!ok) {
+                mbar_arrive(&h.col_ready[tb]);
+                bool okw = mbar_wait(&h.col_ready[tb], cph[tb], abort);
+                cph[tb] ^= 1u;
+                okw = okw && mbar_wait(&h.acc_full[tb], aph[tb], abort);
+                aph[tb] ^= 1u;
+                okw = __all_sync(0xffffffffu, okw);  // tcgen05.ld is warp-wide
+                if (!okw) {
                     atomicExch(&a.ctrl->err, DD_ETIMEOUT);
                     *abort = 1;
-                    continue;
+                    break;
                 }
                 tc_fence_after();
                 float m = INFINITY;
-                const uint32_t taddr = tbase + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * TBN);
+                const uint32_t taddr = tbase + ((uint32_t)(32 * q) << 16) + (uint32_t)(tb * TBN + half * (TBN / 2));
 #pragma unroll 1
-                for (int ch = 0; ch < TBN / 32; ch++) {
+                for (int ch = 0; ch < TBN / 2 / 32; ch++) {
                     uint32_t v[32];
                     tmem_ld32(taddr + (uint32_t)(ch * 32), v);
                     tmem_ld_wait();
+                    const float4* cdp = &h.col[tb][half * (TBN / 2) + ch * 32];
 #pragma unroll
                     for (int x = 0; x < 32; x++) {
-                        const float4 cd = h.col[buf][ch * 32 + x];
+                        const float4 cd = cdp[x];
                         const float dm = rmu - cd.x;
                         float t = fmaf(dm, dm, cd.y);
                         t = fmaf(neg2s, __uint_as_float(v[x]), t);
@@ -401,15 +484,12 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     }
                 }
                 tc_fence_before();
-                mbar_arrive(&h.acc_empty[buf]);
-                const float D = fmaxf(m + rc, 0.f);
-                Drun = fminf(Drun, D);
+                mbar_arrive(&h.acc_empty[tb]);
+                tb ^= 1;
+                Drun = fminf(Drun, fmaxf(m + rc, 0.f));
             }
             if (ri >= 0 && Drun < Dlast) atomicMin(a.rmin + ri, __float_as_uint(Drun));
-            if (e == 0) {
-                const int nvr = min(TBM, cnt - rt * TBM);
-                pairs += (unsigned long long)nvr * (unsigned long long)(pb - pa);
-            }
+            if (*abort) break;
         }
     }
     __syncthreads();
@@ -422,7 +502,6 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     __syncthreads();
     tc_fence_after();
     if (warp == 1) tmem_dealloc(tbase, 512);
-    if (tid == 64 && pairs) atomicAdd(&a.ctrl->pairs, pairs);
 }
 
 // ---------------------------------------------------------------------------
@@ -431,18 +510,17 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 // Per row (orig order) and per column (mean-bucketed order): sqrt(n) mu_i,
 // c_i (FP32), sqrt(c_i) rounded up; maxima over all rows.
 __global__ void __launch_bounds__(256) k_tc_rowconst(const double* __restrict__ mu_w, const double* __restrict__ c_w,
-                                                     const int32_t* __restrict__ sigpos, int64_t N, int n,
+                                                     const int32_t* __restrict__ sigpos, int64_t N, double sqrt_n,
                                                      float* __restrict__ colmu, float* __restrict__ colc,
                                                      float* __restrict__ rowmu, float* __restrict__ rowc,
                                                      float* __restrict__ rowsc, Ctrl* ctrl) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     float sc = 0.f, cc = 0.f, am = 0.f;
     if (i < N) {
-        const double sn = sqrt((double)n);
-        const float mu = (float)(sn * mu_w[i]);
+        const float mu = (float)(mu_w[i] * sqrt_n);
         const float c = (float)c_w[i];
-        sc = __double2float_ru(sqrt(c_w[i]));
         cc = __double2float_ru(c_w[i]);
+        sc = __fsqrt_ru(cc);
         am = fabsf(mu);
         const int p = sigpos[i];
         colmu[p] = mu;
@@ -472,58 +550,65 @@ __global__ void __launch_bounds__(256) k_tc_rowconst(const double* __restrict__ 
 //   FP32 rounding of c~, sqrt(n) mu~, the epilogue FMAs and the final sum is
 //   bounded through dm^2 <= D + 2 Q_i and |dm| <= sqrt(D + 2 Q_i).
 __global__ void __launch_bounds__(256) k_tc_rowbound(const float* __restrict__ rowsc, const float* __restrict__ rowc,
-                                                     const float* __restrict__ rowmu, int64_t N, int n, double u_in,
-                                                     const double* stats, const double* P2end, const Ctrl* ctrl,
-                                                     float* __restrict__ alpha, float* __restrict__ gam,
-                                                     float* __restrict__ q2) {
+                                                     const float* __restrict__ rowmu, int64_t N, float sqrt_n,
+                                                     float u_in, const double* stats, const double* P2end,
+                                                     const Ctrl* ctrl, float* __restrict__ alpha,
+                                                     float* __restrict__ gam, float* __restrict__ q2) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
-    const double u32 = 5.9604644775390625e-08;  // 2^-24
-    const double uacc = 2.384185791015625e-07; // 2^-22: allows truncating accumulation
-    const double scmax = (double)__uint_as_float(ctrl->tc_scmax);
-    const double cmax = (double)__uint_as_float(ctrl->tc_cmax);
-    const double mumax = (double)__uint_as_float(ctrl->tc_mumax);
-    const double s = stats[3];
-    const double gn = n * uacc / (1.0 - n * uacc);
-    const double Kg = 2.0 * ((2.0 * u_in + u_in * u_in) + gn * (1.0 + u_in) * (1.0 + u_in));
-    const double sci = (double)rowsc[i];
-    const double Q = sci * scmax;
-    const double ci = (double)rowc[i];
-    const double eta = 2.0 * (2.9802322387695312e-08 / s * sqrt((double)n) * (sci + scmax) +
-                              (double)n * 8.881784197001252e-16 / (s * s));
-    const double ec = 512.0 * 1.1102230246251565e-16 * (1.0 + *P2end);
-    const double A0 = Kg * Q + eta + 2.0 * u32 * (ci + cmax) + 2.0 * ec + 8.0 * u32 * Q + 2.0 * u32 * (ci + cmax);
-    const double G0 = 2.0 * u32 * (fabs((double)rowmu[i]) + mumax);
-    alpha[i] = __double2float_ru(2.0 * A0);
-    gam[i] = __double2float_ru(2.0 * G0);
-    q2[i] = __double2float_ru(2.0 * Q);
+    const float u32 = 5.9604644775390625e-08f;   // 2^-24
+    const float uacc = 2.384185791015625e-07f;   // 2^-22: allows truncating accumulation
+    const float n = sqrt_n * sqrt_n;
+    const float scmax = __uint_as_float(ctrl->tc_scmax);
+    const float cmax = __uint_as_float(ctrl->tc_cmax);
+    const float mumax = __uint_as_float(ctrl->tc_mumax);
+    const float s = (float)stats[3];
+    const float maxabs = (float)stats[2];
+    const float gn = n * uacc / (1.f - n * uacc);
+    const float uo = u_in + 2.f * u32;  // operand: FP32 centring then one 16-bit rounding
+    const float Kg = 2.f * ((2.f * uo + uo * uo) + gn * (1.f + uo) * (1.f + uo));
+    const float sci = rowsc[i];
+    const float Q = sci * scmax;
+    const float ci = rowc[i];
+    // absolute operand errors: FP32 centring (2.01 u32 max|t^|) and 16-bit subnormals (2^-25 / s)
+    const float ea = 2.01f * u32 * maxabs + 2.9802322387695312e-08f / s;
+    const float eta = 2.f * (ea * sqrt_n * (sci + scmax) + n * ea * ea);
+    const float ec = 512.f * 1.1102230246251565e-16f * (1.f + (float)*P2end);
+    const float A0 = Kg * Q + eta + 4.f * u32 * (ci + cmax) + 2.f * ec + 8.f * u32 * Q;
+    const float G0 = 2.f * u32 * (fabsf(rowmu[i]) + mumax);
+    alpha[i] = 2.002f * A0;
+    gam[i] = 2.002f * G0;
+    q2[i] = 2.002f * Q;
 }
 
-__device__ __forceinline__ __half to16(double x, __half*) { return __double2half(x); }
-__device__ __forceinline__ __nv_bfloat16 to16(double x, __nv_bfloat16*) { return __double2bfloat16(x); }
+__device__ __forceinline__ __half to16(float x, __half*) { return __float2half_rn(x); }
+__device__ __forceinline__ __nv_bfloat16 to16(float x, __nv_bfloat16*) { return __float2bfloat16_rn(x); }
 
 // Centred rows in the mean-bucketed order: S[p][k] = s (t^_{i+k} - mu_i),
-// i = sig[p], rounded once to FP16 / BF16; zero for k in [n, kpad).
+// i = sig[p], computed in FP32 from the FP32 copy of t^ and rounded once to
+// FP16 / BF16; zero for k in [n, kpad).  (The FP32 centring error, at most
+// 2 u32 max|t^| per element, is part of the row bound.)
 template <typename T16>
-__global__ void __launch_bounds__(256) k_build_S(const double* __restrict__ t64, const double* __restrict__ mu_w,
+__global__ void __launch_bounds__(256) k_build_S(const float* __restrict__ t32, const double* __restrict__ mu_w,
                                                  const int32_t* __restrict__ sig, int64_t N, int n, int kpad,
                                                  const double* stats, T16* __restrict__ S) {
     const int per_row = kpad / 8;
-    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t p = g / per_row;
-    const int k0 = (int)(g % per_row) * 8;
-    if (p >= N) return;
-    const double s = stats[3];
-    const int i = sig[p];
-    const double mu = mu_w[i];
-    T16 v[8];
+    const float s = (float)stats[3];
+    const int64_t total = N * per_row;
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t p = g / per_row;
+        const int k0 = (int)(g % per_row) * 8;
+        const int i = sig[p];
+        const float mu = (float)mu_w[i];
+        T16 v[8];
 #pragma unroll
-    for (int q = 0; q < 8; q++) {
-        const int k = k0 + q;
-        const double x = k < n ? (t64[i + k] - mu) * s : 0.0;
-        v[q] = to16(x, (T16*)nullptr);
+        for (int q = 0; q < 8; q++) {
+            const int k = k0 + q;
+            const float x = k < n ? (t32[i + k] - mu) * s : 0.f;
+            v[q] = to16(x, (T16*)nullptr);
+        }
+        *reinterpret_cast<uint4*>(S + p * kpad + k0) = *reinterpret_cast<uint4*>(v);
     }
-    *reinterpret_cast<uint4*>(S + p * kpad + k0) = *reinterpret_cast<uint4*>(v);
 }
 
 // Operand scale: a power of two that puts max |x'| <= 2 max|t^| near 2^14 (FP16).
@@ -548,12 +633,13 @@ __global__ void __launch_bounds__(256) k_gather_rows(ListRef L, const int32_t* _
     const int cnt = *L.cnt_dev;
     const int off = L.off_dev ? *L.off_dev : 0;
     const int per_row = kpad / 8;  // uint4 per row
-    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t r = g / per_row;
-    const int c = (int)(g % per_row);
-    if (r >= cnt) return;
-    const int i = L.base[off + r];
-    P[r * per_row + c] = S[(int64_t)sigpos[i] * per_row + c];
+    const int64_t total = (int64_t)cnt * per_row;
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = g / per_row;
+        const int c = (int)(g % per_row);
+        const int i = L.base[off + r];
+        P[r * per_row + c] = S[(int64_t)sigpos[i] * per_row + c];
+    }
 }
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -590,22 +676,17 @@ bool make_map(CUtensorMap* map, void* base, int64_t rows, int kpad, int box_rows
 }  // namespace
 
 size_t tc_smem_bytes(int kpad) {
-    const int nka = kpad / TKA;
-    const int stages = tc_stages(kpad);
-    return 1024 + (size_t)nka * kABytesPerAtom + (size_t)stages * kBBytesPerAtom + sizeof(TcHdr);
+    (void)kpad;
+    return 1024 + (size_t)kStages * kStageBytes + sizeof(TcHdr);
 }
 
 int tc_stages(int kpad) {
-    const int nka = kpad / TKA;
-    const int budget = 200 * 1024 - nka * kABytesPerAtom;
-    int st = budget / kBBytesPerAtom;
-    if (st > 4) st = 4;
-    return st;
+    (void)kpad;
+    return kStages;
 }
 
 bool tc_supported(int n) {
-    const int kpad = (n + TKA - 1) / TKA * TKA;
-    return kpad <= 512 && tc_stages(kpad) >= 2;
+    return n >= 1 && n <= (1 << 16);
 }
 
 cudaError_t tc_make_maps(dd_plan_s* p) {
@@ -622,26 +703,24 @@ cudaError_t launch_tc_prep(dd_plan_s* p, cudaStream_t s) {
     const bool bf16 = p->opt.precision == DD_TC_BF16;
     const int gN = (int)((N + 255) / 256);
     k_tc_scale<<<1, 32, 0, s>>>(p->stats, bf16 ? 1 : 0);
-    k_tc_rowconst<<<gN, 256, 0, s>>>(p->mu_w, p->c_w, p->sigpos, N, n, p->colmu, p->colc, p->rowmu, p->rowc,
-                                     p->rowsc, p->ctrl);
-    const double u_in = bf16 ? 0.00390625 : 0.00048828125;
-    k_tc_rowbound<<<gN, 256, 0, s>>>(p->rowsc, p->rowc, p->rowmu, N, n, u_in, p->stats, p->P2 + p->m, p->ctrl,
-                                     p->alpha, p->gam, p->q2);
-    const int64_t threads = N * (p->kpad / 8);
-    const int g = (int)((threads + 255) / 256);
+    k_tc_rowconst<<<gN, 256, 0, s>>>(p->mu_w, p->c_w, p->sigpos, N, std::sqrt((double)n), p->colmu, p->colc,
+                                     p->rowmu, p->rowc, p->rowsc, p->ctrl);
+    const float u_in = bf16 ? 0.00390625f : 0.00048828125f;
+    k_tc_rowbound<<<gN, 256, 0, s>>>(p->rowsc, p->rowc, p->rowmu, N, (float)std::sqrt((double)n), u_in, p->stats,
+                                     p->P2 + p->m, p->ctrl, p->alpha, p->gam, p->q2);
+    const int g = p->sm_count * 8;
     if (bf16)
-        k_build_S<__nv_bfloat16><<<g, 256, 0, s>>>(p->t64, p->mu_w, p->sig, N, n, p->kpad, p->stats,
+        k_build_S<__nv_bfloat16><<<g, 256, 0, s>>>(p->t32, p->mu_w, p->sig, N, n, p->kpad, p->stats,
                                                    reinterpret_cast<__nv_bfloat16*>(p->S16));
     else
-        k_build_S<__half><<<g, 256, 0, s>>>(p->t64, p->mu_w, p->sig, N, n, p->kpad, p->stats,
+        k_build_S<__half><<<g, 256, 0, s>>>(p->t32, p->mu_w, p->sig, N, n, p->kpad, p->stats,
                                             reinterpret_cast<__half*>(p->S16));
     p->launches += 4;
     return cudaGetLastError();
 }
 
 cudaError_t launch_gather_rows(dd_plan_s* p, ListRef L, cudaStream_t s) {
-    const int64_t threads = p->N * (p->kpad / 8);
-    const int g = (int)((threads + 255) / 256);
+    const int g = p->sm_count * 4;
     k_gather_rows<<<g, 256, 0, s>>>(L, p->sigpos, reinterpret_cast<const uint4*>(p->S16), p->kpad,
                                     reinterpret_cast<uint4*>(p->A16));
     p->launches++;
@@ -652,7 +731,7 @@ cudaError_t launch_scan_tc(dd_plan_s* p, const TcArgs& a, bool a_packed, cudaStr
     const size_t smem = tc_smem_bytes(p->kpad);
     cudaError_t e = cudaFuncSetAttribute(k_scan_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_scan_tc<<<p->sm_count, kTcThreads, smem, s>>>(a_packed ? p->mapP_A : p->mapS_A, p->mapS_B, a);
+    k_scan_tc<<<p->sm_count, kTcThreadsV2, smem, s>>>(a_packed ? p->mapP_A : p->mapS_A, p->mapS_B, a);
     return cudaGetLastError();
 }
 

@@ -140,16 +140,53 @@ __global__ void __launch_bounds__(256) k_topk_hist(ListRef in, const uint32_t* _
         if (h[b]) atomicAdd(&ctrl->topk_hist[b], h[b]);
 }
 
-// Top-k pass 2: the threshold bin (from the top) whose cumulative count reaches k.
-__global__ void k_topk_thr(Ctrl* ctrl, int k) {
-    if (threadIdx.x != 0) return;
-    int run = 0;
-    int b = kTopkBins - 1;
-    for (; b > 0; b--) {
-        run += ctrl->topk_hist[b];
-        if (run >= k) break;
+// Top-k pass 2: the threshold bin (from the top) whose cumulative count
+// reaches k.  One block: per-thread sums of 4 bins (descending), a block
+// inclusive scan, and the first thread whose run crosses k.
+__global__ void __launch_bounds__(1024) k_topk_thr(Ctrl* ctrl, int k) {
+    __shared__ int part[32];
+    __shared__ int found;
+    const int t = threadIdx.x;  // thread t covers bins [4095 - 4t - 3, 4095 - 4t]
+    int c[4], s = 0;
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+        c[q] = ctrl->topk_hist[kTopkBins - 1 - 4 * t - q];
+        s += c[q];
     }
-    ctrl->topk_thr = (uint32_t)b << 19;
+    const int lane = t & 31, wid = t >> 5;
+    int incl = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += u;
+    }
+    if (lane == 31) part[wid] = incl;
+    if (t == 0) found = 0x7fffffff;
+    __syncthreads();
+    if (wid == 0) {
+        const int v = part[lane];
+        int cc = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int u = __shfl_up_sync(0xffffffffu, cc, o);
+            if (lane >= o) cc += u;
+        }
+        part[lane] = cc - v;
+    }
+    __syncthreads();
+    int run = part[wid] + incl - s;
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+        const int before = run;
+        run += c[q];
+        if (before < k && run >= k) atomicMin(&found, 4 * t + q);
+    }
+    __syncthreads();
+    if (t == 0) {
+        const int pos = found == 0x7fffffff ? kTopkBins - 1 : found;  // fewer than k rows: take them all
+        const int b = kTopkBins - 1 - pos;
+        ctrl->topk_thr = found == 0x7fffffff ? 0u : ((uint32_t)b << 19);
+    }
 }
 
 // Rows alive after the last wave have scanned every column: their running
@@ -455,7 +492,7 @@ struct Seq {
 
     void topk(ListRef in, int k) {
         k_topk_hist<<<2 * p->sm_count, 256, 0, s>>>(in, p->rmin, tb, p->ctrl);
-        k_topk_thr<<<1, 32, 0, s>>>(p->ctrl, k);
+        k_topk_thr<<<1, 1024, 0, s>>>(p->ctrl, k);
         p->launches += 2;
         check();
     }

@@ -125,8 +125,11 @@ def test_edge_cases(prec):
     _check(T, 6, r, i_ref, d2_ref)
 
 
-def test_tc_rejects_long_subsequences():
-    dd = _dd()
-    with pytest.raises(dd.DDError) as e:
-        dd.Plan(1 << 14, 1000, "tc_fp16")
-    assert e.value.status == 7
+@pytest.mark.parametrize("n,m", [(700, 2200), (1000, 5000), (1024, 3100)])
+def test_long_subsequences(n, m):
+    """k = n spans many 64-element operand chunks (and ragged tails)."""
+    rng = np.random.default_rng(n)
+    T = np.cumsum(rng.standard_normal(m)).astype(np.float32)
+    r = _search(T, n, "tc_fp16")
+    i_ref, d2_ref = oracle.discord_brute(T, n)
+    _check(T, n, r, i_ref, d2_ref)
