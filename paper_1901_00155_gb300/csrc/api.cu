@@ -100,8 +100,7 @@ size_t carve(dd_plan_s* p, char* base) {
         p->kpad = (p->n + 63) / 64 * 64;
         p->S16 = c.take<uint16_t>((size_t)N * p->kpad);
         p->A16 = c.take<uint16_t>((size_t)N * p->kpad);
-        p->colmu = c.take<float>(N);
-        p->colc = c.take<float>(N);
+        p->coldat = c.take<float4>(N + 512);
         p->rowmu = c.take<float>(N);
         p->rowc = c.take<float>(N);
         p->rowsc = c.take<float>(N);
@@ -136,15 +135,25 @@ struct BusyGuard {
     }
 };
 
+void rec(dd_plan_s* p, cudaEvent_t e, cudaStream_t s) {
+    if (p->capturing)
+        cudaEventRecordWithFlags(e, s, cudaEventRecordExternal);
+    else
+        cudaEventRecord(e, s);
+}
+
 void prof_begin(dd_plan_s* p, cudaStream_t s) {
     p->ev_used = 0;
-    if (p->profiling) cudaEventRecord(p->call_ev[0], s);
+    if (p->profiling) rec(p, p->call_ev[0], s);
+}
+
+void prof_stop(dd_plan_s* p, cudaStream_t s) {
+    if (p->profiling) rec(p, p->call_ev[1], s);
 }
 
 // Reads back the events of a finished synchronous call.
-void prof_end(dd_plan_s* p, cudaStream_t s, int64_t pairs) {
+void prof_read(dd_plan_s* p, int64_t pairs) {
     if (!p->profiling) return;
-    cudaEventRecord(p->call_ev[1], s);
     cudaEventSynchronize(p->call_ev[1]);
     dd_profile_t r{};
     r.precision = p->opt.precision;
@@ -159,16 +168,75 @@ void prof_end(dd_plan_s* p, cudaStream_t s, int64_t pairs) {
     p->prof = r;
 }
 
-dd_status_t search_sync(dd_plan_s* p, const float* T_dev, dd_result_t* out, cudaStream_t s) {
+// Everything one synchronous search enqueues: the search and the copy of its
+// result to pinned host memory.
+cudaError_t enqueue_sync(dd_plan_s* p, const float* T_dev, cudaStream_t s) {
     prof_begin(p, s);
     cudaError_t e = dd::launch_search(p, T_dev, p->res_dev, s);
-    if (e != cudaSuccess) return from_cuda(e);
+    if (e != cudaSuccess) return e;
     e = cudaMemcpyAsync(p->res_host, p->res_dev, sizeof(dd_result_t), cudaMemcpyDeviceToHost, s);
+    prof_stop(p, s);
+    return e;
+}
+
+// Replays (capturing first if needed) the graph of `kind` for (T, out).
+cudaError_t graph_launch(dd_plan_s* p, int kind, const float* T_dev, dd_result_t* out_dev, cudaStream_t s) {
+    if (!p->gexec || p->g_T != T_dev || p->g_out != out_dev || p->g_kind != kind || p->g_prof != p->profiling) {
+        if (p->gexec) {
+            cudaGraphExecDestroy(p->gexec);
+            p->gexec = nullptr;
+        }
+        if (!p->cap_stream) {
+            cudaError_t e0 = cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking);
+            if (e0 != cudaSuccess) return e0;
+        }
+        cudaError_t e = cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return e;
+        p->capturing = true;
+        int64_t launches = 0;
+        cudaError_t ee;
+        if (kind == 0) {
+            ee = enqueue_sync(p, T_dev, p->cap_stream);
+        } else {
+            ee = dd::launch_search(p, T_dev, out_dev, p->cap_stream);
+        }
+        launches = p->launches;
+        const int used = p->ev_used;
+        cudaGraph_t g = nullptr;
+        e = cudaStreamEndCapture(p->cap_stream, &g);
+        p->capturing = false;
+        if (ee != cudaSuccess || e != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            cudaGetLastError();
+            return ee != cudaSuccess ? ee : e;
+        }
+        e = cudaGraphInstantiate(&p->gexec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            p->gexec = nullptr;
+            return e;
+        }
+        p->g_T = T_dev;
+        p->g_out = out_dev;
+        p->g_kind = kind;
+        p->g_prof = p->profiling;
+        p->launches = launches;
+        p->ev_used = used;
+        p->g_launches = launches;
+        p->g_ev_used = used;
+    }
+    p->launches = p->g_launches;
+    p->ev_used = p->g_ev_used;
+    return cudaGraphLaunch(p->gexec, s);
+}
+
+dd_status_t search_sync(dd_plan_s* p, const float* T_dev, dd_result_t* out, cudaStream_t s) {
+    cudaError_t e = p->use_graph ? graph_launch(p, 0, T_dev, nullptr, s) : enqueue_sync(p, T_dev, s);
     if (e != cudaSuccess) return from_cuda(e);
     e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return from_cuda(e);
     *out = *p->res_host;
-    prof_end(p, s, out->computed_pairs);
+    prof_read(p, out->computed_pairs);
     return (dd_status_t)out->status;
 }
 
@@ -179,7 +247,11 @@ void prof_mark(dd_plan_s* p, cudaStream_t s, bool start) {
     if (!p->profiling) return;
     if (p->ev_used >= (int)p->ev.size()) return;  // pool exhausted: later launches untimed
     (void)start;
-    cudaEventRecord(p->ev[p->ev_used++], s);
+    cudaEvent_t e = p->ev[p->ev_used++];
+    if (p->capturing)
+        cudaEventRecordWithFlags(e, s, cudaEventRecordExternal);
+    else
+        cudaEventRecord(e, s);
 }
 }  // namespace dd
 
@@ -272,6 +344,21 @@ dd_status_t dd_plan_create(dd_plan_t* plan, int64_t m, int32_t n, const dd_optio
         delete p;
         return DD_ENOMEM;
     }
+    {
+        // golden-ratio stride, coprime with N
+        int64_t st = (int64_t)(0.6180339887498949 * (double)p->N);
+        if (st < 1) st = 1;
+        auto gcd = [](int64_t x, int64_t y) {
+            while (y) {
+                const int64_t t = x % y;
+                x = y;
+                y = t;
+            }
+            return x;
+        };
+        while (gcd(st, p->N) != 1) st++;
+        p->mu_stride = st % p->N == 0 ? 1 : st;
+    }
     dd::host_breakpoints(o.alphabet, p->beta_host);
     e = cudaMemcpy(p->beta, p->beta_host, sizeof(double) * (o.alphabet - 1), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(p->t64 + p->m, 0, sizeof(double) * kPad);
@@ -281,6 +368,7 @@ dd_status_t dd_plan_create(dd_plan_t* plan, int64_t m, int32_t n, const dd_optio
         e = cudaGetLastError();
     }
     if (e == cudaSuccess && o.precision != DD_FP32) e = dd::tc_make_maps(p);
+    if (e == cudaSuccess && o.precision != DD_FP32) e = dd::tc_init_plan(p);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
         cudaFreeHost(p->res_host);
@@ -295,6 +383,8 @@ dd_status_t dd_plan_create(dd_plan_t* plan, int64_t m, int32_t n, const dd_optio
 void dd_plan_destroy(dd_plan_t p) {
     if (!p) return;
     cudaDeviceSynchronize();
+    if (p->gexec) cudaGraphExecDestroy(p->gexec);
+    if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
     for (cudaEvent_t e : p->ev) cudaEventDestroy(e);
     for (cudaEvent_t e : p->call_ev)
         if (e) cudaEventDestroy(e);
@@ -314,7 +404,9 @@ dd_status_t dd_find_discord_async(dd_plan_t p, const float* T_dev, dd_result_t* 
     if (!p || !T_dev || !out_dev) return DD_EINVAL;
     BusyGuard g(p);
     if (!g.ok) return DD_EBUSY;
-    return from_cuda(dd::launch_search(p, T_dev, out_dev, static_cast<cudaStream_t>(stream)));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (p->use_graph) return from_cuda(graph_launch(p, 1, T_dev, out_dev, s));
+    return from_cuda(dd::launch_search(p, T_dev, out_dev, s));
 }
 
 dd_status_t dd_find_discord_host(dd_plan_t p, const float* T_host, dd_result_t* out, void* stream) {

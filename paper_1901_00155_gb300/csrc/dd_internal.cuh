@@ -154,8 +154,7 @@ struct TcArgs {
     ListRef rows;
     int a_direct, a_row0;
     const int32_t* sig;
-    const float* colmu;
-    const float* colc;
+    const float4* coldat;
     const float* rowmu;
     const float* rowc;
     const float* alpha;
@@ -218,6 +217,7 @@ struct dd_plan_s {
     int32_t* blockcnt_mu = nullptr;   // [nh * kMuBins]
     int32_t* binstart = nullptr;      // [kMuBins + 1]
     int32_t* sig = nullptr;           // [N] rows in mean-bucketed order
+    int64_t mu_stride = 0;            // stride permutation feeding the mean-bin sort (gcd with N = 1)
     int32_t* sigpos = nullptr;        // [N] position of each row in sig
     int4* ranges = nullptr;           // [N/128 + 1] per-tile column range (L, H, C, segments)
 
@@ -225,8 +225,8 @@ struct dd_plan_s {
     int kpad = 0;                     // n rounded up to 64 (one 128-byte swizzle atom)
     void* S16 = nullptr;              // [N][kpad] centred rows in mean-bucketed order (FP16/BF16)
     void* A16 = nullptr;              // [N][kpad] rows of the current list, packed
-    float* colmu = nullptr;           // [N] sqrt(n) mu in mean-bucketed order
-    float* colc = nullptr;            // [N] c in mean-bucketed order
+    float4* coldat = nullptr;         // [N + 512] per column in mean-bucketed order: (sqrt(n) mu, c, index, 0),
+                                      // 256 padding entries on each side (c = +inf)
     float* rowmu = nullptr;           // [N] sqrt(n) mu (orig order)
     float* rowc = nullptr;            // [N] c
     float* rowsc = nullptr;           // [N] sqrt(c) rounded up
@@ -237,6 +237,19 @@ struct dd_plan_s {
     CUtensorMap mapS_A, mapS_B, mapP_A;
 
     double beta_host[dd::kMaxAlphabet];
+
+    // captured search graph (replayed while the input/output pointers and the
+    // profiling switch stay the same)
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    const void* g_T = nullptr;
+    const void* g_out = nullptr;
+    int g_kind = -1;
+    bool g_prof = false;
+    bool capturing = false;
+    bool use_graph = true;
+    int64_t g_launches = 0;
+    int g_ev_used = 0;
 
     // tracing (dd_plan_set_profiling)
     bool profiling = false;
@@ -261,6 +274,7 @@ size_t tc_smem_bytes(int kpad);
 int tc_stages(int kpad);
 bool tc_supported(int n);
 cudaError_t tc_make_maps(dd_plan_s* p);
+cudaError_t tc_init_plan(dd_plan_s* p);
 cudaError_t launch_tc_prep(dd_plan_s* p, cudaStream_t s);
 cudaError_t launch_gather_rows(dd_plan_s* p, ListRef L, cudaStream_t s);
 cudaError_t launch_scan_tc(dd_plan_s* p, const TcArgs& a, bool a_packed, cudaStream_t s);

@@ -168,40 +168,6 @@ __global__ void __launch_bounds__(1024) k_norm_blocks(const float* __restrict__ 
     }
 }
 
-// Exclusive scan of the block totals (one block; sequential runs per thread).
-__global__ void __launch_bounds__(1024) k_norm_scan_totals(double* bsum, int nscan) {
-    __shared__ double r1[1024], r2[1024];
-    const int per = (nscan + 1023) / 1024;
-    const int lo = threadIdx.x * per, hi = min(nscan, lo + per);
-    double a1 = 0.0, a2 = 0.0;
-    for (int b = lo; b < hi; b++) {
-        a1 += bsum[b];
-        a2 += bsum[nscan + b];
-    }
-    r1[threadIdx.x] = a1;
-    r2[threadIdx.x] = a2;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double c1 = 0.0, c2 = 0.0;
-        for (int t = 0; t < 1024; t++) {
-            double x1 = r1[t], x2 = r2[t];
-            r1[t] = c1;
-            r2[t] = c2;
-            c1 += x1;
-            c2 += x2;
-        }
-    }
-    __syncthreads();
-    double c1 = r1[threadIdx.x], c2 = r2[threadIdx.x];
-    for (int b = lo; b < hi; b++) {
-        double x1 = bsum[b], x2 = bsum[nscan + b];
-        bsum[2 * nscan + b] = c1;
-        bsum[3 * nscan + b] = c2;
-        c1 += x1;
-        c2 += x2;
-    }
-}
-
 // Exclusive block scan of two doubles per thread (1024 threads).
 __device__ void block_exscan2(double& a, double& b, double* sh1, double* sh2) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -238,6 +204,29 @@ __device__ void block_exscan2(double& a, double& b, double* sh1, double* sh2) {
     __syncthreads();
     a = sh1[wid] + (ia - a);
     b = sh2[wid] + (ib - b);
+}
+
+// Exclusive scan of the block totals (one block; each thread a run of
+// consecutive totals, then a block scan of the run sums).
+__global__ void __launch_bounds__(1024) k_norm_scan_totals(double* bsum, int nscan) {
+    __shared__ double sh1[32], sh2[32];
+    const int per = (nscan + 1023) / 1024;
+    const int lo = threadIdx.x * per, hi = min(nscan, lo + per);
+    double a1 = 0.0, a2 = 0.0;
+    for (int b = lo; b < hi; b++) {
+        a1 += bsum[b];
+        a2 += bsum[nscan + b];
+    }
+    double e1 = a1, e2 = a2;
+    block_exscan2(e1, e2, sh1, sh2);
+    double c1 = e1, c2 = e2;
+    for (int b = lo; b < hi; b++) {
+        const double x1 = bsum[b], x2 = bsum[nscan + b];
+        bsum[2 * nscan + b] = c1;
+        bsum[3 * nscan + b] = c2;
+        c1 += x1;
+        c2 += x2;
+    }
 }
 
 __global__ void __launch_bounds__(1024) k_norm_prefix(const double* __restrict__ t64, int64_t m,
@@ -325,22 +314,49 @@ __global__ void __launch_bounds__(256) k_sax(const double* __restrict__ P1, cons
     code[i] = h;
 }
 
+__device__ __forceinline__ int64_t seq_row(int64_t r, int64_t N, int64_t stride) {
+    return stride > 0 ? (int64_t)(((unsigned long long)r * (unsigned long long)stride) % (unsigned long long)N) : r;
+}
+
 // ---- Eq. 8: word histogram, one block-local count per word -----------------
 __global__ void __launch_bounds__(1024) k_word_hist(const int32_t* __restrict__ code, int64_t N, int D,
-                                                    int32_t* __restrict__ hist, int32_t* __restrict__ blockcnt) {
+                                                    int32_t* __restrict__ hist, int32_t* __restrict__ blockcnt,
+                                                    int64_t stride) {
     extern __shared__ int32_t sh_cnt[];
     for (int h = threadIdx.x; h < D; h += blockDim.x) sh_cnt[h] = 0;
     __syncthreads();
     const int64_t base = (int64_t)blockIdx.x * kHistRows;
     for (int r = threadIdx.x; r < kHistRows; r += blockDim.x) {
-        int64_t i = base + r;
-        if (i < N) atomicAdd(&sh_cnt[code[i]], 1);
+        const int64_t e = base + r;
+        if (e < N) atomicAdd(&sh_cnt[code[seq_row(e, N, stride)]], 1);
     }
     __syncthreads();
     for (int h = threadIdx.x; h < D; h += blockDim.x) {
         int c = sh_cnt[h];
         blockcnt[(int64_t)blockIdx.x * D + h] = c;
         if (c) atomicAdd(&hist[h], c);
+    }
+}
+
+// Exclusive scan of column h of the [nblk][D] block-count matrix, starting at
+// `run`; loads are issued eight at a time so their latencies overlap.
+__device__ __forceinline__ void column_scan(int32_t* __restrict__ blockcnt, int D, int nblk, int h, int run) {
+    int b = 0;
+    for (; b + 8 <= nblk; b += 8) {
+        int c[8];
+#pragma unroll
+        for (int q = 0; q < 8; q++) c[q] = blockcnt[(int64_t)(b + q) * D + h];
+#pragma unroll
+        for (int q = 0; q < 8; q++) {
+            blockcnt[(int64_t)(b + q) * D + h] = run;
+            run += c[q];
+        }
+    }
+    for (; b < nblk; b++) {
+        const int64_t ix = (int64_t)b * D + h;
+        const int c = blockcnt[ix];
+        blockcnt[ix] = run;
+        run += c;
     }
 }
 
@@ -400,23 +416,18 @@ __global__ void __launch_bounds__(1024) k_word_plan(const int32_t* __restrict__ 
         ctrl->n2 = (int)(N - n1);
     }
     __syncthreads();
-    for (int h = threadIdx.x; h < D; h += blockDim.x) {
-        int run = word_start[h];
-        for (int b = 0; b < nblk; b++) {
-            int64_t ix = (int64_t)b * D + h;
-            int c = blockcnt[ix];
-            blockcnt[ix] = run;
-            run += c;
-        }
-    }
+    for (int h = threadIdx.x; h < D; h += blockDim.x) column_scan(blockcnt, D, nblk, h, word_start[h]);
 }
 
 // ---- Eq. 10: stable scatter of rows into word order ------------------------
 // Block b handles rows [b*kHistRows, (b+1)*kHistRows); warp w a contiguous
 // slice of it; ranks inside a round of 32 rows come from __match_any_sync.
+// Input element r is row seq_row(r): the identity (stride 0) or a stride
+// permutation r -> r * stride mod N (gcd(stride, N) = 1), which makes the rows of
+// a bucket follow that permutation instead of their index order.
 __global__ void k_word_scatter(const int32_t* __restrict__ code, int64_t N, int D,
                                const int32_t* __restrict__ blockbase, int32_t* __restrict__ order,
-                               int32_t* __restrict__ pos_of) {
+                               int32_t* __restrict__ pos_of, int64_t stride) {
     extern __shared__ int32_t sh_wc[];  // [nwarps][D]
     const int nw = blockDim.x >> 5;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -426,8 +437,8 @@ __global__ void k_word_scatter(const int32_t* __restrict__ code, int64_t N, int 
     const int64_t base = (int64_t)blockIdx.x * kHistRows + (int64_t)wid * per;
     int32_t* wc = sh_wc + wid * D;
     for (int r = lane; r < per; r += 32) {
-        int64_t i = base + r;
-        if (i < N) atomicAdd(&wc[code[i]], 1);
+        const int64_t e = base + r;
+        if (e < N) atomicAdd(&wc[code[seq_row(e, N, stride)]], 1);
     }
     __syncthreads();
     for (int h = threadIdx.x; h < D; h += blockDim.x) {
@@ -441,8 +452,9 @@ __global__ void k_word_scatter(const int32_t* __restrict__ code, int64_t N, int 
     __syncthreads();
     const unsigned lt = (1u << lane) - 1u;
     for (int r0 = 0; r0 < per; r0 += 32) {
-        int64_t i = base + r0 + lane;
-        bool ok = (r0 + lane < per) && (i < N);
+        const int64_t e = base + r0 + lane;
+        bool ok = (r0 + lane < per) && (e < N);
+        const int64_t i = ok ? seq_row(e, N, stride) : 0;
         int h = ok ? code[i] : -1 - lane;  // unique dummy keys for idle lanes
         unsigned peers = __match_any_sync(0xffffffffu, h);
         int rank = __popc(peers & lt);
@@ -515,18 +527,25 @@ __global__ void __launch_bounds__(256) k_bin_bases(int D, int nblk, const int32_
                                                    int32_t* __restrict__ blockcnt) {
     const int h = blockIdx.x * blockDim.x + threadIdx.x;
     if (h >= D) return;
-    int r = binstart[h];
-    for (int b = 0; b < nblk; b++) {
-        const int64_t ix = (int64_t)b * D + h;
-        const int c = blockcnt[ix];
-        blockcnt[ix] = r;
-        r += c;
-    }
+    column_scan(blockcnt, D, nblk, h, binstart[h]);
+}
+
+// Warps per block of the stable scatter: per-warp counters for every word
+// must fit in shared memory (up to 192 KB), and the warps split the block's
+// rows evenly.
+int scatter_warps(int D) {
+    int nw = (192 * 1024 / 4) / D;
+    if (nw > 32) nw = 32;
+    if (nw < 1) nw = 1;
+    while (kHistRows % nw) nw--;
+    return nw;
 }
 
 }  // namespace
 
 cudaError_t launch_prep(dd_plan_s* p, const float* T, cudaStream_t s) {
+    cudaError_t ea = cudaFuncSetAttribute(k_word_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, 192 * 1024);
+    if (ea != cudaSuccess) return ea;
     const int64_t m = p->m, N = p->N;
     const int n = p->n;
     const int D = p->D;
@@ -547,24 +566,22 @@ cudaError_t launch_prep(dd_plan_s* p, const float* T, cudaStream_t s) {
                              p->opt.paa_mode, p->beta, p->code);
     const int nh = (int)((N + kHistRows - 1) / kHistRows);
     cudaMemsetAsync(p->hist, 0, sizeof(int32_t) * D, s);
-    k_word_hist<<<nh, 1024, sizeof(int32_t) * D, s>>>(p->code, N, D, p->hist, p->blockcnt);
+    k_word_hist<<<nh, 1024, sizeof(int32_t) * D, s>>>(p->code, N, D, p->hist, p->blockcnt, 0);
     k_word_plan<<<1, 1024, 0, s>>>(p->hist, D, nh, p->blockcnt, p->word_start, p->opt.phase1_max, N, p->ctrl);
-    int nw = (48 * 1024 / 4) / D;
-    if (nw > 32) nw = 32;
-    if (nw < 1) nw = 1;
-    while (kHistRows % nw) nw--;
-    k_word_scatter<<<nh, nw * 32, sizeof(int32_t) * nw * D, s>>>(p->code, N, D, p->blockcnt, p->order, p->pos_of);
+    int nw = scatter_warps(D);
+    k_word_scatter<<<nh, nw * 32, sizeof(int32_t) * nw * D, s>>>(p->code, N, D, p->blockcnt, p->order, p->pos_of, 0);
     // mean-bucketed order (sig) with bin offsets
     k_mu_bins<<<gN, 256, 0, s>>>(p->mu_w, N, p->stats, p->mubin);
     cudaMemsetAsync(p->hist_mu, 0, sizeof(int32_t) * kMuBins, s);
-    k_word_hist<<<nh, 1024, sizeof(int32_t) * kMuBins, s>>>(p->mubin, N, kMuBins, p->hist_mu, p->blockcnt_mu);
+    // rows of a mean bin follow a golden-ratio stride permutation, not time, so
+    // that neighbours in this order are seldom overlapping subsequences
+    k_word_hist<<<nh, 1024, sizeof(int32_t) * kMuBins, s>>>(p->mubin, N, kMuBins, p->hist_mu, p->blockcnt_mu,
+                                                            p->mu_stride);
     k_bin_scan<<<1, 1024, 0, s>>>(p->hist_mu, kMuBins, p->binstart);
     k_bin_bases<<<(kMuBins + 255) / 256, 256, 0, s>>>(kMuBins, nh, p->binstart, p->blockcnt_mu);
-    int nw2 = (48 * 1024 / 4) / kMuBins;
-    if (nw2 < 1) nw2 = 1;
-    while (kHistRows % nw2) nw2--;
+    const int nw2 = scatter_warps(kMuBins);
     k_word_scatter<<<nh, nw2 * 32, sizeof(int32_t) * nw2 * kMuBins, s>>>(p->mubin, N, kMuBins, p->blockcnt_mu, p->sig,
-                                                                        p->sigpos);
+                                                                        p->sigpos, p->mu_stride);
     p->launches += 17;
     return cudaGetLastError();
 }

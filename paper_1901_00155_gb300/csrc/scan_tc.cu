@@ -45,11 +45,15 @@ constexpr int kStages = 4;
 constexpr int kItemRing = 4;
 constexpr int kEpiWarps = 8;
 constexpr int kEpiThreads = kEpiWarps * 32;
-constexpr int kTcThreadsV2 = 64 + kEpiThreads;
+constexpr int kTcThreadsV2 = 96 + kEpiThreads;  // scheduler, MMA, 8 epilogue warps, TMA producer
+
+constexpr int kColSlots = 4;
+constexpr int kColPad = TBN;  // padding of the per-column constant array on each side
 
 struct ItemDesc {
     int rt, pa, pb, dir, nct;  // nct < 0: no more items
     int pad[3];
+    float4 row[TBM];           // per tile row: (sqrt(n) mu, c, running minimum, index bits)
 };
 
 struct TcHdr {
@@ -57,14 +61,15 @@ struct TcHdr {
     unsigned long long b_empty[kStages];
     unsigned long long acc_full[2];
     unsigned long long acc_empty[2];
-    unsigned long long col_ready[2];
+    unsigned long long col_full[kColSlots];
+    unsigned long long col_empty[kColSlots];
     unsigned long long it_full[kItemRing];
     unsigned long long it_empty[kItemRing];
     uint32_t tmem_base;
     int abort;
     int pad[2];
     ItemDesc items[kItemRing];
-    float4 col[2][TBN];
+    float4 col[kColSlots][TBN];  // per tile column: (sqrt(n) mu, c or +inf, index bits, 0)
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -114,6 +119,13 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, u
         "[%4];" ::"r"(smem_u32(dst)),
         "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
         : "memory");
+}
+
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, unsigned long long* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
 }
 
 __device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
@@ -190,8 +202,9 @@ __device__ __forceinline__ void item_geometry(const TcArgs& a, int item, int RT,
             dir = -1;
         }
     } else {
-        rt = item / nseg0;
-        const int sg = item % nseg0;
+        // column-segment major: concurrent CTAs share the same operand columns through L2
+        const int sg = item / RT;
+        rt = item % RT;
         pa = sg * a.seg_cols;
         pb = min(pa + a.seg_cols, a.N);
         dir = 1;
@@ -239,11 +252,14 @@ __global__ void __launch_bounds__(kTcThreadsV2, 1)
         for (int b = 0; b < 2; b++) {
             mbar_init(&h.acc_full[b], 1);
             mbar_init(&h.acc_empty[b], kEpiThreads);
-            mbar_init(&h.col_ready[b], kEpiThreads);
+        }
+        for (int c = 0; c < kColSlots; c++) {
+            mbar_init(&h.col_full[c], 1);
+            mbar_init(&h.col_empty[c], kEpiThreads);
         }
         for (int r = 0; r < kItemRing; r++) {
             mbar_init(&h.it_full[r], 1);
-            mbar_init(&h.it_empty[r], 1 + kEpiThreads);
+            mbar_init(&h.it_empty[r], 2 + kEpiThreads);  // TMA producer, MMA issuer, epilogue threads
         }
         h.abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -261,10 +277,11 @@ __global__ void __launch_bounds__(kTcThreadsV2, 1)
     const int n = a.n;
     const int nka = a.nka;
 
+    const int tma_warp = 2 + kEpiWarps;
     if (warp == 0) {
-        // ---------------- scheduler + TMA producer ----------------
-        int stage = 0, ring = 0;
-        uint32_t sph = 0, rph = 0;
+        // ---------------- scheduler: work items, rows, alive check ----------------
+        int ring = 0;
+        uint32_t rph = 0;
         unsigned long long pairs = 0;
         bool ok = true;
         for (;;) {
@@ -275,64 +292,47 @@ __global__ void __launch_bounds__(kTcThreadsV2, 1)
             int rt, pa, pb, dir;
             item_geometry(a, item, RT, nseg0, rt, pa, pb, dir);
             if (pa >= pb) continue;
-            // alive check: 4 rows per lane
+            // rows of the tile (4 per lane) and the alive check
             bool any = !a.abandon;
             int nvr = 0;
+            float4 rowd[4];
+            const float bsf = __uint_as_float(*((volatile const unsigned*)&ctrl->bsf));
 #pragma unroll
             for (int q = 0; q < 4; q++) {
                 const int r = rt * TBM + q * 32 + lane;
+                rowd[q] = make_float4(0.f, 0.f, INFINITY, __int_as_float(-1));
                 if (r < cnt) {
                     nvr++;
-                    if (a.abandon) {
-                        const int ri = a.rows.base[off + r];
-                        const float D = __uint_as_float(*((volatile const unsigned*)(a.rmin + ri)));
-                        const float bsf = __uint_as_float(*((volatile const unsigned*)&ctrl->bsf));
-                        any |= !(D + bound_F(D, a.alpha[ri], a.gam[ri], a.q2[ri], a.beta) < bsf);
-                    }
+                    const int ri = a.rows.base[off + r];
+                    const float D = __uint_as_float(*((volatile const unsigned*)(a.rmin + ri)));
+                    rowd[q] = make_float4(a.rowmu[ri], a.rowc[ri], D, __int_as_float(ri));
+                    if (a.abandon) any |= !(D + bound_F(D, a.alpha[ri], a.gam[ri], a.q2[ri], a.beta) < bsf);
                 }
             }
             any = __any_sync(0xffffffffu, any);
             if (!any) continue;
             nvr = __reduce_add_sync(0xffffffffu, nvr);
-            const int nct = (pb - pa + TBN - 1) / TBN;
-            if (lane == 0) {
-                pairs += (unsigned long long)nvr * (unsigned long long)(pb - pa);
-                if (!mbar_wait(&h.it_empty[ring], rph ^ 1u, abort)) ok = false;
-                if (ok) {
-                    ItemDesc d;
-                    d.rt = rt;
-                    d.pa = pa;
-                    d.pb = pb;
-                    d.dir = dir;
-                    d.nct = nct;
-                    h.items[ring] = d;
-                    mbar_arrive(&h.it_full[ring]);
-                    if (++ring == kItemRing) {
-                        ring = 0;
-                        rph ^= 1u;
-                    }
-                    const int arow = rt * TBM + (a.a_direct ? off : 0);
-                    for (int ct = 0; ct < nct && ok; ct++) {
-                        const int p0 = dir > 0 ? pa + ct * TBN : pb - (ct + 1) * TBN;
-                        for (int ka = 0; ka < nka; ka++) {
-                            if (!mbar_wait(&h.b_empty[stage], sph ^ 1u, abort)) {
-                                ok = false;
-                                break;
-                            }
-                            unsigned char* st = stages + stage * kStageBytes;
-                            mbar_expect_tx(&h.b_full[stage], (uint32_t)kStageBytes);
-                            tma_load_2d(st, &mapA, &h.b_full[stage], ka * TKA, arow);
-                            tma_load_2d(st + kABytesPerAtom, &mapB, &h.b_full[stage], ka * TKA, p0);
-                            if (++stage == kStages) {
-                                stage = 0;
-                                sph ^= 1u;
-                            }
-                        }
-                    }
-                }
-            }
+            if (lane == 0 && !mbar_wait(&h.it_empty[ring], rph ^ 1u, abort)) ok = false;
             ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
             if (!ok) break;
+#pragma unroll
+            for (int q = 0; q < 4; q++) h.items[ring].row[q * 32 + lane] = rowd[q];
+            __threadfence_block();
+            __syncwarp();
+            if (lane == 0) {
+                pairs += (unsigned long long)nvr * (unsigned long long)(pb - pa);
+                ItemDesc& d = h.items[ring];
+                d.rt = rt;
+                d.pa = pa;
+                d.pb = pb;
+                d.dir = dir;
+                d.nct = (pb - pa + TBN - 1) / TBN;
+                mbar_arrive(&h.it_full[ring]);
+            }
+            if (++ring == kItemRing) {  // every lane keeps the ring position
+                ring = 0;
+                rph ^= 1u;
+            }
         }
         if (lane == 0) {
             if (!ok) {
@@ -345,6 +345,63 @@ __global__ void __launch_bounds__(kTcThreadsV2, 1)
                 mbar_arrive(&h.it_full[ring]);
             }
             if (pairs) atomicAdd(&a.ctrl->pairs, pairs);
+        }
+        __syncwarp();
+    } else if (warp == tma_warp) {
+        // ---------------- TMA producer ----------------
+        if (lane == 0) {
+            int stage = 0, ring = 0, cslot = 0;
+            uint32_t sph = 0, rph = 0, cph = 0;
+            bool ok = true;
+            for (;;) {
+                if (!mbar_wait(&h.it_full[ring], rph, abort)) {
+                    ok = false;
+                    break;
+                }
+                const int rt = h.items[ring].rt, pa = h.items[ring].pa, pb = h.items[ring].pb;
+                const int dir = h.items[ring].dir, nct = h.items[ring].nct;
+                mbar_arrive(&h.it_empty[ring]);
+                if (++ring == kItemRing) {
+                    ring = 0;
+                    rph ^= 1u;
+                }
+                if (nct < 0) break;
+                const int arow = rt * TBM + (a.a_direct ? off : 0);
+                for (int ct = 0; ct < nct && ok; ct++) {
+                    const int p0 = dir > 0 ? pa + ct * TBN : pb - (ct + 1) * TBN;
+                    // per-column constants of the tile (padded array: p0 >= -TBN, p0 + TBN <= N + TBN)
+                    if (!mbar_wait(&h.col_empty[cslot], cph ^ 1u, abort)) {
+                        ok = false;
+                        break;
+                    }
+                    mbar_expect_tx(&h.col_full[cslot], (uint32_t)(TBN * sizeof(float4)));
+                    bulk_load(&h.col[cslot][0], a.coldat + kColPad + p0, (uint32_t)(TBN * sizeof(float4)),
+                              &h.col_full[cslot]);
+                    if (++cslot == kColSlots) {
+                        cslot = 0;
+                        cph ^= 1u;
+                    }
+                    for (int ka = 0; ka < nka; ka++) {
+                        if (!mbar_wait(&h.b_empty[stage], sph ^ 1u, abort)) {
+                            ok = false;
+                            break;
+                        }
+                        unsigned char* st = stages + stage * kStageBytes;
+                        mbar_expect_tx(&h.b_full[stage], (uint32_t)kStageBytes);
+                        tma_load_2d(st, &mapA, &h.b_full[stage], ka * TKA, arow);
+                        tma_load_2d(st + kABytesPerAtom, &mapB, &h.b_full[stage], ka * TKA, p0);
+                        if (++stage == kStages) {
+                            stage = 0;
+                            sph ^= 1u;
+                        }
+                    }
+                }
+                if (!ok) break;
+            }
+            if (!ok) {
+                atomicExch(&a.ctrl->err, DD_ETIMEOUT);
+                *abort = 1;
+            }
         }
         __syncwarp();
     } else if (warp == 1) {
@@ -406,55 +463,31 @@ __global__ void __launch_bounds__(kTcThreadsV2, 1)
         }
         __syncwarp();
     } else {
-        // ---------------- epilogue ----------------
-        const int e = tid - 64;            // 0 .. kEpiThreads-1
+        // ---------------- epilogue (warps 2 .. 2 + kEpiWarps - 1) ----------------
         const int q = warp & 3;            // TMEM lane quarter
         const int half = (warp - 2) >> 2;  // column half of the tile
         const float neg2s = (float)(-2.0 / (a.stats[3] * a.stats[3]));  // s is a power of two: exact
-        int ring = 0, tb = 0;
-        uint32_t rph = 0;
-        uint32_t aph[2] = {0u, 0u}, cph[2] = {0u, 0u};
+        int ring = 0, tb = 0, cslot = 0;
+        uint32_t rph = 0, cph = 0;
+        uint32_t aph[2] = {0u, 0u};
         for (;;) {
             bool ok = mbar_wait(&h.it_full[ring], rph, abort);
             ok = __all_sync(0xffffffffu, ok);
             if (!ok) break;
-            const ItemDesc d = h.items[ring];
+            const int nct = h.items[ring].nct;
+            const float4 rd = h.items[ring].row[q * 32 + lane];
             mbar_arrive(&h.it_empty[ring]);
             if (++ring == kItemRing) {
                 ring = 0;
                 rph ^= 1u;
             }
-            if (d.nct < 0) break;
-            const int r = d.rt * TBM + q * 32 + lane;
-            const int ri = r < cnt ? a.rows.base[off + r] : -1;
-            float rmu = 0.f, rc = 0.f, Drun = INFINITY;
-            if (ri >= 0) {
-                rmu = a.rowmu[ri];
-                rc = a.rowc[ri];
-                Drun = __uint_as_float(a.rmin[ri]);
-            }
+            if (nct < 0) break;
+            const float rmu = rd.x, rc = rd.y;
+            const int ri = __float_as_int(rd.w);
+            float Drun = rd.z;
             const float Dlast = Drun;
-            for (int ct = 0; ct < d.nct; ct++) {
-                const int p0 = d.dir > 0 ? d.pa + ct * TBN : d.pb - (ct + 1) * TBN;
-                {
-                    const int c = e;  // kEpiThreads == TBN: one column each
-                    const int p = p0 + c;
-                    float4 cd;
-                    if (p >= d.pa && p < d.pb) {
-                        cd.x = a.colmu[p];
-                        cd.y = a.colc[p];
-                        cd.z = __int_as_float(a.sig[p]);
-                    } else {
-                        cd.x = 0.f;
-                        cd.y = INFINITY;
-                        cd.z = __int_as_float(-(1 << 30));
-                    }
-                    cd.w = 0.f;
-                    h.col[tb][c] = cd;
-                }
-                mbar_arrive(&h.col_ready[tb]);
-                bool okw = mbar_wait(&h.col_ready[tb], cph[tb], abort);
-                cph[tb] ^= 1u;
+            for (int ct = 0; ct < nct; ct++) {
+                bool okw = mbar_wait(&h.col_full[cslot], cph, abort);
                 okw = okw && mbar_wait(&h.acc_full[tb], aph[tb], abort);
                 aph[tb] ^= 1u;
                 okw = __all_sync(0xffffffffu, okw);  // tcgen05.ld is warp-wide
@@ -471,7 +504,7 @@ __global__ void __launch_bounds__(kTcThreadsV2, 1)
                     uint32_t v[32];
                     tmem_ld32(taddr + (uint32_t)(ch * 32), v);
                     tmem_ld_wait();
-                    const float4* cdp = &h.col[tb][half * (TBN / 2) + ch * 32];
+                    const float4* cdp = &h.col[cslot][half * (TBN / 2) + ch * 32];
 #pragma unroll
                     for (int x = 0; x < 32; x++) {
                         const float4 cd = cdp[x];
@@ -485,7 +518,12 @@ __global__ void __launch_bounds__(kTcThreadsV2, 1)
                 }
                 tc_fence_before();
                 mbar_arrive(&h.acc_empty[tb]);
+                mbar_arrive(&h.col_empty[cslot]);
                 tb ^= 1;
+                if (++cslot == kColSlots) {
+                    cslot = 0;
+                    cph ^= 1u;
+                }
                 Drun = fminf(Drun, fmaxf(m + rc, 0.f));
             }
             if (ri >= 0 && Drun < Dlast) atomicMin(a.rmin + ri, __float_as_uint(Drun));
@@ -511,7 +549,7 @@ __global__ void __launch_bounds__(kTcThreadsV2, 1)
 // c_i (FP32), sqrt(c_i) rounded up; maxima over all rows.
 __global__ void __launch_bounds__(256) k_tc_rowconst(const double* __restrict__ mu_w, const double* __restrict__ c_w,
                                                      const int32_t* __restrict__ sigpos, int64_t N, double sqrt_n,
-                                                     float* __restrict__ colmu, float* __restrict__ colc,
+                                                     float4* __restrict__ coldat,
                                                      float* __restrict__ rowmu, float* __restrict__ rowc,
                                                      float* __restrict__ rowsc, Ctrl* ctrl) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -523,20 +561,27 @@ __global__ void __launch_bounds__(256) k_tc_rowconst(const double* __restrict__ 
         sc = __fsqrt_ru(cc);
         am = fabsf(mu);
         const int p = sigpos[i];
-        colmu[p] = mu;
-        colc[p] = c;
+        coldat[kColPad + p] = make_float4(mu, c, __int_as_float((int)i), 0.f);
         rowmu[i] = mu;
         rowc[i] = c;
         rowsc[i] = sc;
     }
-    // non-negative floats order like their bit patterns
+    // non-negative floats order like their bit patterns; one atomic per block
+    __shared__ unsigned red[3][8];
     const unsigned bsc = __reduce_max_sync(0xffffffffu, __float_as_uint(sc));
     const unsigned bcc = __reduce_max_sync(0xffffffffu, __float_as_uint(cc));
     const unsigned bam = __reduce_max_sync(0xffffffffu, __float_as_uint(am));
     if ((threadIdx.x & 31) == 0) {
-        atomicMax(&ctrl->tc_scmax, bsc);
-        atomicMax(&ctrl->tc_cmax, bcc);
-        atomicMax(&ctrl->tc_mumax, bam);
+        red[0][threadIdx.x >> 5] = bsc;
+        red[1][threadIdx.x >> 5] = bcc;
+        red[2][threadIdx.x >> 5] = bam;
+    }
+    __syncthreads();
+    if (threadIdx.x < 3) {
+        unsigned v = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) v = max(v, red[threadIdx.x][w]);
+        unsigned int* dst = threadIdx.x == 0 ? &ctrl->tc_scmax : (threadIdx.x == 1 ? &ctrl->tc_cmax : &ctrl->tc_mumax);
+        atomicMax(dst, v);
     }
 }
 
@@ -592,22 +637,20 @@ template <typename T16>
 __global__ void __launch_bounds__(256) k_build_S(const float* __restrict__ t32, const double* __restrict__ mu_w,
                                                  const int32_t* __restrict__ sig, int64_t N, int n, int kpad,
                                                  const double* stats, T16* __restrict__ S) {
-    const int per_row = kpad / 8;
+    // one warp per row; lane l writes elements 2l, 2l+1 of every 64-element chunk
+    const int64_t p = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (p >= N) return;
+    const int lane = threadIdx.x & 31;
     const float s = (float)stats[3];
-    const int64_t total = N * per_row;
-    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t p = g / per_row;
-        const int k0 = (int)(g % per_row) * 8;
-        const int i = sig[p];
-        const float mu = (float)mu_w[i];
-        T16 v[8];
-#pragma unroll
-        for (int q = 0; q < 8; q++) {
-            const int k = k0 + q;
-            const float x = k < n ? (t32[i + k] - mu) * s : 0.f;
-            v[q] = to16(x, (T16*)nullptr);
-        }
-        *reinterpret_cast<uint4*>(S + p * kpad + k0) = *reinterpret_cast<uint4*>(v);
+    const int i = sig[p];
+    const float mu = (float)mu_w[i];
+    const float* x = t32 + i;
+    T16* row = S + p * kpad;
+    for (int k = 2 * lane; k < kpad; k += 64) {
+        const float x0 = k < n ? (x[k] - mu) * s : 0.f;
+        const float x1 = k + 1 < n ? (x[k + 1] - mu) * s : 0.f;
+        T16 v[2] = {to16(x0, (T16*)nullptr), to16(x1, (T16*)nullptr)};
+        *reinterpret_cast<uint32_t*>(row + k) = *reinterpret_cast<uint32_t*>(v);
     }
 }
 
@@ -675,6 +718,18 @@ bool make_map(CUtensorMap* map, void* base, int64_t rows, int kpad, int box_rows
 
 }  // namespace
 
+__global__ void k_coldat_pad(float4* coldat, int64_t N) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= 2 * kColPad) return;
+    const int64_t ix = t < kColPad ? t : N + t;  // [0, pad) and [pad + N, 2 pad + N)
+    coldat[ix] = make_float4(0.f, INFINITY, __int_as_float(-(1 << 30)), 0.f);
+}
+
+cudaError_t tc_init_plan(dd_plan_s* p) {
+    k_coldat_pad<<<(2 * kColPad + 255) / 256, 256>>>(p->coldat, p->N);
+    return cudaGetLastError();
+}
+
 size_t tc_smem_bytes(int kpad) {
     (void)kpad;
     return 1024 + (size_t)kStages * kStageBytes + sizeof(TcHdr);
@@ -703,12 +758,12 @@ cudaError_t launch_tc_prep(dd_plan_s* p, cudaStream_t s) {
     const bool bf16 = p->opt.precision == DD_TC_BF16;
     const int gN = (int)((N + 255) / 256);
     k_tc_scale<<<1, 32, 0, s>>>(p->stats, bf16 ? 1 : 0);
-    k_tc_rowconst<<<gN, 256, 0, s>>>(p->mu_w, p->c_w, p->sigpos, N, std::sqrt((double)n), p->colmu, p->colc,
-                                     p->rowmu, p->rowc, p->rowsc, p->ctrl);
+    k_tc_rowconst<<<gN, 256, 0, s>>>(p->mu_w, p->c_w, p->sigpos, N, std::sqrt((double)n), p->coldat, p->rowmu,
+                                     p->rowc, p->rowsc, p->ctrl);
     const float u_in = bf16 ? 0.00390625f : 0.00048828125f;
     k_tc_rowbound<<<gN, 256, 0, s>>>(p->rowsc, p->rowc, p->rowmu, N, (float)std::sqrt((double)n), u_in, p->stats,
                                      p->P2 + p->m, p->ctrl, p->alpha, p->gam, p->q2);
-    const int g = p->sm_count * 8;
+    const int g = (int)((N + 7) / 8);  // 8 rows (warps) per block
     if (bf16)
         k_build_S<__nv_bfloat16><<<g, 256, 0, s>>>(p->t32, p->mu_w, p->sig, N, n, p->kpad, p->stats,
                                                    reinterpret_cast<__nv_bfloat16*>(p->S16));

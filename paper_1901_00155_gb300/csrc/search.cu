@@ -428,8 +428,7 @@ struct Seq {
         t.a_direct = a_direct ? 1 : 0;
         t.a_row0 = 0;
         t.sig = p->sig;
-        t.colmu = p->colmu;
-        t.colc = p->colc;
+        t.coldat = p->coldat;
         t.rowmu = p->rowmu;
         t.rowc = p->rowc;
         t.alpha = p->alpha;
