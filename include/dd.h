@@ -80,7 +80,7 @@ typedef struct {
                               1 = PAA of the globally normalised values */
     int32_t phase1_max;    /* at most this many Cand rows run in phase 1 (default 4096) */
     int32_t refine_k;      /* rows with the largest first-wave upper bounds that get a full scan
-                              before the other survivors, to raise the best-so-far (default 512) */
+                              before the other survivors, to raise the best-so-far (default 128) */
     int32_t local_cols;    /* first wave: every row scans the rows of nearest window mean, this many
                               on each side of its tile (default 128) */
     int32_t word_cols;     /* same-word wave: survivors scan this many rows sharing their SAX word

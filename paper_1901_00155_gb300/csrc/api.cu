@@ -270,7 +270,7 @@ void dd_options_default(dd_options_t* opt) {
     opt->early_abandon = 1;
     opt->paa_mode = 0;
     opt->phase1_max = 4096;
-    opt->refine_k = 512;
+    opt->refine_k = 128;
     opt->local_cols = 128;
     opt->word_cols = 512;
 }

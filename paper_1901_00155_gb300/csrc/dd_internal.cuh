@@ -73,7 +73,9 @@ struct ListRef {
 //           its first row (Index_Word neighbourhood), starting half a word away;
 //   mode 2: each row tile scans its own range of the mean-bucketed order
 //           (ranges[t] = (L, H, C, segments)) in segments of seg_cols
-//           columns, alternating right / left of C, nearest first.
+//           columns, alternating right / left of C, nearest first;
+//   mode 3: (tensor-core form, list = the mean-bucketed order itself) row tile
+//           [q0, q0+128) against the 256 columns [q0-64, q0+192).
 struct ColSpec {
     int mode;
     int v_lo, v_hi;

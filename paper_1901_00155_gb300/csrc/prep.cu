@@ -293,22 +293,39 @@ __global__ void __launch_bounds__(256) k_sax(const double* __restrict__ P1, cons
     if (i >= N) return;
     const double mu = mu_w[i];
     const double c = c_w[i];
-    const double sd = sqrt(c * inv_n);
+    // The FP64 test lhs >= beta_j * scale is taken in FP32 when the two FP32
+    // sides differ by more than their rounding (<= 6 u32 of their magnitudes;
+    // 1e-6 used), which then gives the same answer; otherwise in FP64.
+    const float sd32 = sqrtf((float)(c * inv_n));
     int32_t h = 0;
     for (int s = 0; s < w; s++) {
         const int a = (int)(((int64_t)s * n) / w), b = (int)(((int64_t)(s + 1) * n) / w);
         const double len = (double)(b - a);
         const double seg = P1[i + b] - P1[i + a];
-        double lhs, scale;
+        double lhs;
+        float scale32;
+        const bool centred = paa_mode == 0 && c > 0.0;
         if (paa_mode == 0) {
-            lhs = (c > 0.0) ? seg - mu * len : 0.0;
-            scale = (c > 0.0) ? len * sd : 1.0;
+            lhs = centred ? fma(-mu, len, seg) : 0.0;
+            scale32 = centred ? (float)len * sd32 : 1.f;
         } else {
             lhs = seg;
-            scale = len;
+            scale32 = (float)len;
         }
+        const float lhs32 = (float)lhs;
         int letter = 0;
-        while (letter < A - 1 && lhs >= beta[letter] * scale) letter++;
+        while (letter < A - 1) {
+            const float thr32 = (float)beta[letter] * scale32;
+            bool ge;
+            if (fabsf(lhs32 - thr32) > 1e-6f * (fabsf(lhs32) + fabsf(thr32)) + 1e-37f) {
+                ge = lhs32 >= thr32;
+            } else {
+                const double scale = centred ? len * sqrt(c * inv_n) : (paa_mode == 0 ? 1.0 : len);
+                ge = lhs >= beta[letter] * scale;
+            }
+            if (!ge) break;
+            letter++;
+        }
         h = h * A + letter;
     }
     code[i] = h;
@@ -319,16 +336,30 @@ __device__ __forceinline__ int64_t seq_row(int64_t r, int64_t N, int64_t stride)
 }
 
 // ---- Eq. 8: word histogram, one block-local count per word -----------------
-__global__ void __launch_bounds__(1024) k_word_hist(const int32_t* __restrict__ code, int64_t N, int D,
-                                                    int32_t* __restrict__ hist, int32_t* __restrict__ blockcnt,
-                                                    int64_t stride) {
+// Keys of a counting sort: input element e is row in_perm[e] (or the stride
+// permutation seq_row(e)); its key is (keys[row] >> shift) & mask.
+struct KeySrc {
+    const int32_t* keys;
+    const int32_t* in_perm;
+    int64_t stride;
+    int shift;
+    int mask;
+};
+
+__device__ __forceinline__ int64_t key_row(const KeySrc& k, int64_t e, int64_t N) {
+    return k.in_perm ? (int64_t)k.in_perm[e] : seq_row(e, N, k.stride);
+}
+__device__ __forceinline__ int key_of(const KeySrc& k, int64_t row) { return (k.keys[row] >> k.shift) & k.mask; }
+
+__global__ void __launch_bounds__(1024) k_word_hist(KeySrc ks, int64_t N, int D, int32_t* __restrict__ hist,
+                                                    int32_t* __restrict__ blockcnt) {
     extern __shared__ int32_t sh_cnt[];
     for (int h = threadIdx.x; h < D; h += blockDim.x) sh_cnt[h] = 0;
     __syncthreads();
     const int64_t base = (int64_t)blockIdx.x * kHistRows;
     for (int r = threadIdx.x; r < kHistRows; r += blockDim.x) {
         const int64_t e = base + r;
-        if (e < N) atomicAdd(&sh_cnt[code[seq_row(e, N, stride)]], 1);
+        if (e < N) atomicAdd(&sh_cnt[key_of(ks, key_row(ks, e, N))], 1);
     }
     __syncthreads();
     for (int h = threadIdx.x; h < D; h += blockDim.x) {
@@ -338,26 +369,68 @@ __global__ void __launch_bounds__(1024) k_word_hist(const int32_t* __restrict__ 
     }
 }
 
-// Exclusive scan of column h of the [nblk][D] block-count matrix, starting at
-// `run`; loads are issued eight at a time so their latencies overlap.
-__device__ __forceinline__ void column_scan(int32_t* __restrict__ blockcnt, int D, int nblk, int h, int run) {
-    int b = 0;
-    for (; b + 8 <= nblk; b += 8) {
-        int c[8];
-#pragma unroll
-        for (int q = 0; q < 8; q++) c[q] = blockcnt[(int64_t)(b + q) * D + h];
-#pragma unroll
-        for (int q = 0; q < 8; q++) {
-            blockcnt[(int64_t)(b + q) * D + h] = run;
-            run += c[q];
+// Exclusive scan down each column h of the [nblk][D] block-count matrix,
+// starting at start[h]: 32 columns per block, the rows split in 16 chunks
+// (chunk sums, then a scan over the chunks, then the writes).
+constexpr int kColChunks = 16;
+__device__ __forceinline__ void colscan_cols(int32_t* __restrict__ blockcnt, int D, int nblk, int h, int c, int hl,
+                                             int start_h, int (*sh)[32]) {
+    const int CH = (nblk + kColChunks - 1) / kColChunks;
+    const int b0 = c * CH, b1 = min(nblk, b0 + CH);
+    int sum = 0;
+    if (h < D)
+        for (int b = b0; b < b1; b++) sum += blockcnt[(int64_t)b * D + h];
+    sh[c][hl] = sum;
+    __syncthreads();
+    int run = start_h;
+    for (int q = 0; q < c; q++) run += sh[q][hl];
+    if (h < D)
+        for (int b = b0; b < b1; b++) {
+            const int64_t ix = (int64_t)b * D + h;
+            const int v = blockcnt[ix];
+            blockcnt[ix] = run;
+            run += v;
+        }
+}
+
+__global__ void __launch_bounds__(32 * kColChunks) k_colscan(int32_t* __restrict__ blockcnt, int D, int nblk,
+                                                             const int32_t* __restrict__ start) {
+    __shared__ int sh[kColChunks][32];
+    const int hl = threadIdx.x, c = threadIdx.y;
+    const int h = blockIdx.x * 32 + hl;
+    colscan_cols(blockcnt, D, nblk, h, c, hl, h < D ? start[h] : 0, sh);
+}
+
+// Plan of one 64-bin radix pass: bin offsets (exclusive scan of the
+// histogram) and the block bases of every bin.  Two blocks of 32 bins.
+__global__ void __launch_bounds__(32 * kColChunks) k_radix_plan(const int32_t* __restrict__ hist,
+                                                                int32_t* __restrict__ blockcnt, int nblk) {
+    __shared__ int sh[kColChunks][32];
+    __shared__ int st[64];
+    if (threadIdx.y == 0 && threadIdx.x == 0) {
+        int run = 0;
+        for (int b = 0; b < 64; b++) {
+            st[b] = run;
+            run += hist[b];
         }
     }
-    for (; b < nblk; b++) {
-        const int64_t ix = (int64_t)b * D + h;
-        const int c = blockcnt[ix];
-        blockcnt[ix] = run;
-        run += c;
-    }
+    __syncthreads();
+    const int hl = threadIdx.x, c = threadIdx.y;
+    const int h = blockIdx.x * 32 + hl;
+    colscan_cols(blockcnt, 64, nblk, h, c, hl, st[h], sh);
+}
+
+// Bin offsets of the sorted mean order: binstart[b] = first position whose
+// row lies in bin >= b (binstart[kMuBins] = N).
+__global__ void __launch_bounds__(256) k_bin_bounds(const int32_t* __restrict__ sig, const int32_t* __restrict__ mubin,
+                                                    int64_t N, int32_t* __restrict__ binstart) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= N) return;
+    const int b1 = min(max(mubin[sig[p]], 0), kMuBins - 1);
+    const int b0 = p > 0 ? min(max(mubin[sig[p - 1]], 0), kMuBins - 1) : -1;
+    for (int b = b0 + 1; b <= b1; b++) binstart[b] = (int32_t)p;
+    if (p == N - 1)
+        for (int b = b1 + 1; b <= kMuBins; b++) binstart[b] = (int32_t)N;
 }
 
 // ---- Eq. 7 / Eq. 10 plan: words ordered by (frequency, word), offsets,
@@ -404,7 +477,8 @@ __global__ void __launch_bounds__(1024) k_word_plan(const int32_t* __restrict__ 
         const int fmin = sh_min;
         for (int r = 0; r < D; r++) {
             int h = (int)(keys[r] & 0xffffffffull);
-            int c = hist[h];
+            unsigned long long fk = keys[r] >> 32;
+            int c = fk == 0xffffffffull ? 0 : (int)fk;  // the sort key holds the frequency
             word_start[h] = run;
             run += c;
             if (c == fmin) ncand += c;
@@ -416,18 +490,17 @@ __global__ void __launch_bounds__(1024) k_word_plan(const int32_t* __restrict__ 
         ctrl->n2 = (int)(N - n1);
     }
     __syncthreads();
-    for (int h = threadIdx.x; h < D; h += blockDim.x) column_scan(blockcnt, D, nblk, h, word_start[h]);
+    (void)blockcnt;
+    (void)nblk;
 }
 
 // ---- Eq. 10: stable scatter of rows into word order ------------------------
 // Block b handles rows [b*kHistRows, (b+1)*kHistRows); warp w a contiguous
 // slice of it; ranks inside a round of 32 rows come from __match_any_sync.
-// Input element r is row seq_row(r): the identity (stride 0) or a stride
-// permutation r -> r * stride mod N (gcd(stride, N) = 1), which makes the rows of
-// a bucket follow that permutation instead of their index order.
-__global__ void k_word_scatter(const int32_t* __restrict__ code, int64_t N, int D,
-                               const int32_t* __restrict__ blockbase, int32_t* __restrict__ order,
-                               int32_t* __restrict__ pos_of, int64_t stride) {
+// Stable scatter: element e (in input order) of key h goes to position
+// (block base of h) + (rank of e among the block's elements of key h).
+__global__ void k_word_scatter(KeySrc ks, int64_t N, int D, const int32_t* __restrict__ blockbase,
+                               int32_t* __restrict__ order, int32_t* __restrict__ pos_of) {
     extern __shared__ int32_t sh_wc[];  // [nwarps][D]
     const int nw = blockDim.x >> 5;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -438,7 +511,7 @@ __global__ void k_word_scatter(const int32_t* __restrict__ code, int64_t N, int 
     int32_t* wc = sh_wc + wid * D;
     for (int r = lane; r < per; r += 32) {
         const int64_t e = base + r;
-        if (e < N) atomicAdd(&wc[code[seq_row(e, N, stride)]], 1);
+        if (e < N) atomicAdd(&wc[key_of(ks, key_row(ks, e, N))], 1);
     }
     __syncthreads();
     for (int h = threadIdx.x; h < D; h += blockDim.x) {
@@ -454,8 +527,8 @@ __global__ void k_word_scatter(const int32_t* __restrict__ code, int64_t N, int 
     for (int r0 = 0; r0 < per; r0 += 32) {
         const int64_t e = base + r0 + lane;
         bool ok = (r0 + lane < per) && (e < N);
-        const int64_t i = ok ? seq_row(e, N, stride) : 0;
-        int h = ok ? code[i] : -1 - lane;  // unique dummy keys for idle lanes
+        const int64_t i = ok ? key_row(ks, e, N) : 0;
+        int h = ok ? key_of(ks, i) : -1 - lane;  // unique dummy keys for idle lanes
         unsigned peers = __match_any_sync(0xffffffffu, h);
         int rank = __popc(peers & lt);
         int b = ok ? wc[h] : 0;
@@ -463,7 +536,7 @@ __global__ void k_word_scatter(const int32_t* __restrict__ code, int64_t N, int 
         if (ok) {
             int pos = b + rank;
             order[pos] = (int32_t)i;
-            pos_of[i] = pos;
+            if (pos_of) pos_of[i] = pos;
             if (rank == 0) wc[h] = b + __popc(peers);
         }
         __syncwarp();
@@ -480,54 +553,8 @@ __global__ void __launch_bounds__(256) k_mu_bins(const double* __restrict__ mu_w
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     const double b = floor((mu_w[i] - stats[6]) * stats[9]);
-    bin[i] = b < 0.0 ? 0 : (b >= (double)kMuBins ? kMuBins - 1 : (int)b);
-}
-
-// Bin order plan, part 1: bin offsets (exclusive scan of the histogram in bin
-// order).  One block; each thread a run of consecutive bins.
-__global__ void __launch_bounds__(1024) k_bin_scan(const int32_t* __restrict__ hist, int D,
-                                                   int32_t* __restrict__ binstart) {
-    __shared__ int32_t part[1024];
-    const int per = (D + 1023) / 1024;
-    const int lo = threadIdx.x * per, hi = min(D, lo + per);
-    int s = 0;
-    for (int h = lo; h < hi; h++) s += hist[h];
-    // block exclusive scan of the per-thread sums (warp scans + one pass over warp totals)
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    int incl = s;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int u = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += u;
-    }
-    if (lane == 31) part[wid] = incl;
-    __syncthreads();
-    if (wid == 0) {
-        const int v = part[lane];
-        int c = v;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int u = __shfl_up_sync(0xffffffffu, c, o);
-            if (lane >= o) c += u;
-        }
-        part[lane] = c - v;
-        if (lane == 31) binstart[D] = c;
-    }
-    __syncthreads();
-    int run = part[wid] + incl - s;
-    for (int h = lo; h < hi; h++) {
-        binstart[h] = run;
-        run += hist[h];
-    }
-}
-
-// Part 2: each block's base offset per bin (column scan of the block counts),
-// one thread per bin.
-__global__ void __launch_bounds__(256) k_bin_bases(int D, int nblk, const int32_t* __restrict__ binstart,
-                                                   int32_t* __restrict__ blockcnt) {
-    const int h = blockIdx.x * blockDim.x + threadIdx.x;
-    if (h >= D) return;
-    column_scan(blockcnt, D, nblk, h, binstart[h]);
+    // NaN (non-finite series) and out-of-range values land in the end bins
+    bin[i] = (b >= 0.0) ? (b < (double)kMuBins ? (int)b : kMuBins - 1) : 0;
 }
 
 // Warps per block of the stable scatter: per-warp counters for every word
@@ -566,23 +593,30 @@ cudaError_t launch_prep(dd_plan_s* p, const float* T, cudaStream_t s) {
                              p->opt.paa_mode, p->beta, p->code);
     const int nh = (int)((N + kHistRows - 1) / kHistRows);
     cudaMemsetAsync(p->hist, 0, sizeof(int32_t) * D, s);
-    k_word_hist<<<nh, 1024, sizeof(int32_t) * D, s>>>(p->code, N, D, p->hist, p->blockcnt, 0);
+    const KeySrc words{p->code, nullptr, 0, 0, 0x7fffffff};
+    k_word_hist<<<nh, 1024, sizeof(int32_t) * D, s>>>(words, N, D, p->hist, p->blockcnt);
     k_word_plan<<<1, 1024, 0, s>>>(p->hist, D, nh, p->blockcnt, p->word_start, p->opt.phase1_max, N, p->ctrl);
+    k_colscan<<<(D + 31) / 32, dim3(32, kColChunks), 0, s>>>(p->blockcnt, D, nh, p->word_start);
     int nw = scatter_warps(D);
-    k_word_scatter<<<nh, nw * 32, sizeof(int32_t) * nw * D, s>>>(p->code, N, D, p->blockcnt, p->order, p->pos_of, 0);
-    // mean-bucketed order (sig) with bin offsets
+    k_word_scatter<<<nh, nw * 32, sizeof(int32_t) * nw * D, s>>>(words, N, D, p->blockcnt, p->order, p->pos_of);
+    // mean-bucketed order (sig): rows sorted by mean bin with two stable 64-bin
+    // radix passes; the input follows a golden-ratio stride permutation, so the
+    // rows of a bin are not in time order and neighbours in this order are
+    // seldom overlapping subsequences
     k_mu_bins<<<gN, 256, 0, s>>>(p->mu_w, N, p->stats, p->mubin);
-    cudaMemsetAsync(p->hist_mu, 0, sizeof(int32_t) * kMuBins, s);
-    // rows of a mean bin follow a golden-ratio stride permutation, not time, so
-    // that neighbours in this order are seldom overlapping subsequences
-    k_word_hist<<<nh, 1024, sizeof(int32_t) * kMuBins, s>>>(p->mubin, N, kMuBins, p->hist_mu, p->blockcnt_mu,
-                                                            p->mu_stride);
-    k_bin_scan<<<1, 1024, 0, s>>>(p->hist_mu, kMuBins, p->binstart);
-    k_bin_bases<<<(kMuBins + 255) / 256, 256, 0, s>>>(kMuBins, nh, p->binstart, p->blockcnt_mu);
-    const int nw2 = scatter_warps(kMuBins);
-    k_word_scatter<<<nh, nw2 * 32, sizeof(int32_t) * nw2 * kMuBins, s>>>(p->mubin, N, kMuBins, p->blockcnt_mu, p->sig,
-                                                                        p->sigpos, p->mu_stride);
-    p->launches += 17;
+    int32_t* tmp = p->list[3];
+    const int nw64 = scatter_warps(64);
+    for (int pass = 0; pass < 2; pass++) {
+        const KeySrc ks{p->mubin, pass == 0 ? nullptr : tmp, pass == 0 ? p->mu_stride : 0, 6 * pass, 63};
+        cudaMemsetAsync(p->hist_mu, 0, sizeof(int32_t) * 64, s);
+        k_word_hist<<<nh, 1024, sizeof(int32_t) * 64, s>>>(ks, N, 64, p->hist_mu, p->blockcnt_mu);
+        k_radix_plan<<<2, dim3(32, kColChunks), 0, s>>>(p->hist_mu, p->blockcnt_mu, nh);
+        k_word_scatter<<<nh, nw64 * 32, sizeof(int32_t) * nw64 * 64, s>>>(ks, N, 64, p->blockcnt_mu,
+                                                                          pass == 0 ? tmp : p->sig,
+                                                                          pass == 0 ? nullptr : p->sigpos);
+    }
+    k_bin_bounds<<<gN, 256, 0, s>>>(p->sig, p->mubin, N, p->binstart);
+    p->launches += 20;
     return cudaGetLastError();
 }
 

@@ -30,7 +30,7 @@ __device__ __forceinline__ void lb_range(float R, int i, int n, int N, const dou
     }
     const double h = sqrt((double)R / (double)n) * (1.0 + 1e-4) + 1e-12;
     const double kb = ceil(h / w) + 1.0;
-    const int k = kb > (double)kMuBins ? kMuBins : (int)kb;
+    const int k = kb < (double)kMuBins ? (int)kb : kMuBins;  // NaN -> every bin
     const int b = mubin[i];
     L = binstart[b - k < 0 ? 0 : b - k];
     H = binstart[b + k + 1 > kMuBins ? kMuBins : b + k + 1];

@@ -201,6 +201,13 @@ __device__ __forceinline__ void item_geometry(const TcArgs& a, int item, int RT,
             pa = max(pb - a.seg_cols, r.x);
             dir = -1;
         }
+    } else if (a.mode == 3) {
+        // band: the row tile [q0, q0 + 128) of the mean-ordered list against the
+        // 256 columns [q0 - 64, q0 + 192) around it (the A rows lie inside that B tile)
+        rt = item;
+        pa = rt * TBM - (TBN - TBM) / 2;
+        pb = pa + TBN;
+        dir = 1;
     } else {
         // column-segment major: concurrent CTAs share the same operand columns through L2
         const int sg = item / RT;
@@ -239,6 +246,8 @@ __global__ void __launch_bounds__(kTcThreadsV2, 1)
         const int smax = *a.smax;
         if (smax <= 0) return;
         items = (long long)RT * smax;
+    } else if (a.mode == 3) {
+        items = RT;
     } else {
         nseg0 = (a.N + a.seg_cols - 1) / a.seg_cols;
         items = (long long)RT * nseg0;
@@ -276,6 +285,7 @@ __global__ void __launch_bounds__(kTcThreadsV2, 1)
     volatile int* abort = &h.abort;
     const int n = a.n;
     const int nka = a.nka;
+    const bool band = a.mode == 3;
 
     const int tma_warp = 2 + kEpiWarps;
     if (warp == 0) {
@@ -387,8 +397,12 @@ __global__ void __launch_bounds__(kTcThreadsV2, 1)
                             break;
                         }
                         unsigned char* st = stages + stage * kStageBytes;
-                        mbar_expect_tx(&h.b_full[stage], (uint32_t)kStageBytes);
-                        tma_load_2d(st, &mapA, &h.b_full[stage], ka * TKA, arow);
+                        if (band) {  // A rows come from inside the B tile
+                            mbar_expect_tx(&h.b_full[stage], (uint32_t)kBBytesPerAtom);
+                        } else {
+                            mbar_expect_tx(&h.b_full[stage], (uint32_t)kStageBytes);
+                            tma_load_2d(st, &mapA, &h.b_full[stage], ka * TKA, arow);
+                        }
                         tma_load_2d(st + kABytesPerAtom, &mapB, &h.b_full[stage], ka * TKA, p0);
                         if (++stage == kStages) {
                             stage = 0;
@@ -437,7 +451,8 @@ __global__ void __launch_bounds__(kTcThreadsV2, 1)
                         }
                         tc_fence_after();
                         const uint32_t sa = smem_u32(stages + stage * kStageBytes);
-                        const uint64_t ad = sw128_desc(sa);
+                        // band mode: A = B rows [64, 192), 8 KB into the B tile (a whole number of 1 KB swizzle atoms)
+                        const uint64_t ad = sw128_desc(band ? sa + kABytesPerAtom + (TBN - TBM) / 2 * 128 : sa);
                         const uint64_t bd = sw128_desc(sa + kABytesPerAtom);
 #pragma unroll
                         for (int kk = 0; kk < TKA / 16; kk++)
@@ -637,20 +652,37 @@ template <typename T16>
 __global__ void __launch_bounds__(256) k_build_S(const float* __restrict__ t32, const double* __restrict__ mu_w,
                                                  const int32_t* __restrict__ sig, int64_t N, int n, int kpad,
                                                  const double* stats, T16* __restrict__ S) {
-    // one warp per row; lane l writes elements 2l, 2l+1 of every 64-element chunk
-    const int64_t p = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (p >= N) return;
+    // one warp per 4 rows (their loads are issued together)
+    constexpr int R = 4;
+    const int64_t p0 = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * R;
+    if (p0 >= N) return;
     const int lane = threadIdx.x & 31;
     const float s = (float)stats[3];
-    const int i = sig[p];
-    const float mu = (float)mu_w[i];
-    const float* x = t32 + i;
-    T16* row = S + p * kpad;
+    int ii[R];
+    float mu[R];
+#pragma unroll
+    for (int r = 0; r < R; r++) {
+        const int64_t p = p0 + r < N ? p0 + r : N - 1;
+        ii[r] = sig[p];
+    }
+#pragma unroll
+    for (int r = 0; r < R; r++) mu[r] = (float)mu_w[ii[r]];
+    // lane l writes elements 2l, 2l+1 of every 64-element chunk (4-byte stores)
     for (int k = 2 * lane; k < kpad; k += 64) {
-        const float x0 = k < n ? (x[k] - mu) * s : 0.f;
-        const float x1 = k + 1 < n ? (x[k + 1] - mu) * s : 0.f;
-        T16 v[2] = {to16(x0, (T16*)nullptr), to16(x1, (T16*)nullptr)};
-        *reinterpret_cast<uint32_t*>(row + k) = *reinterpret_cast<uint32_t*>(v);
+        float x0[R], x1[R];
+#pragma unroll
+        for (int r = 0; r < R; r++) {
+            x0[r] = k < n ? t32[ii[r] + k] : 0.f;
+            x1[r] = k + 1 < n ? t32[ii[r] + k + 1] : 0.f;
+        }
+#pragma unroll
+        for (int r = 0; r < R; r++) {
+            if (p0 + r >= N) break;
+            const float y0 = k < n ? (x0[r] - mu[r]) * s : 0.f;
+            const float y1 = k + 1 < n ? (x1[r] - mu[r]) * s : 0.f;
+            T16 v[2] = {to16(y0, (T16*)nullptr), to16(y1, (T16*)nullptr)};
+            *reinterpret_cast<uint32_t*>(S + (p0 + r) * kpad + k) = *reinterpret_cast<uint32_t*>(v);
+        }
     }
 }
 
@@ -763,7 +795,7 @@ cudaError_t launch_tc_prep(dd_plan_s* p, cudaStream_t s) {
     const float u_in = bf16 ? 0.00390625f : 0.00048828125f;
     k_tc_rowbound<<<gN, 256, 0, s>>>(p->rowsc, p->rowc, p->rowmu, N, (float)std::sqrt((double)n), u_in, p->stats,
                                      p->P2 + p->m, p->ctrl, p->alpha, p->gam, p->q2);
-    const int g = (int)((N + 7) / 8);  // 8 rows (warps) per block
+    const int g = (int)((N + 31) / 32);  // 8 warps x 4 rows per block
     if (bf16)
         k_build_S<__nv_bfloat16><<<g, 256, 0, s>>>(p->t32, p->mu_w, p->sig, N, n, p->kpad, p->stats,
                                                    reinterpret_cast<__nv_bfloat16*>(p->S16));

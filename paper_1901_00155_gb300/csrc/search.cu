@@ -260,7 +260,7 @@ __global__ void __launch_bounds__(128) k_tile_ranges(ListRef L, int kind, int K,
             } else {
                 const double h = sqrt((double)R / (double)n) * (1.0 + 1e-4) + 1e-12;
                 const double kb = ceil(h / w) + 1.0;
-                const int k = kb > (double)kMuBins ? kMuBins : (int)kb;
+                const int k = kb < (double)kMuBins ? (int)kb : kMuBins;  // NaN -> every bin
                 const int b = mubin[i];
                 lo = binstart[b - k < 0 ? 0 : b - k];
                 hi = binstart[b + k + 1 > kMuBins ? kMuBins : b + k + 1];
@@ -423,7 +423,7 @@ struct Seq {
         t.nka = p->kpad / 64;
         t.stages = tc_stages(p->kpad);
         t.seg_cols = kSegCols;
-        t.mode = col.mode == 2 ? 2 : 0;
+        t.mode = col.mode == 2 || col.mode == 3 ? col.mode : 0;
         t.rows = rows;
         t.a_direct = a_direct ? 1 : 0;
         t.a_row0 = 0;
@@ -528,8 +528,13 @@ cudaError_t launch_search(dd_plan_s* p, const float* T, dd_result_t* out_dev, cu
     } else {
         // Upper bounds for every row from its nearest-mean neighbourhood.
         if (o.local_cols > 0) {
-            const int* sm = q.ranges(all, 0, o.local_cols);
-            q.scan(all, ColSpec{2, 0, 0, 0}, 1, sm, true);
+            if (q.tc) {
+                // tensor-core form: one 128 x 256 band tile per row tile
+                q.scan(all, ColSpec{3, 0, 0, 0}, 1, nullptr, true);
+            } else {
+                const int* sm = q.ranges(all, 0, o.local_cols);
+                q.scan(all, ColSpec{2, 0, 0, 0}, 1, sm, true);
+            }
         }
         // Algorithm 3 (PotentialDiscord): the Cand rows (rarest SAX words).
         ListRef cand = q.compact(all, p->list[0], 2);
