@@ -367,13 +367,15 @@ dd_status_t dd_plan_create(dd_plan_t* plan, int64_t m, int32_t n, const dd_optio
         k_iota<<<(unsigned)((p->N + 255) / 256), 256>>>(p->seq_rows, p->N);
         e = cudaGetLastError();
     }
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->side_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming);
     if (e == cudaSuccess && o.precision != DD_FP32) e = dd::tc_make_maps(p);
     if (e == cudaSuccess && o.precision != DD_FP32) e = dd::tc_init_plan(p);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
-        cudaFreeHost(p->res_host);
-        if (p->own_ws) cudaFree(p->ws);
-        delete p;
+        cudaGetLastError();
+        dd_plan_destroy(p);
         return from_cuda(e);
     }
     *plan = p;
@@ -385,6 +387,9 @@ void dd_plan_destroy(dd_plan_t p) {
     cudaDeviceSynchronize();
     if (p->gexec) cudaGraphExecDestroy(p->gexec);
     if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
+    if (p->side_stream) cudaStreamDestroy(p->side_stream);
+    if (p->ev_fork) cudaEventDestroy(p->ev_fork);
+    if (p->ev_join) cudaEventDestroy(p->ev_join);
     for (cudaEvent_t e : p->ev) cudaEventDestroy(e);
     for (cudaEvent_t e : p->call_ev)
         if (e) cudaEventDestroy(e);

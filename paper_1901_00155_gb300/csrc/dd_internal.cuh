@@ -243,6 +243,8 @@ struct dd_plan_s {
     // captured search graph (replayed while the input/output pointers and the
     // profiling switch stay the same)
     cudaStream_t cap_stream = nullptr;
+    cudaStream_t side_stream = nullptr;  // SAX / word order run here, beside the mean order
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     cudaGraphExec_t gexec = nullptr;
     const void* g_T = nullptr;
     const void* g_out = nullptr;
@@ -265,6 +267,9 @@ namespace dd {
 
 // prep.cu
 cudaError_t launch_prep(dd_plan_s* p, const float* T, cudaStream_t s);
+cudaError_t launch_prep_common(dd_plan_s* p, const float* T, cudaStream_t s);
+cudaError_t launch_prep_words(dd_plan_s* p, cudaStream_t s);
+cudaError_t launch_prep_mean(dd_plan_s* p, cudaStream_t s);
 // search.cu
 cudaError_t launch_search(dd_plan_s* p, const float* T, dd_result_t* out_dev, cudaStream_t s);
 cudaError_t launch_profile(dd_plan_s* p, const float* T, const int32_t* rows, int count, float* nn2,

@@ -570,12 +570,12 @@ int scatter_warps(int D) {
 
 }  // namespace
 
-cudaError_t launch_prep(dd_plan_s* p, const float* T, cudaStream_t s) {
+// Preparation, part 1: Eq. 2 statistics, normalisation, prefix sums, row statistics.
+cudaError_t launch_prep_common(dd_plan_s* p, const float* T, cudaStream_t s) {
     cudaError_t ea = cudaFuncSetAttribute(k_word_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, 192 * 1024);
     if (ea != cudaSuccess) return ea;
     const int64_t m = p->m, N = p->N;
     const int n = p->n;
-    const int D = p->D;
     int nb = (int)((m + 2047) / 2048);
     if (nb > kStatBlocks) nb = kStatBlocks;
     if (nb < 1) nb = 1;
@@ -589,6 +589,16 @@ cudaError_t launch_prep(dd_plan_s* p, const float* T, cudaStream_t s) {
     k_norm_prefix<<<nscan, 1024, 0, s>>>(p->t64, m, p->bsum, nscan, p->P1, p->P2);
     const int gN = (int)((N + 255) / 256);
     k_window_stats<<<gN, 256, 0, s>>>(p->P1, p->P2, N, n, 1.0 / (double)n, p->mu_w, p->c_w);
+    p->launches += 8;
+    return cudaGetLastError();
+}
+
+// Part 2: SAX words (Eq. 3, 4, 9), Freq / Cand / Index_Word (Eq. 7, 8, 10).
+cudaError_t launch_prep_words(dd_plan_s* p, cudaStream_t s) {
+    const int64_t N = p->N;
+    const int n = p->n;
+    const int D = p->D;
+    const int gN = (int)((N + 255) / 256);
     k_sax<<<gN, 256, 0, s>>>(p->P1, p->mu_w, p->c_w, N, n, 1.0 / (double)n, p->opt.paa_w, p->opt.alphabet,
                              p->opt.paa_mode, p->beta, p->code);
     const int nh = (int)((N + kHistRows - 1) / kHistRows);
@@ -599,6 +609,15 @@ cudaError_t launch_prep(dd_plan_s* p, const float* T, cudaStream_t s) {
     k_colscan<<<(D + 31) / 32, dim3(32, kColChunks), 0, s>>>(p->blockcnt, D, nh, p->word_start);
     int nw = scatter_warps(D);
     k_word_scatter<<<nh, nw * 32, sizeof(int32_t) * nw * D, s>>>(words, N, D, p->blockcnt, p->order, p->pos_of);
+    p->launches += 5;
+    return cudaGetLastError();
+}
+
+// Part 3: the mean-bucketed order and its bin offsets.
+cudaError_t launch_prep_mean(dd_plan_s* p, cudaStream_t s) {
+    const int64_t N = p->N;
+    const int gN = (int)((N + 255) / 256);
+    const int nh = (int)((N + kHistRows - 1) / kHistRows);
     // mean-bucketed order (sig): rows sorted by mean bin with two stable 64-bin
     // radix passes; the input follows a golden-ratio stride permutation, so the
     // rows of a bin are not in time order and neighbours in this order are
@@ -616,8 +635,15 @@ cudaError_t launch_prep(dd_plan_s* p, const float* T, cudaStream_t s) {
                                                                           pass == 0 ? nullptr : p->sigpos);
     }
     k_bin_bounds<<<gN, 256, 0, s>>>(p->sig, p->mubin, N, p->binstart);
-    p->launches += 20;
+    p->launches += 8;
     return cudaGetLastError();
+}
+
+cudaError_t launch_prep(dd_plan_s* p, const float* T, cudaStream_t s) {
+    cudaError_t e = launch_prep_common(p, T, s);
+    if (e == cudaSuccess) e = launch_prep_words(p, s);
+    if (e == cudaSuccess) e = launch_prep_mean(p, s);
+    return e;
 }
 
 // Breakpoints of the SAX alphabet (text after Eq. 4): Phi(beta_j) = j / A for

@@ -665,8 +665,10 @@ __global__ void __launch_bounds__(256) k_build_S(const float* __restrict__ t32, 
         const int64_t p = p0 + r < N ? p0 + r : N - 1;
         ii[r] = sig[p];
     }
+    // one FP64 -> FP32 conversion per row (FP64 throughput is low on this GPU)
+    const float mu_l = lane < R ? (float)mu_w[ii[lane < R ? lane : 0]] : 0.f;
 #pragma unroll
-    for (int r = 0; r < R; r++) mu[r] = (float)mu_w[ii[r]];
+    for (int r = 0; r < R; r++) mu[r] = __shfl_sync(0xffffffffu, mu_l, r);
     // lane l writes elements 2l, 2l+1 of every 64-element chunk (4-byte stores)
     for (int k = 2 * lane; k < kpad; k += 64) {
         float x0[R], x1[R];

@@ -514,13 +514,27 @@ cudaError_t launch_search(dd_plan_s* p, const float* T, dd_result_t* out_dev, cu
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(p->rmin, 0x7f, sizeof(uint32_t) * p->N, s);
     if (e != cudaSuccess) return e;
-    e = launch_prep(p, T, s);
+    e = launch_prep_common(p, T, s);
+    if (e != cudaSuccess) return e;
+    // The SAX words and the word order (needed from Algorithm 3 on) are built on
+    // a side stream while the mean order, the operand matrix and the first wave
+    // run here.
+    e = cudaEventRecord(p->ev_fork, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(p->side_stream, p->ev_fork, 0);
+    if (e == cudaSuccess) e = launch_prep_words(p, p->side_stream);
+    if (e == cudaSuccess) e = cudaEventRecord(p->ev_join, p->side_stream);
+    if (e == cudaSuccess) e = launch_prep_mean(p, s);
     if (e != cudaSuccess) return e;
 
     Seq q(p, s);
     if (q.tc) q.keep(launch_tc_prep(p, s));
     const dd_options_t& o = p->opt;
     ListRef all = q.constant_list(p->sig, (int)p->N);  // every row, mean-bucketed order
+    bool joined = false;
+    auto join = [&]() {
+        if (!joined) q.keep(cudaStreamWaitEvent(s, p->ev_join, 0));
+        joined = true;
+    };
     if (!o.early_abandon) {
         // every row scans every column; the argmax runs over all rows
         q.scan(all, ColSpec{0, 0, (int)p->N, 0}, 0, nullptr, true);
@@ -536,6 +550,7 @@ cudaError_t launch_search(dd_plan_s* p, const float* T, dd_result_t* out_dev, cu
                 q.scan(all, ColSpec{2, 0, 0, 0}, 1, sm, true);
             }
         }
+        join();
         // Algorithm 3 (PotentialDiscord): the Cand rows (rarest SAX words).
         ListRef cand = q.compact(all, p->list[0], 2);
         q.full(cand);
@@ -557,6 +572,7 @@ cudaError_t launch_search(dd_plan_s* p, const float* T, dd_result_t* out_dev, cu
         ListRef rest = q.compact(alive, p->list[2], 0);
         q.full(rest);
     }
+    join();
     if (q.tc) {
         // every row the bound cannot rule out, rescored exactly in FP64
         ListRef cands = q.compact(all, p->list[3], 0);
