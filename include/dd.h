@@ -206,6 +206,40 @@ typedef struct {
 DD_API dd_status_t dd_plan_set_profiling(dd_plan_t plan, int32_t enable);
 DD_API dd_status_t dd_plan_get_profile(dd_plan_t plan, dd_profile_t* out);
 
+/* Waves of distance tiles of the last call (tracing).  A search runs its
+ * rows through a fixed sequence of waves (Algorithm 2): the nearest-mean
+ * neighbourhood of every row (LOCAL in the FP32 form, BAND in the tensor-core
+ * form), the Cand rows of Algorithm 3 (CAND), the rows with the largest upper
+ * bounds (TOP), the rows of a word (WORD, FP32 form) and the rest of
+ * Algorithm 4 (REST); exhaustive calls run EXHAUSTIVE waves. */
+typedef enum {
+    DD_WAVE_EXHAUSTIVE = 0,
+    DD_WAVE_LOCAL = 1,
+    DD_WAVE_BAND = 2,
+    DD_WAVE_CAND = 3,
+    DD_WAVE_TOP = 4,
+    DD_WAVE_WORD = 5,
+    DD_WAVE_REST = 6
+} dd_wave_kind_t;
+
+typedef struct {
+    int32_t kind;      /* dd_wave_kind_t */
+    int32_t rows;      /* rows in the wave's list */
+    int64_t items;     /* work items run (items whose rows were all abandoned, or
+                          that no row's lower bound admits, are skipped) */
+    int64_t pairs;     /* (row, column) distance pairs evaluated */
+    double ms;         /* duration from CUDA events on the call's stream when
+                          profiling is enabled (dd_plan_set_profiling), else -1 */
+} dd_wave_t;
+
+/* Copies up to `cap` waves of the plan's last call into out[] (host memory)
+ * and returns how many waves that call ran (which may exceed cap), or a
+ * negative dd_status_t (-DD_EINVAL for a null plan or out with cap > 0,
+ * -DD_EBUSY while a call is in flight, -DD_ECUDA).  Reads the plan's
+ * device-side counters: call it after the call has finished (synchronous
+ * calls, or after synchronising the stream of an asynchronous one). */
+DD_API int32_t dd_plan_get_waves(dd_plan_t plan, dd_wave_t* out, int32_t cap);
+
 /* Exhaustive nearest-neighbour profile without any device allocation.
  * The paper has no counterpart to this entry point; it exists for callers
  * that may not allocate device memory at the time of the call -- code running

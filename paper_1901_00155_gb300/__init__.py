@@ -225,6 +225,17 @@ class Plan:
         return {"dist_launches": int(pr.dist_launches), "precision": int(pr.precision), "dist_ms": float(pr.dist_ms),
                 "computed_pairs": int(pr.computed_pairs), "call_ms": float(pr.call_ms)}
 
+    def waves(self) -> list:
+        """Waves of distance tiles of the last call: kind, rows, items run, pairs
+        evaluated and (with set_profiling) duration in ms, else -1."""
+        cap = 64
+        buf = (_lib.Wave * cap)()
+        nw = int(self._lib.dd_plan_get_waves(self._ptr, buf, cap))
+        if nw < 0:
+            _check(-nw, "dd_plan_get_waves")
+        return [{"kind": _lib.WAVE_KINDS.get(int(w.kind), str(int(w.kind))), "rows": int(w.rows),
+                 "items": int(w.items), "pairs": int(w.pairs), "ms": float(w.ms)} for w in buf[:min(nw, cap)]]
+
 
 def find_discord(T, n: int, precision="fp32", stream=None, **opts) -> DiscordResult:
     """One-shot search (creates and destroys a plan)."""

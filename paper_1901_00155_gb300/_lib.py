@@ -40,6 +40,13 @@ class Profile(ctypes.Structure):
                 ("computed_pairs", ctypes.c_int64), ("call_ms", ctypes.c_double), ("reserved", ctypes.c_int64 * 4)]
 
 
+class Wave(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("rows", ctypes.c_int32), ("items", ctypes.c_int64),
+                ("pairs", ctypes.c_int64), ("ms", ctypes.c_double)]
+
+
+WAVE_KINDS = {0: "exhaustive", 1: "local", 2: "band", 3: "cand", 4: "top", 5: "word", 6: "rest"}
+
 _lock = threading.Lock()
 _lib = None
 
@@ -66,6 +73,7 @@ SIGNATURES = {
     "dd_status_string": ([ctypes.c_int], ctypes.c_char_p),
     "dd_plan_set_profiling": ([ctypes.c_void_p, ctypes.c_int32], ctypes.c_int),
     "dd_plan_get_profile": ([ctypes.c_void_p, ctypes.POINTER(Profile)], ctypes.c_int),
+    "dd_plan_get_waves": ([ctypes.c_void_p, ctypes.POINTER(Wave), ctypes.c_int32], ctypes.c_int32),
     "dd_nn_profile_static": ([ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p],
                              ctypes.c_int),
 }

@@ -224,9 +224,13 @@ cudaError_t graph_launch(dd_plan_s* p, int kind, const float* T_dev, dd_result_t
         p->ev_used = used;
         p->g_launches = launches;
         p->g_ev_used = used;
+        p->g_nwaves = p->nwaves;
+        for (int w = 0; w < p->nwaves; w++) p->g_waves[w] = p->waves[w];
     }
     p->launches = p->g_launches;
     p->ev_used = p->g_ev_used;
+    p->nwaves = p->g_nwaves;
+    for (int w = 0; w < p->g_nwaves; w++) p->waves[w] = p->g_waves[w];
     return cudaGraphLaunch(p->gexec, s);
 }
 
@@ -517,6 +521,35 @@ dd_status_t dd_plan_set_profiling(dd_plan_t p, int32_t enable) {
     }
     p->profiling = enable != 0;
     return DD_OK;
+}
+
+int32_t dd_plan_get_waves(dd_plan_t p, dd_wave_t* out, int32_t cap) {
+    if (!p || (cap > 0 && !out)) return -DD_EINVAL;
+    BusyGuard g(p);
+    if (!g.ok) return -DD_EBUSY;
+    const int nw = p->nwaves;
+    if (nw == 0 || cap <= 0) return nw;
+    unsigned long long pairs[dd::kMaxWaves], items[dd::kMaxWaves];
+    int rows[dd::kMaxWaves];
+    cudaError_t e = cudaMemcpy(pairs, p->ctrl->wave_pairs, sizeof(pairs), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(items, p->ctrl->wave_items, sizeof(items), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(rows, p->ctrl->wave_rows, sizeof(rows), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return -DD_ECUDA;
+    for (int w = 0; w < nw && w < cap; w++) {
+        dd_wave_t r{};
+        r.kind = p->waves[w].kind;
+        r.rows = rows[w];
+        r.items = (int64_t)items[w];
+        r.pairs = (int64_t)pairs[w];
+        r.ms = -1.0;
+        const int k = p->waves[w].ev;
+        float ms = 0.f;
+        if (p->profiling && k >= 0 && k + 1 < p->ev_used &&
+            cudaEventElapsedTime(&ms, p->ev[k], p->ev[k + 1]) == cudaSuccess)
+            r.ms = ms;
+        out[w] = r;
+    }
+    return nw;
 }
 
 dd_status_t dd_plan_get_profile(dd_plan_t p, dd_profile_t* out) {

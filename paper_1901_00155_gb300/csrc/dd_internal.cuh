@@ -24,6 +24,7 @@ constexpr int kTopkBins = 4096;          // bins of the top-k radix select (floa
 constexpr int kMuBins = 4096;            // bins of the mean-bucketed row order
 constexpr int kMaxLaunchSlots = 512;     // work counters per search
 constexpr int kMaxListSlots = 256;       // list counts per search
+constexpr int kMaxWaves = 64;            // distance waves traced per call
 
 // FP32 direct-difference tile kernel
 constexpr int kF32BM = 128;  // rows per tile
@@ -55,7 +56,13 @@ struct Ctrl {
     int smax[64];                 // largest per-tile segment count of each tile-range launch
     int cnt[kMaxListSlots];       // list counts written by compactions
     int work[kMaxLaunchSlots];    // dynamic-schedule work counters, one per launch
-    int topk_hist[kTopkBins];     // radix-select histogram
+    unsigned long long wave_pairs[kMaxWaves];  // per distance wave (by launch slot)
+    unsigned long long wave_items[kMaxWaves];
+    int wave_rows[kMaxWaves];
+    int topk_bin;                 // top-k select: bin of the first pass holding the k-th row (-1: take all)
+    int topk_need;                // rows still needed from that bin
+    int topk_hist[kTopkBins];     // radix-select histogram, pass 1 (float bits >> 19)
+    int topk_hist2[kTopkBins];    // pass 2 inside topk_bin (float bits >> 7, low 12 bits)
 };
 
 // A list of rows (orig indices).  Row r of the list is base[off + r] with
@@ -128,6 +135,7 @@ struct ScanArgs {
     int work_slot;
     int min_seg_tiles;
     int target_items;
+    int wave;                 // trace slot (< kMaxWaves) or -1
 };
 
 // Upper / lower bounds of a row's nearest-neighbour distance from its running
@@ -163,13 +171,16 @@ struct TcArgs {
     const float* gam;
     const float* q2;
     float beta;
-    const int4* ranges;
+    int4* ranges;  // per row tile (mode 2); the kernel narrows them as rows finish
     const int* smax;
     uint32_t* rmin;
     Ctrl* ctrl;
     const double* stats;
     int abandon, work_slot;
     uint32_t idesc;
+    int wave;               // trace slot (< kMaxWaves) or -1
+    const int32_t* sigpos;  // orig row -> position in the mean order
+    int local_k;            // mode 2: > 0 limits row i to positions within local_k of its own
 };
 
 }  // namespace dd
@@ -243,6 +254,14 @@ struct dd_plan_s {
     // captured search graph (replayed while the input/output pointers and the
     // profiling switch stay the same)
     cudaStream_t cap_stream = nullptr;
+    struct WaveMeta {
+        int kind;  // dd_wave_kind_t
+        int ev;    // index of its start event in ev[], -1 if untimed
+    };
+    WaveMeta waves[dd::kMaxWaves];  // host-side metadata of the last call's waves (by launch slot)
+    int nwaves = 0;
+    WaveMeta g_waves[dd::kMaxWaves];  // the same for the captured graph
+    int g_nwaves = 0;
     cudaStream_t side_stream = nullptr;  // SAX / word order run here, beside the mean order
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     cudaGraphExec_t gexec = nullptr;

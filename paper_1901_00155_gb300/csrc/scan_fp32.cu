@@ -74,6 +74,7 @@ __global__ void __launch_bounds__(NT, 2) k_scan_fp32(ScanArgs a) {
     if (ctrl->nonfinite || ctrl->degenerate) return;
     const int cnt = *a.rows.cnt_dev;
     const int off = a.rows.off_dev ? *a.rows.off_dev : 0;
+    if (blockIdx.x == 0 && threadIdx.x == 0 && a.wave >= 0) a.ctrl->wave_rows[a.wave] = cnt;
     const int RT = (cnt + BM - 1) / BM;
     if (RT <= 0) return;
     const int mode = a.col.mode;
@@ -105,7 +106,7 @@ __global__ void __launch_bounds__(NT, 2) k_scan_fp32(ScanArgs a) {
     const int tx = tid & 15, ty = tid >> 4;
     const int n = a.n;
     const int nk = (n + BK - 1) / BK;
-    unsigned long long pairs = 0;
+    unsigned long long pairs = 0, nrun = 0;
 
     for (;;) {
         __syncthreads();  // the previous item is done with sm.item and the tiles
@@ -162,6 +163,7 @@ __global__ void __launch_bounds__(NT, 2) k_scan_fp32(ScanArgs a) {
             L = a.col.local_cols < bsz ? a.col.local_cols : bsz;
         }
         const int nvr = __syncthreads_count(tid < BM && sm.row[tid] >= 0);
+        bool ran = false;
 
         for (int ct = ct0; ct < ct1; ct++) {
             if (a.abandon) {
@@ -196,6 +198,10 @@ __global__ void __launch_bounds__(NT, 2) k_scan_fp32(ScanArgs a) {
             const int nvc = __syncthreads_count(valid_col);
             if (nvc == 0) continue;
             pairs += (unsigned long long)nvr * (unsigned long long)nvc;
+            if (!ran) {
+                ran = true;
+                nrun++;
+            }
 
             float acc[8][8];
 #pragma unroll
@@ -272,6 +278,10 @@ __global__ void __launch_bounds__(NT, 2) k_scan_fp32(ScanArgs a) {
         __syncthreads();
     }
     if (tid == 0 && pairs) atomicAdd(&a.ctrl->pairs, pairs);
+    if (tid == 0 && a.wave >= 0) {
+        if (pairs) atomicAdd(&a.ctrl->wave_pairs[a.wave], pairs);
+        if (nrun) atomicAdd(&a.ctrl->wave_items[a.wave], nrun);
+    }
 }
 
 }  // namespace

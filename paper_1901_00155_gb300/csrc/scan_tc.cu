@@ -16,11 +16,15 @@
 // lower bound), and every row that the bound cannot rule out is rescored
 // exactly in FP64 (rescore.cu).
 //
-// Roles (192 threads, one CTA per SM, persistent):
-//   warp 0  lane 0 : TMA producer (A tile resident per item, B tiles through a ring)
+// Roles (352 threads, one CTA per SM, persistent):
+//   warp 0         : scheduler -- claims work items, loads their rows, skips
+//                    items whose rows are all abandoned, publishes the rest
 //   warp 1         : TMEM allocation (512 columns = two 128x256 FP32 buffers);
 //                    lane 0 issues the UMMAs and commits them to mbarriers
-//   warps 2-5      : epilogue, one tile row per thread (TMEM lane = row)
+//   warps 2-9      : epilogue, two warps per 32-lane TMEM quarter (TMEM lane =
+//                    tile row), each taking half of the tile's columns
+//   warp 10 lane 0 : TMA producer (operand k-chunks through a ring of stages,
+//                    per-column constants by bulk copy)
 // All mbarrier waits are bounded with %globaltimer; on expiry the CTA records
 // DD_ETIMEOUT in the control block, drains and returns.
 #include <cuda.h>
@@ -238,6 +242,7 @@ __global__ void __launch_bounds__(kTcThreadsV2, 1)
     if (ctrl->nonfinite || ctrl->degenerate) return;
     const int cnt = *a.rows.cnt_dev;
     const int off = a.rows.off_dev ? *a.rows.off_dev : 0;
+    if (blockIdx.x == 0 && tid == 0 && a.wave >= 0) a.ctrl->wave_rows[a.wave] = cnt;
     const int RT = (cnt + TBM - 1) / TBM;
     if (RT <= 0) return;
     long long items;
@@ -290,59 +295,132 @@ __global__ void __launch_bounds__(kTcThreadsV2, 1)
     const int tma_warp = 2 + kEpiWarps;
     if (warp == 0) {
         // ---------------- scheduler: work items, rows, alive check ----------------
+        // Items are claimed kClaim at a time; the row loads of a whole batch are
+        // issued together and the next claim is in flight while the batch is
+        // published, so the global-memory latency is paid once per batch.
+        constexpr int kClaim = 4;
+        // short waves claim one item at a time so that every CTA gets work
+        const int claim = items >= (long long)gridDim.x * kClaim * 2 ? kClaim : 1;
         int ring = 0;
         uint32_t rph = 0;
-        unsigned long long pairs = 0;
+        unsigned long long pairs = 0, nrun = 0;
         bool ok = true;
-        for (;;) {
-            int item = 0;
-            if (lane == 0) item = atomicAdd(&a.ctrl->work[a.work_slot], 1);
-            item = __shfl_sync(0xffffffffu, item, 0);
-            if (item >= items || *abort) break;
-            int rt, pa, pb, dir;
-            item_geometry(a, item, RT, nseg0, rt, pa, pb, dir);
-            if (pa >= pb) continue;
-            // rows of the tile (4 per lane) and the alive check
-            bool any = !a.abandon;
-            int nvr = 0;
-            float4 rowd[4];
-            const float bsf = __uint_as_float(*((volatile const unsigned*)&ctrl->bsf));
+        // Lower-bound full scans (mode 2) also skip a segment when no row of the
+        // tile can still be lowered by it: every column j of the segment has
+        // d^2 >= n (mu_i - mu_j)^2 and that exceeds the row's current upper
+        // bound.  The segment's sqrt(n) mu range comes from its end columns
+        // widened by one mean bin (columns are sorted by bin, not by exact mean).
+        const bool seg_check = a.mode == 2 && a.abandon;
+        // local waves (mode 2 with local_k > 0): row i only needs the columns
+        // within local_k positions of its own place in the mean order
+        const bool local = a.mode == 2 && a.local_k > 0;
+        const float snw = sqrtf((float)n) * (float)a.stats[7] * 1.001f;
+        int base = 0;
+        if (lane == 0) base = atomicAdd(&a.ctrl->work[a.work_slot], claim);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        while (ok && base < items && !*abort) {
+            int rt[kClaim], pa[kClaim], pb[kClaim], dir[kClaim];
+            int ri[kClaim][4];
+            float segL[kClaim], segH[kClaim];
 #pragma unroll
-            for (int q = 0; q < 4; q++) {
-                const int r = rt * TBM + q * 32 + lane;
-                rowd[q] = make_float4(0.f, 0.f, INFINITY, __int_as_float(-1));
-                if (r < cnt) {
-                    nvr++;
-                    const int ri = a.rows.base[off + r];
-                    const float D = __uint_as_float(*((volatile const unsigned*)(a.rmin + ri)));
-                    rowd[q] = make_float4(a.rowmu[ri], a.rowc[ri], D, __int_as_float(ri));
-                    if (a.abandon) any |= !(D + bound_F(D, a.alpha[ri], a.gam[ri], a.q2[ri], a.beta) < bsf);
+            for (int b = 0; b < kClaim; b++) {
+                const long long item = b < claim ? (long long)base + b : items;
+                rt[b] = 0;
+                pa[b] = pb[b] = 0;
+                dir[b] = 1;
+                if (item < items) item_geometry(a, (int)item, RT, nseg0, rt[b], pa[b], pb[b], dir[b]);
+                // the row tile is known without the column range: load its rows in parallel with it
+                const int rtb = item < items ? (a.mode == 3 ? (int)item : (int)(item % RT)) : RT;
+#pragma unroll
+                for (int q = 0; q < 4; q++) {
+                    const int r = rtb * TBM + q * 32 + lane;
+                    ri[b][q] = r < cnt ? a.rows.base[off + r] : -1;
+                }
+                segL[b] = -INFINITY;
+                segH[b] = INFINITY;
+                if (seg_check && pa[b] < pb[b]) {
+                    segL[b] = a.coldat[kColPad + pa[b]].x - snw;
+                    segH[b] = a.coldat[kColPad + pb[b] - 1].x + snw;
                 }
             }
-            any = __any_sync(0xffffffffu, any);
-            if (!any) continue;
-            nvr = __reduce_add_sync(0xffffffffu, nvr);
-            if (lane == 0 && !mbar_wait(&h.it_empty[ring], rph ^ 1u, abort)) ok = false;
-            ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
-            if (!ok) break;
+            const float bsf = __uint_as_float(*((volatile const unsigned*)&ctrl->bsf));
+            float4 rowd[kClaim][4];
+            bool any[kClaim];
 #pragma unroll
-            for (int q = 0; q < 4; q++) h.items[ring].row[q * 32 + lane] = rowd[q];
-            __threadfence_block();
-            __syncwarp();
-            if (lane == 0) {
-                pairs += (unsigned long long)nvr * (unsigned long long)(pb - pa);
-                ItemDesc& d = h.items[ring];
-                d.rt = rt;
-                d.pa = pa;
-                d.pb = pb;
-                d.dir = dir;
-                d.nct = (pb - pa + TBN - 1) / TBN;
-                mbar_arrive(&h.it_full[ring]);
+            for (int b = 0; b < kClaim; b++) {
+                const bool up = dir[b] > 0;
+                bool fin = true;  // no live row needs this segment or any farther one on its side
+                any[b] = !a.abandon && !local;
+#pragma unroll
+                for (int q = 0; q < 4; q++) {
+                    const int i = ri[b][q];
+                    rowd[b][q] = make_float4(0.f, 0.f, INFINITY, __int_as_float(-1));
+                    if (i < 0 || pa[b] >= pb[b]) continue;
+                    const float D = __uint_as_float(*((volatile const unsigned*)(a.rmin + i)));
+                    rowd[b][q] = make_float4(a.rowmu[i], a.rowc[i], D, __int_as_float(i));
+                    if (!a.abandon && !local) continue;
+                    const float R = D + bound_F(D, a.alpha[i], a.gam[i], a.q2[i], a.beta);
+                    // a row whose upper bound is below the best-so-far stays below it
+                    if (a.abandon && R < bsf) continue;
+                    bool need = true, need_far = true;
+                    if (seg_check) {
+                        const float x = rowd[b][q].x;
+                        const float lim = sqrtf(R) * 1.001f + 1e-5f * (fabsf(x) + fabsf(segL[b]) + fabsf(segH[b]));
+                        const float dd = fmaxf(fmaxf(segL[b] - x, x - segH[b]), 0.f);
+                        // every column at or beyond the segment (on its side) lies past segL / segH
+                        const float df = fmaxf(up ? segL[b] - x : x - segH[b], 0.f);
+                        need = !(dd > lim);  // NaN -> needed
+                        need_far = !(df > lim);
+                    }
+                    if (local) {
+                        const int qi = a.sigpos[i];
+                        need = need && pa[b] <= qi + a.local_k && pb[b] > qi - a.local_k;
+                        need_far = need_far && (up ? qi + a.local_k >= pa[b] : qi - a.local_k < pb[b]);
+                    }
+                    any[b] |= need;
+                    fin = fin && !need_far;
+                }
+                // shrink the tile's column range: later items of this side see an empty segment
+                if ((seg_check || local) && pa[b] < pb[b] && __all_sync(0xffffffffu, fin) && lane == 0) {
+                    if (up)
+                        atomicMin(&a.ranges[rt[b]].y, pa[b]);
+                    else
+                        atomicMax(&a.ranges[rt[b]].x, pb[b]);
+                }
             }
-            if (++ring == kItemRing) {  // every lane keeps the ring position
-                ring = 0;
-                rph ^= 1u;
+            int nbase = 0;
+            if (lane == 0) nbase = atomicAdd(&a.ctrl->work[a.work_slot], claim);
+#pragma unroll
+            for (int b = 0; b < kClaim; b++) {
+                if (!__any_sync(0xffffffffu, any[b] && pa[b] < pb[b])) continue;
+                int nvr = 0;
+#pragma unroll
+                for (int q = 0; q < 4; q++) nvr += ri[b][q] >= 0 ? 1 : 0;
+                nvr = __reduce_add_sync(0xffffffffu, nvr);
+                if (lane == 0 && !mbar_wait(&h.it_empty[ring], rph ^ 1u, abort)) ok = false;
+                ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+                if (!ok) break;
+#pragma unroll
+                for (int q = 0; q < 4; q++) h.items[ring].row[q * 32 + lane] = rowd[b][q];
+                __threadfence_block();
+                __syncwarp();
+                if (lane == 0) {
+                    pairs += (unsigned long long)nvr * (unsigned long long)(pb[b] - pa[b]);
+                    nrun++;
+                    ItemDesc& d = h.items[ring];
+                    d.rt = rt[b];
+                    d.pa = pa[b];
+                    d.pb = pb[b];
+                    d.dir = dir[b];
+                    d.nct = (pb[b] - pa[b] + TBN - 1) / TBN;
+                    mbar_arrive(&h.it_full[ring]);
+                }
+                if (++ring == kItemRing) {  // every lane keeps the ring position
+                    ring = 0;
+                    rph ^= 1u;
+                }
             }
+            base = __shfl_sync(0xffffffffu, nbase, 0);
         }
         if (lane == 0) {
             if (!ok) {
@@ -355,6 +433,10 @@ __global__ void __launch_bounds__(kTcThreadsV2, 1)
                 mbar_arrive(&h.it_full[ring]);
             }
             if (pairs) atomicAdd(&a.ctrl->pairs, pairs);
+            if (a.wave >= 0) {
+                if (pairs) atomicAdd(&a.ctrl->wave_pairs[a.wave], pairs);
+                if (nrun) atomicAdd(&a.ctrl->wave_items[a.wave], nrun);
+            }
         }
         __syncwarp();
     } else if (warp == tma_warp) {

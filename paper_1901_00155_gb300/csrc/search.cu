@@ -24,7 +24,8 @@ __device__ __forceinline__ bool is_alive(const TcBound& b, int i, uint32_t rbits
 
 // Compaction pass 1: predicate per list entry + per-block counts.
 // pred 0: alive against the best-so-far; pred 1: alive and rmin >= top-k
-// threshold; pred 2: member of Cand.
+// threshold; pred 2: member of Cand; pred 3: alive with no finite upper bound
+// yet (the running minimum still holds its initial value).
 __global__ void __launch_bounds__(256) k_compact_flags(ListRef in, const uint32_t* __restrict__ rmin, TcBound tb,
                                                        const Ctrl* ctrl, int pred, const int32_t* __restrict__ code,
                                                        const int32_t* __restrict__ hist, int phase1_max,
@@ -35,7 +36,7 @@ __global__ void __launch_bounds__(256) k_compact_flags(ListRef in, const uint32_
     const int cnt = *in.cnt_dev;
     const int off = in.off_dev ? *in.off_dev : 0;
     const uint32_t bsf = ctrl->bsf;
-    const uint32_t thr = pred == 1 ? ctrl->topk_thr : 0u;
+    const uint32_t thr = pred == 1 ? ctrl->topk_thr : (pred == 3 ? 0x7f000000u : 0u);
     int local = 0;
     const int base = blockIdx.x * kCompactRows + threadIdx.x * 8;
 #pragma unroll
@@ -120,37 +121,53 @@ __global__ void __launch_bounds__(256) k_compact_scatter(ListRef in, const uint8
     }
 }
 
-// Top-k radix select, pass 1: histogram of (float bits >> 19) of the rows'
-// running minima (alive rows only).
+// Top-k radix select over the rows' running minima (alive rows only), two
+// passes of 12 bits each: pass 0 histograms float bits >> 19; pass 1
+// histograms bits 7..18 of the rows inside the bin that holds the k-th row.
 __global__ void __launch_bounds__(256) k_topk_hist(ListRef in, const uint32_t* __restrict__ rmin, TcBound tb,
-                                                   Ctrl* ctrl) {
+                                                   Ctrl* ctrl, int pass) {
     __shared__ int h[kTopkBins];
     for (int b = threadIdx.x; b < kTopkBins; b += blockDim.x) h[b] = 0;
     __syncthreads();
     const int cnt = *in.cnt_dev;
     const int off = in.off_dev ? *in.off_dev : 0;
     const uint32_t bsf = ctrl->bsf;
-    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < cnt; r += gridDim.x * blockDim.x) {
-        const int i = in.base[off + r];
-        const uint32_t b = rmin[i];
-        if (is_alive(tb, i, b, bsf)) atomicAdd(&h[b >> 19], 1);
+    const int sel = pass == 0 ? 0 : ctrl->topk_bin;
+    if (sel >= 0) {
+        for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < cnt; r += gridDim.x * blockDim.x) {
+            const int i = in.base[off + r];
+            const uint32_t b = rmin[i];
+            if (!is_alive(tb, i, b, bsf)) continue;
+            if (pass == 0)
+                atomicAdd(&h[b >> 19], 1);
+            else if ((int)(b >> 19) == sel)
+                atomicAdd(&h[(b >> 7) & (kTopkBins - 1)], 1);
+        }
     }
     __syncthreads();
+    int* dst = pass == 0 ? ctrl->topk_hist : ctrl->topk_hist2;
     for (int b = threadIdx.x; b < kTopkBins; b += blockDim.x)
-        if (h[b]) atomicAdd(&ctrl->topk_hist[b], h[b]);
+        if (h[b]) atomicAdd(&dst[b], h[b]);
 }
 
-// Top-k pass 2: the threshold bin (from the top) whose cumulative count
-// reaches k.  One block: per-thread sums of 4 bins (descending), a block
-// inclusive scan, and the first thread whose run crosses k.
-__global__ void __launch_bounds__(1024) k_topk_thr(Ctrl* ctrl, int k) {
+// Top-k threshold of one pass: the bin (from the top) whose cumulative count
+// reaches the number of rows still wanted.  One block: per-thread sums of 4
+// bins (descending), a block inclusive scan, and the first thread whose run
+// crosses it.  Pass 0 records the bin and the rows still needed inside it;
+// pass 1 refines the threshold to 2^7 ulps.
+__global__ void __launch_bounds__(1024) k_topk_thr(Ctrl* ctrl, int k, int pass) {
     __shared__ int part[32];
     __shared__ int found;
+    __shared__ int above, total;
+    const int sel = pass == 0 ? 0 : ctrl->topk_bin;
+    if (sel < 0) return;  // pass 0 took every row
+    const int want = pass == 0 ? k : ctrl->topk_need;
+    const int* hist = pass == 0 ? ctrl->topk_hist : ctrl->topk_hist2;
     const int t = threadIdx.x;  // thread t covers bins [4095 - 4t - 3, 4095 - 4t]
     int c[4], s = 0;
 #pragma unroll
     for (int q = 0; q < 4; q++) {
-        c[q] = ctrl->topk_hist[kTopkBins - 1 - 4 * t - q];
+        c[q] = hist[kTopkBins - 1 - 4 * t - q];
         s += c[q];
     }
     const int lane = t & 31, wid = t >> 5;
@@ -179,13 +196,32 @@ __global__ void __launch_bounds__(1024) k_topk_thr(Ctrl* ctrl, int k) {
     for (int q = 0; q < 4; q++) {
         const int before = run;
         run += c[q];
-        if (before < k && run >= k) atomicMin(&found, 4 * t + q);
+        if (before < want && run >= want) {
+            atomicMin(&found, 4 * t + q);
+            above = before;  // written by the single crossing thread
+            total = run;
+        }
     }
     __syncthreads();
     if (t == 0) {
-        const int pos = found == 0x7fffffff ? kTopkBins - 1 : found;  // fewer than k rows: take them all
-        const int b = kTopkBins - 1 - pos;
-        ctrl->topk_thr = found == 0x7fffffff ? 0u : ((uint32_t)b << 19);
+        if (found == 0x7fffffff) {  // fewer rows than wanted
+            if (pass == 0) {
+                ctrl->topk_thr = 0u;  // take them all
+                ctrl->topk_bin = -1;
+            } else {
+                ctrl->topk_thr = (uint32_t)sel << 19;
+            }
+        } else {
+            const int b = kTopkBins - 1 - found;
+            if (pass == 0) {
+                // refine only when the first pass would take over twice the rows wanted
+                ctrl->topk_bin = total > 2 * want ? b : -1;
+                ctrl->topk_need = want - above;
+                ctrl->topk_thr = (uint32_t)b << 19;
+            } else {
+                ctrl->topk_thr = ((uint32_t)sel << 19) | ((uint32_t)b << 7);
+            }
+        }
     }
 }
 
@@ -340,6 +376,7 @@ __global__ void k_check_rows(const int32_t* __restrict__ rows, int count, int64_
 // ---------------------------------------------------------------------------
 // Host-side sequencing (no synchronisation; counts stay on the device).
 constexpr int kSegCols = 512;
+constexpr int kFillCols = 2048;  // half-width of the neighbourhood of rows the band wave left unbounded
 
 struct Seq {
     dd_plan_s* p;
@@ -379,11 +416,17 @@ struct Seq {
 
     // One wave of distance tiles for the rows of `rows`.  a_direct: the list
     // is the mean-bucketed order itself (its operand rows need no packing).
-    void scan(ListRef rows, ColSpec col, int abandon, const int* smax = nullptr, bool a_direct = false) {
+    void scan(int kind, ListRef rows, ColSpec col, int abandon, const int* smax = nullptr, bool a_direct = false) {
+        if (tc && col.mode == 1) return;  // the same-word wave runs in the FP32 form only
         const int slot = work_slot++;
         if (work_slot > kMaxLaunchSlots) {
             err = cudaErrorInvalidValue;
             return;
+        }
+        int wave = -1;
+        if (p->nwaves < kMaxWaves) {
+            wave = p->nwaves++;
+            p->waves[wave] = dd_plan_s::WaveMeta{kind, p->profiling ? p->ev_used : -1};
         }
         if (!tc) {
             ScanArgs a{};
@@ -407,6 +450,7 @@ struct Seq {
             a.abandon = abandon;
             a.work_slot = slot;
             a.min_seg_tiles = 4;
+            a.wave = wave;
             const int grid = scan_fp32_grid(p);
             a.target_items = grid * 2;
             prof_mark(p, s, true);
@@ -415,7 +459,6 @@ struct Seq {
             p->launches++;
             return;
         }
-        if (col.mode == 1) return;  // the same-word wave runs in the FP32 form only
         if (!a_direct) keep(launch_gather_rows(p, rows, s));
         TcArgs t{};
         t.N = (int)p->N;
@@ -436,6 +479,8 @@ struct Seq {
         t.q2 = p->q2;
         t.beta = tb.beta;
         t.ranges = p->ranges;
+        t.sigpos = p->sigpos;
+        t.local_k = t.mode == 2 ? col.local_cols : 0;
         t.smax = smax;
         t.rmin = p->rmin;
         t.ctrl = p->ctrl;
@@ -443,6 +488,7 @@ struct Seq {
         t.abandon = abandon;
         t.work_slot = slot;
         const uint32_t ty = p->opt.precision == DD_TC_BF16 ? 1u : 0u;
+        t.wave = wave;
         t.idesc = (1u << 4) | (ty << 7) | (ty << 10) | ((uint32_t)(256 >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
         prof_mark(p, s, true);
         keep(launch_scan_tc(p, t, !a_direct, s));
@@ -490,18 +536,20 @@ struct Seq {
     }
 
     void topk(ListRef in, int k) {
-        k_topk_hist<<<2 * p->sm_count, 256, 0, s>>>(in, p->rmin, tb, p->ctrl);
-        k_topk_thr<<<1, 1024, 0, s>>>(p->ctrl, k);
-        p->launches += 2;
+        for (int pass = 0; pass < 2; pass++) {
+            k_topk_hist<<<2 * p->sm_count, 256, 0, s>>>(in, p->rmin, tb, p->ctrl, pass);
+            k_topk_thr<<<1, 1024, 0, s>>>(p->ctrl, k, pass);
+        }
+        p->launches += 4;
         check();
     }
 
     // Full scan of each row of `in`: every column whose lower bound
     // n (mu_i - mu_j)^2 can still undercut the row's upper bound, nearest mean
     // first, abandoning against the best-so-far; survivors complete.
-    void full(ListRef in) {
+    void full(int kind, ListRef in) {
         const int* sm = ranges(in, 1, 0);
-        scan(in, ColSpec{2, 0, 0, 0}, 1, sm);
+        scan(kind, in, ColSpec{2, 0, 0, 0}, 1, sm);
         complete(in);
     }
 };
@@ -510,6 +558,7 @@ struct Seq {
 
 cudaError_t launch_search(dd_plan_s* p, const float* T, dd_result_t* out_dev, cudaStream_t s) {
     p->launches = 0;
+    p->nwaves = 0;
     cudaError_t e = cudaMemsetAsync(p->ctrl, 0, sizeof(Ctrl), s);
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(p->rmin, 0x7f, sizeof(uint32_t) * p->N, s);
@@ -537,40 +586,46 @@ cudaError_t launch_search(dd_plan_s* p, const float* T, dd_result_t* out_dev, cu
     };
     if (!o.early_abandon) {
         // every row scans every column; the argmax runs over all rows
-        q.scan(all, ColSpec{0, 0, (int)p->N, 0}, 0, nullptr, true);
+        q.scan(DD_WAVE_EXHAUSTIVE, all, ColSpec{0, 0, (int)p->N, 0}, 0, nullptr, true);
         q.complete(all);
     } else {
         // Upper bounds for every row from its nearest-mean neighbourhood.
         if (o.local_cols > 0) {
             if (q.tc) {
                 // tensor-core form: one 128 x 256 band tile per row tile
-                q.scan(all, ColSpec{3, 0, 0, 0}, 1, nullptr, true);
+                q.scan(DD_WAVE_BAND, all, ColSpec{3, 0, 0, 0}, 1, nullptr, true);
+                // rows the band left without a finite upper bound (every column of
+                // their band tile was within n of them in time): a wider
+                // neighbourhood in the mean order, row by row
+                ListRef lone = q.compact(all, p->list[0], 3);
+                const int* sm = q.ranges(lone, 0, kFillCols);
+                q.scan(DD_WAVE_LOCAL, lone, ColSpec{2, 0, 0, kFillCols}, 1, sm);
             } else {
                 const int* sm = q.ranges(all, 0, o.local_cols);
-                q.scan(all, ColSpec{2, 0, 0, 0}, 1, sm, true);
+                q.scan(DD_WAVE_LOCAL, all, ColSpec{2, 0, 0, 0}, 1, sm, true);
             }
         }
         join();
         // Algorithm 3 (PotentialDiscord): the Cand rows (rarest SAX words).
         ListRef cand = q.compact(all, p->list[0], 2);
-        q.full(cand);
+        q.full(DD_WAVE_CAND, cand);
         // Raise the best-so-far further: full scans of the rows with the
         // largest upper bounds (the likeliest discords) next.
         ListRef alive = q.compact(all, p->list[1], 0);
         if (o.refine_k > 0) {
             q.topk(alive, o.refine_k);
             ListRef top = q.compact(alive, p->list[2], 1);
-            q.full(top);
+            q.full(DD_WAVE_TOP, top);
         }
         // Algorithm 4 (RefineDiscord) over the remaining rows: rows sharing the
         // SAX word first (Index_Word), then every column the bound allows.
         if (o.word_cols > 0 && !q.tc) {
             ListRef words = q.constant_list(p->order, (int)p->N);
             ListRef wl = q.compact(words, p->list[3], 0);
-            q.scan(wl, ColSpec{1, 0, 0, o.word_cols}, 1);
+            q.scan(DD_WAVE_WORD, wl, ColSpec{1, 0, 0, o.word_cols}, 1);
         }
         ListRef rest = q.compact(alive, p->list[2], 0);
-        q.full(rest);
+        q.full(DD_WAVE_REST, rest);
     }
     join();
     if (q.tc) {
@@ -588,6 +643,7 @@ cudaError_t launch_search(dd_plan_s* p, const float* T, dd_result_t* out_dev, cu
 cudaError_t launch_profile(dd_plan_s* p, const float* T, const int32_t* rows, int count, float* nn2,
                            cudaStream_t s) {
     p->launches = 0;
+    p->nwaves = 0;
     cudaError_t e = cudaMemsetAsync(p->ctrl, 0, sizeof(Ctrl), s);
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(p->rmin, 0x7f, sizeof(uint32_t) * p->N, s);
@@ -599,7 +655,7 @@ cudaError_t launch_profile(dd_plan_s* p, const float* T, const int32_t* rows, in
     const int32_t* r = rows ? rows : p->seq_rows;
     const int c = rows ? count : (int)p->N;
     ListRef L = q.constant_list(r, c);
-    q.scan(L, ColSpec{0, 0, (int)p->N, 0}, 0);
+    q.scan(DD_WAVE_EXHAUSTIVE, L, ColSpec{0, 0, (int)p->N, 0}, 0);
     k_gather_min<<<(c + 255) / 256, 256, 0, s>>>(r, c, p->rmin, nn2);
     p->launches++;
     q.check();

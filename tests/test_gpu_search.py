@@ -187,3 +187,27 @@ def test_batched_uneven():
     out = dd.find_discord_batched(series, ns)
     for r, (T, n, i_ref, d2_ref) in zip(out, refs):
         _check_against(T, n, r, i_ref, d2_ref)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "tc_fp16"])
+def test_wave_trace(precision):
+    """The per-wave trace accounts for every evaluated pair, in the wave order
+    of Algorithm 2 (nearest-mean neighbourhood first, then Cand, top, rest)."""
+    dd = _dd()
+    spec = synth.workloads_medium()[2]
+    T, _ = synth.make_series(spec)
+    Td = torch.from_numpy(T).cuda()
+    with dd.Plan(T.size, spec.n, precision) as p:
+        p.set_profiling(True)
+        for _ in range(2):  # the second call replays the captured graph
+            r = p.find_discord(Td)
+            waves = p.waves()
+            assert waves, waves
+            assert sum(w["pairs"] for w in waves) == r.computed_pairs
+            first = "band" if precision != "fp32" else "local"
+            assert waves[0]["kind"] == first and waves[0]["rows"] == T.size - spec.n + 1
+            kinds = [w["kind"] for w in waves]
+            assert "cand" in kinds and kinds[-1] == "rest", kinds
+            assert all(w["ms"] >= 0.0 for w in waves), waves
+            assert all(w["items"] >= 0 and w["rows"] >= 0 for w in waves)
+            assert p.profile()["dist_launches"] == len(waves)
