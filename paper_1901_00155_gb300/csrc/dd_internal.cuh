@@ -125,7 +125,9 @@ struct ScanArgs {
     const int32_t* word_start;
     ColSpec col;
     const int32_t* sig;       // mean-bucketed order (mode 2)
-    const int4* ranges;       // per row tile (mode 2)
+    const int32_t* mubin;     // per orig row: mean bin (mode 2 lower-bound skips)
+    const double* stats;      // [7] = mean bin width
+    int4* ranges;             // per row tile (mode 2); narrowed as rows finish
     const int* smax;          // largest segment count over the tiles (mode 2)
     int seg_cols;             // columns per segment (mode 2)
     uint32_t* rmin;           // per orig row: float bits of the running minimum

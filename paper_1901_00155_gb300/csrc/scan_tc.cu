@@ -46,6 +46,10 @@ constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s
 
 constexpr int kStageBytes = kABytesPerAtom + kBBytesPerAtom;  // one k-chunk of A and B: 48 KB
 constexpr int kStages = 4;
+// band mode loads no separate A operand (its rows lie inside the B tile): the
+// same bytes hold six B-only stages, so more of the operand stream is in flight
+constexpr int kStagesBand = kStages * kStageBytes / kBBytesPerAtom;  // 6
+constexpr int kMaxStages = kStagesBand;
 constexpr int kItemRing = 4;
 constexpr int kEpiWarps = 8;
 constexpr int kEpiThreads = kEpiWarps * 32;
@@ -61,8 +65,8 @@ struct ItemDesc {
 };
 
 struct TcHdr {
-    unsigned long long b_full[kStages];
-    unsigned long long b_empty[kStages];
+    unsigned long long b_full[kMaxStages];
+    unsigned long long b_empty[kMaxStages];
     unsigned long long acc_full[2];
     unsigned long long acc_empty[2];
     unsigned long long col_full[kColSlots];
@@ -259,7 +263,7 @@ __global__ void __launch_bounds__(kTcThreadsV2, 1)
     }
 
     if (tid == 0) {
-        for (int s = 0; s < kStages; s++) {
+        for (int s = 0; s < kMaxStages; s++) {
             mbar_init(&h.b_full[s], 1);
             mbar_init(&h.b_empty[s], 1);
         }
@@ -291,6 +295,9 @@ __global__ void __launch_bounds__(kTcThreadsV2, 1)
     const int n = a.n;
     const int nka = a.nka;
     const bool band = a.mode == 3;
+    const int nst = band ? kStagesBand : kStages;              // stages in the ring
+    const int sbytes = band ? kBBytesPerAtom : kStageBytes;    // bytes per stage
+    const int boff = band ? 0 : kABytesPerAtom;                // B operand offset in a stage
 
     const int tma_warp = 2 + kEpiWarps;
     if (warp == 0) {
@@ -478,15 +485,15 @@ __global__ void __launch_bounds__(kTcThreadsV2, 1)
                             ok = false;
                             break;
                         }
-                        unsigned char* st = stages + stage * kStageBytes;
+                        unsigned char* st = stages + stage * sbytes;
                         if (band) {  // A rows come from inside the B tile
                             mbar_expect_tx(&h.b_full[stage], (uint32_t)kBBytesPerAtom);
                         } else {
                             mbar_expect_tx(&h.b_full[stage], (uint32_t)kStageBytes);
                             tma_load_2d(st, &mapA, &h.b_full[stage], ka * TKA, arow);
                         }
-                        tma_load_2d(st + kABytesPerAtom, &mapB, &h.b_full[stage], ka * TKA, p0);
-                        if (++stage == kStages) {
+                        tma_load_2d(st + boff, &mapB, &h.b_full[stage], ka * TKA, p0);
+                        if (++stage == nst) {
                             stage = 0;
                             sph ^= 1u;
                         }
@@ -532,16 +539,16 @@ __global__ void __launch_bounds__(kTcThreadsV2, 1)
                             break;
                         }
                         tc_fence_after();
-                        const uint32_t sa = smem_u32(stages + stage * kStageBytes);
+                        const uint32_t sa = smem_u32(stages + stage * sbytes);
                         // band mode: A = B rows [64, 192), 8 KB into the B tile (a whole number of 1 KB swizzle atoms)
-                        const uint64_t ad = sw128_desc(band ? sa + kABytesPerAtom + (TBN - TBM) / 2 * 128 : sa);
-                        const uint64_t bd = sw128_desc(sa + kABytesPerAtom);
+                        const uint64_t ad = sw128_desc(band ? sa + (TBN - TBM) / 2 * 128 : sa);
+                        const uint64_t bd = sw128_desc(sa + boff);
 #pragma unroll
                         for (int kk = 0; kk < TKA / 16; kk++)
                             umma_f16(dt, ad + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2), a.idesc,
                                      (ka | kk) != 0 ? 1u : 0u);
                         umma_commit(&h.b_empty[stage]);
-                        if (++stage == kStages) {
+                        if (++stage == nst) {
                             stage = 0;
                             sph ^= 1u;
                         }
