@@ -125,9 +125,7 @@ struct ScanArgs {
     const int32_t* word_start;
     ColSpec col;
     const int32_t* sig;       // mean-bucketed order (mode 2)
-    const int32_t* mubin;     // per orig row: mean bin (mode 2 lower-bound skips)
-    const double* stats;      // [7] = mean bin width
-    int4* ranges;             // per row tile (mode 2); narrowed as rows finish
+    const int4* ranges;       // per row tile (mode 2)
     const int* smax;          // largest segment count over the tiles (mode 2)
     int seg_cols;             // columns per segment (mode 2)
     uint32_t* rmin;           // per orig row: float bits of the running minimum
@@ -238,8 +236,8 @@ struct dd_plan_s {
 
     // Gram (tensor-core) form
     int kpad = 0;                     // n rounded up to 64 (one 128-byte swizzle atom)
-    void* S16 = nullptr;              // [N][kpad] centred rows in mean-bucketed order (FP16/BF16)
-    void* A16 = nullptr;              // [N][kpad] rows of the current list, packed
+    void* S16 = nullptr;              // [kpad/64][N][64] centred rows in mean-bucketed order (FP16/BF16), k-chunk major
+    void* A16 = nullptr;              // [kpad/64][N][64] rows of the current list, packed the same way
     float4* coldat = nullptr;         // [N + 512] per column in mean-bucketed order: (sqrt(n) mu, c, index, 0),
                                       // 256 padding entries on each side (c = +inf)
     float* rowmu = nullptr;           // [N] sqrt(n) mu (orig order)

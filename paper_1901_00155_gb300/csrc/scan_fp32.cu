@@ -29,7 +29,6 @@ struct __align__(16) F32Smem {
     int col[BN];
     float rmin[BM];
     float last[BM];
-    int bin[BM];
     int item;
     unsigned bsf;
     int nvalid_rows;
@@ -107,8 +106,6 @@ __global__ void __launch_bounds__(NT, 2) k_scan_fp32(ScanArgs a) {
     const int tx = tid & 15, ty = tid >> 4;
     const int n = a.n;
     const int nk = (n + BK - 1) / BK;
-    const float inv_n = 1.0f / (float)n;
-    const float inv_w = (float)(1.0 / a.stats[7]);
     unsigned long long pairs = 0, nrun = 0;
 
     for (;;) {
@@ -152,7 +149,6 @@ __global__ void __launch_bounds__(NT, 2) k_scan_fp32(ScanArgs a) {
             const float v = ri >= 0 ? __uint_as_float(a.rmin[ri]) : INFINITY;
             sm.rmin[tid] = v;
             sm.last[tid] = v;
-            sm.bin[tid] = (mode == 2 && ri >= 0) ? a.mubin[ri] : 0;
         }
         __syncthreads();
         // same-word neighbourhood of the tile's first row (mode 1)
@@ -171,45 +167,17 @@ __global__ void __launch_bounds__(NT, 2) k_scan_fp32(ScanArgs a) {
 
         for (int ct = ct0; ct < ct1; ct++) {
             if (a.abandon) {
-                // need: a live row whose lower bound n (mu_i - mu_j)^2 admits a
-                // column of this tile; far: ... or of any tile farther out on
-                // this side of a lower-bound segment (mode 2: columns sorted by
-                // mean bin, radius in bins from the row's running minimum)
-                bool need = false, far = false;
-                int tlo = 0, thi = 0;
-                if (mode == 2) {
-                    tlo = dir > 0 ? pa + ct * BN : max(pb - (ct + 1) * BN, pa);
-                    thi = dir > 0 ? min(pa + (ct + 1) * BN, pb) : pb - ct * BN;
-                }
+                bool alive = false;
                 if (tid < BM) {
                     const int ri = sm.row[tid];
                     if (ri >= 0) {
                         const float g = __uint_as_float(*((volatile const unsigned*)(a.rmin + ri)));
                         const float bsf = __uint_as_float(*((volatile const unsigned*)&ctrl->bsf));
                         const float mn = fminf(sm.rmin[tid], g);
-                        need = far = !(mn < bsf);
-                        if (need && mode == 2) {
-                            const int blo = a.mubin[a.sig[tlo]], bhi = a.mubin[a.sig[thi - 1]];
-                            const float hb = sqrtf(fmaxf(mn, 0.f) * inv_n) * 1.001f * inv_w;
-                            const int k = hb < 1e8f ? (int)ceilf(hb) + 2 : (1 << 28);  // NaN / inf -> every bin
-                            const int b = sm.bin[tid];
-                            need = b + k >= blo && b - k <= bhi;
-                            far = dir > 0 ? b + k >= blo : b - k <= bhi;
-                        }
+                        alive = !(mn < bsf);
                     }
                 }
-                const int any_need = __syncthreads_or(need);
-                if (!__syncthreads_or(far)) {
-                    // no row needs this tile or any farther one: later segments of the side see an empty range
-                    if (mode == 2 && tid == 0) {
-                        if (dir > 0)
-                            atomicMin(&a.ranges[rt].y, tlo);
-                        else
-                            atomicMax(&a.ranges[rt].x, thi);
-                    }
-                    break;
-                }
-                if (!any_need) continue;
+                if (!__syncthreads_or(alive)) break;
             }
             int valid_col = 0;
             if (tid < BN) {

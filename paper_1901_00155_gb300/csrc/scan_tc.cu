@@ -120,12 +120,14 @@ __device__ bool mbar_wait(unsigned long long* bar, uint32_t parity, volatile int
     }
 }
 
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, unsigned long long* bar, int x,
-                                            int y) {
+// Operand matrices are stored k-chunk major ([kpad / 64][rows][64]): one box of
+// a chunk plane (64 elements x box rows) is a single contiguous block in HBM.
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, unsigned long long* bar, int row,
+                                            int chunk) {
     asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
-        "[%4];" ::"r"(smem_u32(dst)),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(0), "r"(row), "r"(chunk), "r"(smem_u32(bar))
         : "memory");
 }
 
@@ -327,8 +329,9 @@ __global__ void __launch_bounds__(kTcThreadsV2, 1)
         base = __shfl_sync(0xffffffffu, base, 0);
         while (ok && base < items && !*abort) {
             int rt[kClaim], pa[kClaim], pb[kClaim], dir[kClaim];
-            int ri[kClaim][4];
+            float4 rowd[kClaim][4];  // per row: (sqrt(n) mu, c, running minimum, orig index bits)
             float segL[kClaim], segH[kClaim];
+            const float bsf = __uint_as_float(*((volatile const unsigned*)&ctrl->bsf));
 #pragma unroll
             for (int b = 0; b < kClaim; b++) {
                 const long long item = b < claim ? (long long)base + b : items;
@@ -341,7 +344,14 @@ __global__ void __launch_bounds__(kTcThreadsV2, 1)
 #pragma unroll
                 for (int q = 0; q < 4; q++) {
                     const int r = rtb * TBM + q * 32 + lane;
-                    ri[b][q] = r < cnt ? a.rows.base[off + r] : -1;
+                    rowd[b][q] = make_float4(0.f, 0.f, INFINITY, __int_as_float(-1));
+                    if (r < cnt) {
+                        if (a.a_direct) {  // the list is the mean order itself: row r is column off + r
+                            const float4 cd = a.coldat[kColPad + off + r];  // (sqrt(n) mu, c, index bits, 0)
+                            rowd[b][q] = make_float4(cd.x, cd.y, INFINITY, cd.z);
+                        } else
+                            rowd[b][q].w = __int_as_float(a.rows.base[off + r]);
+                    }
                 }
                 segL[b] = -INFINITY;
                 segH[b] = INFINITY;
@@ -350,8 +360,8 @@ __global__ void __launch_bounds__(kTcThreadsV2, 1)
                     segH[b] = a.coldat[kColPad + pb[b] - 1].x + snw;
                 }
             }
-            const float bsf = __uint_as_float(*((volatile const unsigned*)&ctrl->bsf));
-            float4 rowd[kClaim][4];
+            // the error bound of a row is needed to test it against a best-so-far or a lower bound
+            const bool need_bound = seg_check || local || (a.abandon && bsf > 0.f);
             bool any[kClaim];
 #pragma unroll
             for (int b = 0; b < kClaim; b++) {
@@ -360,12 +370,23 @@ __global__ void __launch_bounds__(kTcThreadsV2, 1)
                 any[b] = !a.abandon && !local;
 #pragma unroll
                 for (int q = 0; q < 4; q++) {
-                    const int i = ri[b][q];
-                    rowd[b][q] = make_float4(0.f, 0.f, INFINITY, __int_as_float(-1));
-                    if (i < 0 || pa[b] >= pb[b]) continue;
+                    const int i = __float_as_int(rowd[b][q].w);
+                    if (i < 0 || pa[b] >= pb[b]) {
+                        rowd[b][q] = make_float4(0.f, 0.f, INFINITY, __int_as_float(-1));
+                        continue;
+                    }
                     const float D = __uint_as_float(*((volatile const unsigned*)(a.rmin + i)));
-                    rowd[b][q] = make_float4(a.rowmu[i], a.rowc[i], D, __int_as_float(i));
+                    rowd[b][q].z = D;
+                    if (!a.a_direct) {
+                        rowd[b][q].x = a.rowmu[i];
+                        rowd[b][q].y = a.rowc[i];
+                    }
                     if (!a.abandon && !local) continue;
+                    if (!need_bound) {  // nothing has completed: every row is live and needs every column
+                        any[b] = true;
+                        fin = false;
+                        continue;
+                    }
                     const float R = D + bound_F(D, a.alpha[i], a.gam[i], a.q2[i], a.beta);
                     // a row whose upper bound is below the best-so-far stays below it
                     if (a.abandon && R < bsf) continue;
@@ -402,7 +423,7 @@ __global__ void __launch_bounds__(kTcThreadsV2, 1)
                 if (!__any_sync(0xffffffffu, any[b] && pa[b] < pb[b])) continue;
                 int nvr = 0;
 #pragma unroll
-                for (int q = 0; q < 4; q++) nvr += ri[b][q] >= 0 ? 1 : 0;
+                for (int q = 0; q < 4; q++) nvr += __float_as_int(rowd[b][q].w) >= 0 ? 1 : 0;
                 nvr = __reduce_add_sync(0xffffffffu, nvr);
                 if (lane == 0 && !mbar_wait(&h.it_empty[ring], rph ^ 1u, abort)) ok = false;
                 ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
@@ -490,9 +511,9 @@ __global__ void __launch_bounds__(kTcThreadsV2, 1)
                             mbar_expect_tx(&h.b_full[stage], (uint32_t)kBBytesPerAtom);
                         } else {
                             mbar_expect_tx(&h.b_full[stage], (uint32_t)kStageBytes);
-                            tma_load_2d(st, &mapA, &h.b_full[stage], ka * TKA, arow);
+                            tma_load_3d(st, &mapA, &h.b_full[stage], arow, ka);
                         }
-                        tma_load_2d(st + boff, &mapB, &h.b_full[stage], ka * TKA, p0);
+                        tma_load_3d(st + boff, &mapB, &h.b_full[stage], p0, ka);
                         if (++stage == nst) {
                             stage = 0;
                             sph ^= 1u;
@@ -772,7 +793,8 @@ __global__ void __launch_bounds__(256) k_build_S(const float* __restrict__ t32, 
             const float y0 = k < n ? (x0[r] - mu[r]) * s : 0.f;
             const float y1 = k + 1 < n ? (x1[r] - mu[r]) * s : 0.f;
             T16 v[2] = {to16(y0, (T16*)nullptr), to16(y1, (T16*)nullptr)};
-            *reinterpret_cast<uint32_t*>(S + (p0 + r) * kpad + k) = *reinterpret_cast<uint32_t*>(v);
+            *reinterpret_cast<uint32_t*>(S + ((int64_t)(k >> 6) * N + p0 + r) * TKA + (k & (TKA - 1))) =
+                *reinterpret_cast<uint32_t*>(v);
         }
     }
 }
@@ -795,16 +817,18 @@ __global__ void k_tc_scale(double* stats, int is_bf16) {
 
 // Packs the operand rows of a list (in list order) for TMA.
 __global__ void __launch_bounds__(256) k_gather_rows(ListRef L, const int32_t* __restrict__ sigpos,
-                                                     const uint4* __restrict__ S, int kpad, uint4* __restrict__ P) {
+                                                     const uint4* __restrict__ S, int kpad, int64_t N,
+                                                     uint4* __restrict__ P) {
     const int cnt = *L.cnt_dev;
     const int off = L.off_dev ? *L.off_dev : 0;
-    const int per_row = kpad / 8;  // uint4 per row
+    const int per_row = kpad / 8;  // uint4 per row (8 per 64-element chunk)
     const int64_t total = (int64_t)cnt * per_row;
     for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += (int64_t)gridDim.x * blockDim.x) {
         const int64_t r = g / per_row;
         const int c = (int)(g % per_row);
         const int i = L.base[off + r];
-        P[r * per_row + c] = S[(int64_t)sigpos[i] * per_row + c];
+        const int64_t plane = (int64_t)(c >> 3) * N;  // chunk-major: [chunk][row][8 uint4]
+        P[(plane + r) * 8 + (c & 7)] = S[(plane + sigpos[i]) * 8 + (c & 7)];
     }
 }
 
@@ -829,11 +853,12 @@ EncodeTiledFn encode_fn() {
 bool make_map(CUtensorMap* map, void* base, int64_t rows, int kpad, int box_rows, bool bf16) {
     EncodeTiledFn fn = encode_fn();
     if (!fn) return false;
-    cuuint64_t dims[2] = {(cuuint64_t)kpad, (cuuint64_t)rows};
-    cuuint64_t strides[1] = {(cuuint64_t)kpad * 2};
-    cuuint32_t box[2] = {(cuuint32_t)TKA, (cuuint32_t)box_rows};
-    cuuint32_t es[2] = {1, 1};
-    CUresult r = fn(map, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, base, dims,
+    // [kpad / 64][rows][64] elements: 128-byte rows, one plane per 64-element k-chunk
+    cuuint64_t dims[3] = {(cuuint64_t)TKA, (cuuint64_t)rows, (cuuint64_t)(kpad / TKA)};
+    cuuint64_t strides[2] = {(cuuint64_t)TKA * 2, (cuuint64_t)rows * TKA * 2};
+    cuuint32_t box[3] = {(cuuint32_t)TKA, (cuuint32_t)box_rows, 1};
+    cuuint32_t es[3] = {1, 1, 1};
+    CUresult r = fn(map, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3, base, dims,
                     strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
@@ -899,7 +924,7 @@ cudaError_t launch_tc_prep(dd_plan_s* p, cudaStream_t s) {
 
 cudaError_t launch_gather_rows(dd_plan_s* p, ListRef L, cudaStream_t s) {
     const int g = p->sm_count * 4;
-    k_gather_rows<<<g, 256, 0, s>>>(L, p->sigpos, reinterpret_cast<const uint4*>(p->S16), p->kpad,
+    k_gather_rows<<<g, 256, 0, s>>>(L, p->sigpos, reinterpret_cast<const uint4*>(p->S16), p->kpad, p->N,
                                     reinterpret_cast<uint4*>(p->A16));
     p->launches++;
     return cudaGetLastError();

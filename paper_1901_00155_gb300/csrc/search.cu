@@ -441,8 +441,6 @@ struct Seq {
             a.word_start = p->word_start;
             a.col = col;
             a.sig = p->sig;
-            a.mubin = p->mubin;
-            a.stats = p->stats;
             a.ranges = p->ranges;
             a.smax = smax;
             a.seg_cols = kSegCols;
