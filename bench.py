@@ -128,6 +128,43 @@ def _kernel_traffic(precision: str):
     return ent["dram_bytes_per_launch"] if h == ent.get("source_sha256_16") else None
 
 
+def _exhaustive(dd, Td, m: int, n: int, forms, peaks, rows: int = 8192, reps: int = 3) -> dict:
+    """Exhaustive mode (no abandon, metric (i)): dd_nn_rows over `rows` evenly spaced
+    rows against all N columns, CUDA events around each call on its stream."""
+    import torch
+    N = m - n + 1
+    stride = max(1, N // rows)
+    R = torch.arange(0, stride * rows, stride, dtype=torch.int32, device=Td.device)
+    R = R[R < N].contiguous()
+    out = {}
+    for prec in forms:
+        with dd.Plan(m, n, prec) as p:
+            y = p.nn_rows(Td, R)
+            torch.cuda.synchronize()
+            ts = []
+            for _ in range(reps):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record()
+                p.nn_rows(Td, R, out=y)
+                e1.record()
+                e1.synchronize()
+                ts.append(e0.elapsed_time(e1))
+        ms = statistics.median(ts)
+        pairs = R.numel() * N
+        if prec == "fp32":
+            work = 2.0 * n * pairs / (ms * 1e-3) / 1e12
+            peak = SM_COUNT * FP32_LANES_PER_SM * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+            unit = "Tinstr/s"
+        else:
+            work = 2.0 * plan_nkpad(n) * pairs / (ms * 1e-3) / 1e12
+            peak = float(peaks.get("bf16_tflops", 1900.0))
+            unit = "TFLOP/s"
+        out[prec] = {"pairs_per_s": pairs / (ms * 1e-3), "ms": ms, "rows": int(R.numel()), "columns": N,
+                     "achieved": work, "unit": unit, "peak": peak, "frac": work / peak}
+    return out
+
+
 def _reference_arm(args, rank: int):
     """The FP64 oracle (CPU HOTSAX, Algorithms 2-4) on the host cores, each step a
     bounded prefix sample of the benchmark workload."""
@@ -187,6 +224,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="best", choices=["best", "all", "fp32", "tc_fp16", "tc_bf16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-exhaustive", action="store_true",
+                    help="skip the exhaustive-mode (no abandon) pair-distances/s of each form")
     ap.add_argument("--workload", default="large", choices=["large", "medium"],
                     help="large: m=2^20 n=256 (the benchmark); medium: m=262144 n=256 (profiling captures)")
     args = ap.parse_args()
@@ -315,6 +354,9 @@ def main():
         plan.close()
 
     head = results[forms[0]]
+    exh = None
+    if not args.no_exhaustive:
+        exh = _exhaustive(dd, Td, m, n, [f for f in ("tc_fp16", "fp32") if f in supported], peaks)
     if rank == 0:
         cpu = None if args.no_cpu_baseline else _cpu_baseline()
         line = {"metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -332,7 +374,8 @@ def main():
                 "clocks": clocks_all, "gpu_launches": int(round(head["kernel_launches_per_step"] * args.steps)),
                 "forms": {k: {kk: vv for kk, vv in v.items() if kk != "roofline"} | {"roofline_frac": v["roofline"]["frac"]}
                           for k, v in results.items()},
-                "discord": {"index": head["index"], "nn_distance": head["nn_distance"]}}
+                "discord": {"index": head["index"], "nn_distance": head["nn_distance"]},
+                "exhaustive": exh}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
