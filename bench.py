@@ -165,6 +165,61 @@ def _exhaustive(dd, Td, m: int, n: int, forms, peaks, rows: int = 8192, reps: in
     return out
 
 
+def _batch(dd, precision: str, count: int = 512) -> dict:
+    """Many uneven series (m log-uniform in [2048, 65536], n in {64, 128, 256}) resident on
+    the device, searched by one dd_find_discord_batched call (an engine of 8 workers)."""
+    import torch
+    from paper_1901_00155_gb300 import synth
+    specs = synth.workload_batch(0, count)
+    series = [torch.from_numpy(synth.make_series(s)[0]).cuda() for s in specs]
+    ns = [s.n for s in specs]
+    dd.find_discord_batched(series[:16], ns[:16], precision)  # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    res = dd.find_discord_batched(series, ns, precision)
+    dt = time.perf_counter() - t0
+    pairs = sum(_pairs_unordered(s.m - s.n + 1, s.n) for s in specs)
+    return {"workload": f"{count} series, m log-uniform [2048, 65536], n in {{64,128,256}}, rw/sine, seed 0",
+            "precision": precision, "ms": dt * 1e3, "series_per_s": count / dt,
+            "value": pairs / dt, "unit": "pair-distances/s (brute-force equivalent)", "workers": 8,
+            "failed": sum(1 for r in res if isinstance(r, Exception))}
+
+
+def _serve(dd, precision: str, duration_s: float = 5.0, workers: int = 8, rate: float = 200.0) -> dict:
+    """Poisson arrivals (rate per s) of host series (m log-uniform in [4096, 2^20], n in
+    {64, ..., 1024}) into an engine of `workers`; latency = submission -> result on the host
+    (queue + host->device copy + plan + search + result copy)."""
+    import torch
+    from paper_1901_00155_gb300 import synth
+    trace = synth.serving_requests(0, rate, duration_s)
+    series = [torch.from_numpy(synth.make_series(s)[0]).pin_memory() for _, s in trace]
+    lat = []
+    with dd.Engine(workers, 1 << 20, 1024, precision) as E:
+        for k in range(min(workers, len(trace))):  # warm-up: every worker once
+            E.submit(series[k], trace[k][1].n, id=-1 - k)
+        E.drain()
+        t_start = time.perf_counter()
+        done = []
+        for k, (t, s) in enumerate(trace):
+            while True:
+                now = time.perf_counter() - t_start
+                if now >= t:
+                    break
+                done += E.poll(256, 0)
+                time.sleep(min(0.0005, t - now))
+            E.submit(series[k], s.n, id=k)
+        done += E.drain()
+        t_end = time.perf_counter()
+    failed = sum(1 for c in done if isinstance(c.result, Exception))
+    lat = sorted(c.queue_ms + c.service_ms for c in done)
+    q = lambda f: lat[min(len(lat) - 1, int(f * len(lat)))]
+    return {"workload": f"Poisson {rate:g}/s for {duration_s:g} s ({len(trace)} requests), m log-uniform "
+                        f"[4096, 2^20], n in {{64..1024}}, host series, seed 0",
+            "precision": precision, "workers": workers, "requests": len(done), "failed": failed,
+            "p50_ms": q(0.50), "p99_ms": q(0.99), "max_ms": lat[-1], "mean_ms": sum(lat) / len(lat),
+            "throughput_rps": len(done) / (t_end - t_start)}
+
+
 def _reference_arm(args, rank: int):
     """The FP64 oracle (CPU HOTSAX, Algorithms 2-4) on the host cores, each step a
     bounded prefix sample of the benchmark workload."""
@@ -224,6 +279,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="best", choices=["best", "all", "fp32", "tc_fp16", "tc_bf16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 512-series batched search")
+    ap.add_argument("--no-serve", action="store_true", help="skip the Poisson serving run (p50/p99)")
     ap.add_argument("--no-exhaustive", action="store_true",
                     help="skip the exhaustive-mode (no abandon) pair-distances/s of each form")
     ap.add_argument("--workload", default="large", choices=["large", "medium"],
@@ -354,6 +411,11 @@ def main():
         plan.close()
 
     head = results[forms[0]]
+    batch = serve = None
+    if not args.no_batch:
+        batch = _batch(dd, forms[0])
+    if not args.no_serve:
+        serve = _serve(dd, forms[0])
     exh = None
     if not args.no_exhaustive:
         exh = _exhaustive(dd, Td, m, n, [f for f in ("tc_fp16", "fp32") if f in supported], peaks)
@@ -375,7 +437,7 @@ def main():
                 "forms": {k: {kk: vv for kk, vv in v.items() if kk != "roofline"} | {"roofline_frac": v["roofline"]["frac"]}
                           for k, v in results.items()},
                 "discord": {"index": head["index"], "nn_distance": head["nn_distance"]},
-                "exhaustive": exh}
+                "exhaustive": exh, "batch": batch, "serve": serve}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

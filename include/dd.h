@@ -85,7 +85,14 @@ typedef struct {
                               on each side of its tile (default 128) */
     int32_t word_cols;     /* same-word wave: survivors scan this many rows sharing their SAX word
                               (Index_Word, Eq. 10) before their full scans; 0 = skip (default 512) */
-    int32_t reserved[7];   /* must be zero */
+    int32_t shard_count;   /* row sharding (multi-GPU, one process per GPU): 0 or 1 = every row.
+                              With G > 1 the search considers only the rows of shard shard_index:
+                              positions [floor(k N / G), floor((k + 1) N / G)) of the mean-bucketed
+                              visit order (every row still scans all columns).  The series' discord
+                              is the shard result with the largest nn_distance, ties to the
+                              smallest index -- one all-gather of (nn_distance, index) */
+    int32_t shard_index;   /* k in [0, G) (default 0) */
+    int32_t reserved[5];   /* must be zero */
 } dd_options_t;
 
 typedef struct {
@@ -162,7 +169,9 @@ DD_API dd_status_t dd_find_discord_host(dd_plan_t plan, const float* T_host, dd_
  * and subsequence lengths (T_dev[k]: m[k] float32 values on the device,
  * n[k]); one options struct for all (NULL = defaults).  Results go to
  * out[k] (host memory); out[k].status reports each series' own error.
- * Returns the first error met, DD_OK if every search succeeded. */
+ * Runs on a temporary engine (below) with up to 8 workers, longest series
+ * first; waits for `stream` first so that the series are ready.  Returns
+ * the first error met, DD_OK if every search succeeded. */
 DD_API dd_status_t dd_find_discord_batched(int32_t count, const float* const* T_dev, const int64_t* m, const int32_t* n,
                                     const dd_options_t* opt, dd_result_t* out, void* stream);
 
@@ -210,8 +219,12 @@ DD_API dd_status_t dd_plan_get_profile(dd_plan_t plan, dd_profile_t* out);
  * rows through a fixed sequence of waves (Algorithm 2): the nearest-mean
  * neighbourhood of every row (LOCAL in the FP32 form, BAND in the tensor-core
  * form), the Cand rows of Algorithm 3 (CAND), the rows with the largest upper
- * bounds (TOP), the rows of a word (WORD, FP32 form) and the rest of
- * Algorithm 4 (REST); exhaustive calls run EXHAUSTIVE waves. */
+ * bounds (TOP), the columns next to each surviving row in time (TIME: the
+ * index-order inner loop of Algorithm 4, direct FP32 differences in both
+ * forms), the rows of a word (WORD, FP32 form) and the rest of Algorithm 4
+ * (REST); the Gram form ends with direct FP32 full scans of its remaining
+ * candidates when there are many (SETTLE); exhaustive calls run EXHAUSTIVE
+ * waves. */
 typedef enum {
     DD_WAVE_EXHAUSTIVE = 0,
     DD_WAVE_LOCAL = 1,
@@ -219,7 +232,9 @@ typedef enum {
     DD_WAVE_CAND = 3,
     DD_WAVE_TOP = 4,
     DD_WAVE_WORD = 5,
-    DD_WAVE_REST = 6
+    DD_WAVE_REST = 6,
+    DD_WAVE_TIME = 7,
+    DD_WAVE_SETTLE = 8
 } dd_wave_kind_t;
 
 typedef struct {
@@ -263,6 +278,58 @@ DD_API dd_status_t dd_nn_profile_static(const float* T_dev, int64_t m, int32_t n
 
 /* Static text for a status code. */
 DD_API const char* dd_status_string(dd_status_t status);
+
+/* ---- engine: concurrent searches for batches and serving ---------------
+ *
+ * Not in the paper (which runs one search at a time): a pool of workers,
+ * each a host thread with its own CUDA stream, device workspace and plan,
+ * takes requests from one FIFO queue and runs them concurrently on the GPU,
+ * so that many small searches overlap.  Each worker keeps its last plan and
+ * reuses it for requests of the same (m, n); a new shape builds a plan in
+ * the worker's workspace without waiting for the other workers.  Every
+ * request uses the engine's options.  A request's result equals that of a
+ * plan searching the same series alone. */
+typedef struct dd_engine_s* dd_engine_t;
+
+typedef struct {
+    int64_t id;          /* the caller's request id */
+    dd_result_t result;  /* result.status is the request's own status */
+    double queue_ms;     /* submission -> a worker took the request */
+    double service_ms;   /* a worker took it -> result on the host (includes
+                            the host->device copy of a host series) */
+} dd_completion_t;
+
+enum { DD_SERIES_DEVICE = 0, DD_SERIES_HOST = 1 };
+
+/* workers in [1, 64].  Each worker reserves enough device memory for the
+ * plan of any series with m <= m_max and n <= n_max (the largest
+ * dd_plan_footprint over those shapes), plus m_max floats for host series.
+ * Admission: a request whose plan does not fit, or a host series longer than
+ * m_max, completes with DD_ENOMEM.  (m_max, n_max) must itself be a valid
+ * shape.  Errors: DD_EINVAL (bad sizes or options), DD_ENOMEM, DD_ECUDA. */
+DD_API dd_status_t dd_engine_create(dd_engine_t* engine, int32_t workers, const dd_options_t* opt, int64_t m_max,
+                                    int32_t n_max);
+
+/* Queues a search of the m values at T (device memory, or host memory with
+ * flags = DD_SERIES_HOST) with subsequence length n.  T must stay valid and
+ * unchanged until the request's completion has been polled; a device series
+ * must already be complete (the engine's streams are not ordered after the
+ * caller's).  Invalid sizes complete with DD_EINVAL.  Returns DD_EINVAL for a
+ * null engine or series or bad flags, DD_EBUSY once destruction has begun. */
+DD_API dd_status_t dd_engine_submit(dd_engine_t engine, int64_t id, const float* T, int64_t m, int32_t n,
+                                    int32_t flags);
+
+/* Moves up to cap finished requests to out[] (host memory), in the order
+ * they finished.  When none is ready, waits up to wait_ms milliseconds
+ * (negative: until one is).  Returns how many it moved, or -DD_EINVAL. */
+DD_API int32_t dd_engine_poll(dd_engine_t engine, dd_completion_t* out, int32_t cap, int32_t wait_ms);
+
+/* Requests submitted and not yet polled. */
+DD_API int64_t dd_engine_outstanding(dd_engine_t engine);
+
+/* Lets running requests finish, drops queued ones, joins the workers and
+ * frees everything. */
+DD_API void dd_engine_destroy(dd_engine_t engine);
 
 #ifdef __cplusplus
 }

@@ -17,7 +17,7 @@ from dataclasses import dataclass
 
 from . import _lib
 
-__all__ = ["Plan", "DiscordResult", "DDError", "find_discord", "find_discord_batched", "PRECISIONS"]
+__all__ = ["Plan", "Engine", "Completion", "DiscordResult", "DDError", "find_discord", "find_discord_batched", "PRECISIONS"]
 
 PRECISIONS = {"fp32": _lib.DD_FP32, "tc_fp16": _lib.DD_TC_FP16, "tc_bf16": _lib.DD_TC_BF16}
 
@@ -56,7 +56,7 @@ def _check(st: int, what: str):
 
 
 def _options(precision="fp32", paa_w=4, alphabet=4, early_abandon=True, paa_mode=0, phase1_max=4096,
-             refine_k=128, local_cols=128, word_cols=512) -> _lib.Options:
+             refine_k=128, local_cols=128, word_cols=512, shard_count=1, shard_index=0) -> _lib.Options:
     o = _lib.Options()
     _lib.load().dd_options_default(ctypes.byref(o))
     o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
@@ -68,6 +68,8 @@ def _options(precision="fp32", paa_w=4, alphabet=4, early_abandon=True, paa_mode
     o.refine_k = refine_k
     o.local_cols = local_cols
     o.word_cols = word_cols
+    o.shard_count = shard_count
+    o.shard_index = shard_index
     return o
 
 
@@ -261,3 +263,86 @@ def find_discord_batched(series, ns, precision="fp32", stream=None, **opts):
     if st != _lib.DD_OK and all(isinstance(r, DDError) for r in results):
         raise DDError(st, "dd_find_discord_batched")
     return results
+
+
+@dataclass
+class Completion:
+    id: int
+    result: object      # DiscordResult, or DDError for a failed request
+    queue_ms: float     # submission -> a worker took it
+    service_ms: float   # a worker took it -> result on the host
+
+
+class Engine:
+    """Concurrent searches (dd_engine_*): ``workers`` host threads, each with its own
+    CUDA stream, workspace and plan, take requests from one queue.  ``submit`` accepts
+    a CUDA float32 tensor (already complete on its stream) or host data (numpy / CPU
+    tensor; the worker copies it); the series is kept alive until its completion is
+    polled."""
+
+    def __init__(self, workers: int, m_max: int, n_max: int, precision="fp32", **opts):
+        self._lib = _lib.load()
+        self.options = _options(precision, **opts)
+        self._ptr = ctypes.c_void_p()
+        _check(self._lib.dd_engine_create(ctypes.byref(self._ptr), int(workers), ctypes.byref(self.options),
+                                          int(m_max), int(n_max)), "dd_engine_create")
+        self._keep = {}
+        self._next = 0
+
+    def submit(self, T, n: int, id: int | None = None) -> int:
+        import numpy as np
+        if id is None:
+            id = self._next
+        self._next = max(self._next, int(id) + 1)
+        if hasattr(T, "is_cuda") and T.is_cuda:
+            if T.dtype != _torch().float32 or not T.is_contiguous():
+                raise TypeError("T must be a contiguous float32 tensor")
+            ptr, m, flags, keep = T.data_ptr(), T.numel(), _lib.DD_SERIES_DEVICE, T
+        else:
+            a = np.ascontiguousarray(T.numpy() if hasattr(T, "numpy") else T, dtype=np.float32)
+            ptr, m, flags, keep = a.ctypes.data, a.size, _lib.DD_SERIES_HOST, a
+        self._keep[int(id)] = keep
+        _check(self._lib.dd_engine_submit(self._ptr, int(id), ctypes.c_void_p(ptr), int(m), int(n), flags),
+               "dd_engine_submit")
+        return int(id)
+
+    def poll(self, max_items: int = 64, wait_ms: int = 0) -> list:
+        buf = (_lib.Completion * max_items)()
+        k = int(self._lib.dd_engine_poll(self._ptr, buf, max_items, int(wait_ms)))
+        if k < 0:
+            _check(-k, "dd_engine_poll")
+        out = []
+        for c in buf[:k]:
+            self._keep.pop(int(c.id), None)
+            r = c.result
+            res = _as_result(r) if r.status == _lib.DD_OK else DDError(r.status, f"request {int(c.id)}")
+            out.append(Completion(int(c.id), res, float(c.queue_ms), float(c.service_ms)))
+        return out
+
+    def outstanding(self) -> int:
+        return int(self._lib.dd_engine_outstanding(self._ptr))
+
+    def drain(self) -> list:
+        """Waits for every outstanding request; returns their completions."""
+        out = []
+        while self.outstanding() > 0:
+            out += self.poll(256, -1)
+        return out
+
+    def close(self):
+        if getattr(self, "_ptr", None) and self._ptr.value:
+            self._lib.dd_engine_destroy(self._ptr)
+            self._ptr = ctypes.c_void_p()
+            self._keep.clear()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

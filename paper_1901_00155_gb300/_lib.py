@@ -19,7 +19,7 @@ class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("paa_w", ctypes.c_int32), ("alphabet", ctypes.c_int32),
                 ("early_abandon", ctypes.c_int32), ("paa_mode", ctypes.c_int32), ("phase1_max", ctypes.c_int32),
                 ("refine_k", ctypes.c_int32), ("local_cols", ctypes.c_int32), ("word_cols", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 7)]
+                ("shard_count", ctypes.c_int32), ("shard_index", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
 
 
 class Result(ctypes.Structure):
@@ -40,12 +40,21 @@ class Profile(ctypes.Structure):
                 ("computed_pairs", ctypes.c_int64), ("call_ms", ctypes.c_double), ("reserved", ctypes.c_int64 * 4)]
 
 
+class Completion(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_int64), ("result", Result), ("queue_ms", ctypes.c_double),
+                ("service_ms", ctypes.c_double)]
+
+
+DD_SERIES_DEVICE = 0
+DD_SERIES_HOST = 1
+
+
 class Wave(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("rows", ctypes.c_int32), ("items", ctypes.c_int64),
                 ("pairs", ctypes.c_int64), ("ms", ctypes.c_double)]
 
 
-WAVE_KINDS = {0: "exhaustive", 1: "local", 2: "band", 3: "cand", 4: "top", 5: "word", 6: "rest"}
+WAVE_KINDS = {0: "exhaustive", 1: "local", 2: "band", 3: "cand", 4: "top", 5: "word", 6: "rest", 7: "time", 8: "settle"}
 
 _lock = threading.Lock()
 _lib = None
@@ -76,6 +85,13 @@ SIGNATURES = {
     "dd_plan_get_waves": ([ctypes.c_void_p, ctypes.POINTER(Wave), ctypes.c_int32], ctypes.c_int32),
     "dd_nn_profile_static": ([ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p],
                              ctypes.c_int),
+    "dd_engine_create": ([ctypes.POINTER(ctypes.c_void_p), ctypes.c_int32, ctypes.POINTER(Options), ctypes.c_int64,
+                          ctypes.c_int32], ctypes.c_int),
+    "dd_engine_submit": ([ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32,
+                          ctypes.c_int32], ctypes.c_int),
+    "dd_engine_poll": ([ctypes.c_void_p, ctypes.POINTER(Completion), ctypes.c_int32, ctypes.c_int32], ctypes.c_int32),
+    "dd_engine_outstanding": ([ctypes.c_void_p], ctypes.c_int64),
+    "dd_engine_destroy": ([ctypes.c_void_p], None),
 }
 
 

@@ -1,5 +1,7 @@
 // api.cu -- the C ABI of libdd.so (declared in include/dd.h): plans, their
 // device workspace, and the entry points that enqueue preparation + search.
+#include <algorithm>
+#include <vector>
 #include <cstring>
 #include <new>
 
@@ -33,7 +35,9 @@ bool valid_options(const dd_options_t& o) {
     if (o.early_abandon != 0 && o.early_abandon != 1) return false;
     if (o.paa_mode != 0 && o.paa_mode != 1) return false;
     if (o.phase1_max < 0 || o.refine_k < 0 || o.local_cols < 0 || o.word_cols < 0) return false;
-    for (int i = 0; i < 7; i++)
+    if (o.shard_count < 0 || o.shard_index < 0 || o.shard_index >= (o.shard_count > 1 ? o.shard_count : 1))
+        return false;
+    for (int i = 0; i < 5; i++)
         if (o.reserved[i] != 0) return false;
     return true;
 }
@@ -108,6 +112,7 @@ size_t carve(dd_plan_s* p, char* base) {
         p->gam = c.take<float>(N);
         p->q2 = c.take<float>(N);
         p->ex64 = c.take<double>(N);
+        p->rmin32 = c.take<uint32_t>(N);
     }
     return (c.off + kAlign - 1) / kAlign * kAlign;
 }
@@ -235,6 +240,13 @@ cudaError_t graph_launch(dd_plan_s* p, int kind, const float* T_dev, dd_result_t
 }
 
 dd_status_t search_sync(dd_plan_s* p, const float* T_dev, dd_result_t* out, cudaStream_t s) {
+    if (!p->res_host) {  // engine plans allocate their pinned result slot on first synchronous use
+        if (cudaMallocHost(reinterpret_cast<void**>(&p->res_host), sizeof(dd_result_t)) != cudaSuccess) {
+            cudaGetLastError();
+            p->res_host = nullptr;
+            return DD_ENOMEM;
+        }
+    }
     cudaError_t e = p->use_graph ? graph_launch(p, 0, T_dev, nullptr, s) : enqueue_sync(p, T_dev, s);
     if (e != cudaSuccess) return from_cuda(e);
     e = cudaStreamSynchronize(s);
@@ -262,6 +274,130 @@ void prof_mark(dd_plan_s* p, cudaStream_t s, bool start) {
 namespace {
 
 }  // namespace
+
+namespace dd {
+
+// Builds a plan. Public plans (engine == false) allocate their workspace unless
+// one is given, initialise on the legacy stream and wait for the device. Engine
+// plans live in a worker's workspace and are initialised on that worker's
+// stream, so building one never waits for another worker's searches. They run
+// without graph capture (every shape is used once or a few times) and have no
+// pinned result buffer.
+dd_status_t create_plan(dd_plan_s** plan, int64_t m, int32_t n, const dd_options_t* opt, void* workspace,
+                        size_t workspace_bytes, bool engine, cudaStream_t init) {
+    if (!plan) return DD_EINVAL;
+    *plan = nullptr;
+    dd_options_t o;
+    if (opt)
+        o = *opt;
+    else
+        dd_options_default(&o);
+    if (!valid_options(o) || !valid_sizes(m, n)) return DD_EINVAL;
+    clamp_word(o, n);
+    if (o.precision != DD_FP32 && !dd::tc_supported(n)) return DD_ENOTSUP;
+    if (workspace && (reinterpret_cast<uintptr_t>(workspace) % kAlign) != 0) return DD_EINVAL;
+    if (engine && !workspace) return DD_EINVAL;
+    dd_plan_s* p = new (std::nothrow) dd_plan_s();
+    if (!p) return DD_ENOMEM;
+    p->m = m;
+    p->n = n;
+    p->N = m - n + 1;
+    p->opt = o;
+    p->D = dict_size(o);
+    p->use_graph = !engine;
+    cudaError_t e = cudaGetDevice(&p->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&p->sm_count, cudaDevAttrMultiProcessorCount, p->device);
+    if (e != cudaSuccess) {
+        delete p;
+        return from_cuda(e);
+    }
+    const size_t need = carve(p, nullptr);
+    p->ws_bytes = need;
+    if (workspace) {
+        if (workspace_bytes < need) {
+            delete p;
+            return DD_ENOMEM;
+        }
+        p->ws = workspace;
+        p->own_ws = false;
+    } else {
+        e = cudaMalloc(&p->ws, need);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            delete p;
+            return DD_ENOMEM;
+        }
+        p->own_ws = true;
+    }
+    carve(p, static_cast<char*>(p->ws));
+    if (!engine) {
+        e = cudaMallocHost(reinterpret_cast<void**>(&p->res_host), sizeof(dd_result_t));
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            if (p->own_ws) cudaFree(p->ws);
+            delete p;
+            return DD_ENOMEM;
+        }
+    }
+    {
+        // golden-ratio stride, coprime with N
+        int64_t st = (int64_t)(0.6180339887498949 * (double)p->N);
+        if (st < 1) st = 1;
+        auto gcd = [](int64_t x, int64_t y) {
+            while (y) {
+                const int64_t t = x % y;
+                x = y;
+                y = t;
+            }
+            return x;
+        };
+        while (gcd(st, p->N) != 1) st++;
+        p->mu_stride = st % p->N == 0 ? 1 : st;
+    }
+    dd::host_breakpoints(o.alphabet, p->beta_host);
+    e = cudaMemcpyAsync(p->beta, p->beta_host, sizeof(double) * (o.alphabet - 1), cudaMemcpyHostToDevice, init);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->t64 + p->m, 0, sizeof(double) * kPad, init);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->t32 + p->m, 0, sizeof(float) * kPad, init);
+    if (e == cudaSuccess) {
+        k_iota<<<(unsigned)((p->N + 255) / 256), 256, 0, init>>>(p->seq_rows, p->N);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->side_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming);
+    if (e == cudaSuccess && o.precision != DD_FP32) e = dd::tc_make_maps(p);
+    if (e == cudaSuccess && o.precision != DD_FP32) e = dd::tc_init_plan(p, init);
+    // the host copy above reads p->beta_host: wait for the init stream before returning
+    if (e == cudaSuccess) e = engine ? cudaStreamSynchronize(init) : cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        destroy_plan(p, !engine);
+        return from_cuda(e);
+    }
+    *plan = p;
+    return DD_OK;
+}
+
+// Releases a plan. wait_device: wait for all device work first (public plans,
+// whose last call's stream is unknown here); engine workers destroy plans only
+// after synchronising their own stream.
+void destroy_plan(dd_plan_s* p, bool wait_device) {
+    if (!p) return;
+    if (wait_device) cudaDeviceSynchronize();
+    if (p->gexec) cudaGraphExecDestroy(p->gexec);
+    if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
+    if (p->side_stream) cudaStreamDestroy(p->side_stream);
+    if (p->ev_fork) cudaEventDestroy(p->ev_fork);
+    if (p->ev_join) cudaEventDestroy(p->ev_join);
+    for (cudaEvent_t e : p->ev) cudaEventDestroy(e);
+    for (cudaEvent_t e : p->call_ev)
+        if (e) cudaEventDestroy(e);
+    if (p->res_host) cudaFreeHost(p->res_host);
+    if (p->own_ws && p->ws) cudaFree(p->ws);
+    delete p;
+}
+
+}  // namespace dd
 
 extern "C" {
 
@@ -296,111 +432,13 @@ size_t dd_plan_footprint(int64_t m, int32_t n, const dd_options_t* opt) {
     return carve(&tmp, nullptr);
 }
 
+
 dd_status_t dd_plan_create(dd_plan_t* plan, int64_t m, int32_t n, const dd_options_t* opt, void* workspace,
                            size_t workspace_bytes) {
-    if (!plan) return DD_EINVAL;
-    *plan = nullptr;
-    dd_options_t o;
-    if (opt)
-        o = *opt;
-    else
-        dd_options_default(&o);
-    if (!valid_options(o) || !valid_sizes(m, n)) return DD_EINVAL;
-    clamp_word(o, n);
-    if (o.precision != DD_FP32 && !dd::tc_supported(n)) return DD_ENOTSUP;
-    if (workspace && (reinterpret_cast<uintptr_t>(workspace) % kAlign) != 0) return DD_EINVAL;
-    dd_plan_s* p = new (std::nothrow) dd_plan_s();
-    if (!p) return DD_ENOMEM;
-    p->m = m;
-    p->n = n;
-    p->N = m - n + 1;
-    p->opt = o;
-    p->D = dict_size(o);
-    cudaError_t e = cudaGetDevice(&p->device);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&p->sm_count, cudaDevAttrMultiProcessorCount, p->device);
-    if (e != cudaSuccess) {
-        delete p;
-        return from_cuda(e);
-    }
-    const size_t need = carve(p, nullptr);
-    p->ws_bytes = need;
-    if (workspace) {
-        if (workspace_bytes < need) {
-            delete p;
-            return DD_ENOMEM;
-        }
-        p->ws = workspace;
-        p->own_ws = false;
-    } else {
-        e = cudaMalloc(&p->ws, need);
-        if (e != cudaSuccess) {
-            cudaGetLastError();
-            delete p;
-            return DD_ENOMEM;
-        }
-        p->own_ws = true;
-    }
-    carve(p, static_cast<char*>(p->ws));
-    e = cudaMallocHost(reinterpret_cast<void**>(&p->res_host), sizeof(dd_result_t));
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        if (p->own_ws) cudaFree(p->ws);
-        delete p;
-        return DD_ENOMEM;
-    }
-    {
-        // golden-ratio stride, coprime with N
-        int64_t st = (int64_t)(0.6180339887498949 * (double)p->N);
-        if (st < 1) st = 1;
-        auto gcd = [](int64_t x, int64_t y) {
-            while (y) {
-                const int64_t t = x % y;
-                x = y;
-                y = t;
-            }
-            return x;
-        };
-        while (gcd(st, p->N) != 1) st++;
-        p->mu_stride = st % p->N == 0 ? 1 : st;
-    }
-    dd::host_breakpoints(o.alphabet, p->beta_host);
-    e = cudaMemcpy(p->beta, p->beta_host, sizeof(double) * (o.alphabet - 1), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemset(p->t64 + p->m, 0, sizeof(double) * kPad);
-    if (e == cudaSuccess) e = cudaMemset(p->t32 + p->m, 0, sizeof(float) * kPad);
-    if (e == cudaSuccess) {
-        k_iota<<<(unsigned)((p->N + 255) / 256), 256>>>(p->seq_rows, p->N);
-        e = cudaGetLastError();
-    }
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->side_stream, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming);
-    if (e == cudaSuccess && o.precision != DD_FP32) e = dd::tc_make_maps(p);
-    if (e == cudaSuccess && o.precision != DD_FP32) e = dd::tc_init_plan(p);
-    if (e == cudaSuccess) e = cudaDeviceSynchronize();
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        dd_plan_destroy(p);
-        return from_cuda(e);
-    }
-    *plan = p;
-    return DD_OK;
+    return dd::create_plan(plan, m, n, opt, workspace, workspace_bytes, false, nullptr);
 }
 
-void dd_plan_destroy(dd_plan_t p) {
-    if (!p) return;
-    cudaDeviceSynchronize();
-    if (p->gexec) cudaGraphExecDestroy(p->gexec);
-    if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
-    if (p->side_stream) cudaStreamDestroy(p->side_stream);
-    if (p->ev_fork) cudaEventDestroy(p->ev_fork);
-    if (p->ev_join) cudaEventDestroy(p->ev_join);
-    for (cudaEvent_t e : p->ev) cudaEventDestroy(e);
-    for (cudaEvent_t e : p->call_ev)
-        if (e) cudaEventDestroy(e);
-    if (p->res_host) cudaFreeHost(p->res_host);
-    if (p->own_ws && p->ws) cudaFree(p->ws);
-    delete p;
-}
+void dd_plan_destroy(dd_plan_t p) { dd::destroy_plan(p, true); }
 
 dd_status_t dd_find_discord(dd_plan_t p, const float* T_dev, dd_result_t* out, void* stream) {
     if (!p || !T_dev || !out) return DD_EINVAL;
@@ -431,28 +469,47 @@ dd_status_t dd_find_discord_host(dd_plan_t p, const float* T_host, dd_result_t* 
 dd_status_t dd_find_discord_batched(int32_t count, const float* const* T_dev, const int64_t* m, const int32_t* n,
                                     const dd_options_t* opt, dd_result_t* out, void* stream) {
     if (count < 0 || (count > 0 && (!T_dev || !m || !n || !out))) return DD_EINVAL;
-    dd_status_t first = DD_OK;
-    dd_plan_t plan = nullptr;
-    int64_t pm = -1;
-    int32_t pn = -1;
+    if (count == 0) return DD_OK;
+    dd_options_t o;
+    if (opt)
+        o = *opt;
+    else
+        dd_options_default(&o);
+    // the shapes the engine must hold; invalid series fail on their own
+    int64_t m_max = 0;
+    int32_t n_max = 0;
+    for (int32_t k = 0; k < count; k++)
+        if (dd_plan_footprint(m[k], n[k], &o) > 0) {
+            m_max = m[k] > m_max ? m[k] : m_max;
+            n_max = n[k] > n_max ? n[k] : n_max;
+        }
+    if (cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) != cudaSuccess) return DD_ECUDA;
     for (int32_t k = 0; k < count; k++) {
-        dd_status_t st = DD_OK;
-        if (!plan || pm != m[k] || pn != n[k]) {
-            dd_plan_destroy(plan);
-            plan = nullptr;
-            st = dd_plan_create(&plan, m[k], n[k], opt, nullptr, 0);
-            pm = m[k];
-            pn = n[k];
-        }
-        if (st == DD_OK) st = dd_find_discord(plan, T_dev[k], &out[k], stream);
-        if (st != DD_OK) {
-            std::memset(&out[k], 0, sizeof(dd_result_t));
-            out[k].index = -1;
-            out[k].status = st;
-            if (first == DD_OK) first = st;
-        }
+        std::memset(&out[k], 0, sizeof(dd_result_t));
+        out[k].index = -1;
+        out[k].status = DD_EINVAL;
     }
-    dd_plan_destroy(plan);
+    if (m_max == 0) return DD_EINVAL;
+    dd_engine_t E = nullptr;
+    dd_status_t st = dd_engine_create(&E, count < 8 ? count : 8, &o, m_max, n_max);
+    if (st != DD_OK) return st;
+    // longest series first, so that the last ones to start are short
+    std::vector<int32_t> ord((size_t)count);
+    for (int32_t k = 0; k < count; k++) ord[(size_t)k] = k;
+    std::stable_sort(ord.begin(), ord.end(), [&](int32_t a, int32_t b) { return m[a] > m[b]; });
+    for (int32_t k : ord) dd_engine_submit(E, k, T_dev[k], m[k], n[k], DD_SERIES_DEVICE);
+    std::vector<dd_completion_t> c((size_t)count);
+    int32_t got = 0;
+    while (got < count) {
+        const int32_t r = dd_engine_poll(E, c.data(), count, -1);
+        if (r < 0) break;
+        for (int32_t j = 0; j < r; j++) out[c[(size_t)j].id] = c[(size_t)j].result;
+        got += r;
+    }
+    dd_engine_destroy(E);
+    dd_status_t first = DD_OK;
+    for (int32_t k = 0; k < count && first == DD_OK; k++)
+        if (out[k].status != DD_OK) first = (dd_status_t)out[k].status;
     return first;
 }
 

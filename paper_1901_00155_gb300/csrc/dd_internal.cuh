@@ -83,6 +83,11 @@ struct ListRef {
 //           columns, alternating right / left of C, nearest first;
 //   mode 3: (tensor-core form, list = the mean-bucketed order itself) row tile
 //           [q0, q0+128) against the 256 columns [q0-64, q0+192).
+// Column sets of a wave.  mode 0: positions [v_lo, v_hi) of `order`; 1: the
+// tile's first row's SAX word (local_cols of them); 2: lower-bound segments of
+// the mean order (ranges); 3: the band tile around the row tile (Gram form);
+// 4: time-local -- local_cols columns on each side of the tile's rows in time,
+// just outside their exclusion zones.
 struct ColSpec {
     int mode;
     int v_lo, v_hi;
@@ -114,6 +119,35 @@ struct PrepArrays {
     Ctrl* ctrl;
 };
 
+// In the Gram form every row also carries r32[i]: the smallest rigorous upper
+// bound on d^2 that a direct FP32 wave found for it (FP32 distance plus its
+// error bound; +inf when none).  An upper bound on the row's nearest-neighbour
+// distance is then min(D + F_i(D), r32[i]).  A lower bound after a full scan
+// of the row's columns stays D' - F_i(D') - gam^2 with D' = min(D, r32[i]):
+// D' is still at most the value the Gram tiles computed for the true
+// nearest column, and x - F_i(x) increases with x.
+struct TcBound {
+    const float* alpha;
+    const float* gam;
+    const float* q2;
+    float beta;
+    int on;
+    const uint32_t* r32;  // may be null
+};
+
+__device__ __forceinline__ float row_ub(const TcBound& b, int i, float D) {
+    if (!b.on) return D;
+    const float u = D + (b.alpha[i] + b.beta * D + b.gam[i] * sqrtf(fmaxf(D, 0.f) + b.q2[i]));
+    return b.r32 ? fminf(u, __uint_as_float(b.r32[i])) : u;
+}
+__device__ __forceinline__ float row_lb(const TcBound& b, int i, float D) {
+    if (!b.on) return D;
+    if (b.r32) D = fminf(D, __uint_as_float(b.r32[i]));
+    const float g = b.gam[i];
+    const float v = D - (b.alpha[i] + b.beta * D + g * sqrtf(fmaxf(D, 0.f) + b.q2[i])) - g * g;
+    return v > 0.f ? v : 0.f;
+}
+
 struct ScanArgs {
     const float* t32;
     int N, n;
@@ -136,28 +170,17 @@ struct ScanArgs {
     int min_seg_tiles;
     int target_items;
     int wave;                 // trace slot (< kMaxWaves) or -1
+    int min_rows;             // the wave runs only when the list has more rows than this
+    // Gram-form plans run the time-local wave (mode 4) with this kernel: it then
+    // tests rows against tb (the Gram bound) and writes rigorous FP32 upper
+    // bounds into r32 instead of plain minima into rmin
+    TcBound tb;
+    uint32_t* r32;
+    const double* stats;      // [2] = max |t^| of the series (FP32 error bound)
 };
 
 // Upper / lower bounds of a row's nearest-neighbour distance from its running
 // minimum D: identical to D for the FP32 form; D +- F_i(D) for the Gram form.
-struct TcBound {
-    const float* alpha;
-    const float* gam;
-    const float* q2;
-    float beta;
-    int on;
-};
-
-__device__ __forceinline__ float row_ub(const TcBound& b, int i, float D) {
-    if (!b.on) return D;
-    return D + (b.alpha[i] + b.beta * D + b.gam[i] * sqrtf(fmaxf(D, 0.f) + b.q2[i]));
-}
-__device__ __forceinline__ float row_lb(const TcBound& b, int i, float D) {
-    if (!b.on) return D;
-    const float g = b.gam[i];
-    const float v = D - (b.alpha[i] + b.beta * D + g * sqrtf(fmaxf(D, 0.f) + b.q2[i])) - g * g;
-    return v > 0.f ? v : 0.f;
-}
 
 struct TcArgs {
     int N, n, nka, stages, seg_cols, mode;
@@ -179,6 +202,7 @@ struct TcArgs {
     int abandon, work_slot;
     uint32_t idesc;
     int wave;               // trace slot (< kMaxWaves) or -1
+    const uint32_t* r32;    // per orig row: FP32 upper bound of the time-local wave (see TcBound)
     const int32_t* sigpos;  // orig row -> position in the mean order
     int local_k;            // mode 2: > 0 limits row i to positions within local_k of its own
 };
@@ -219,6 +243,7 @@ struct dd_plan_s {
     int32_t* order = nullptr;
     int32_t* pos_of = nullptr;
     uint32_t* rmin = nullptr;
+    uint32_t* rmin32 = nullptr;  // Gram form: FP32 upper bounds from the time-local wave (TcBound::r32)
     int32_t* list[4] = {nullptr, nullptr, nullptr, nullptr};
     uint8_t* flag = nullptr;
     int32_t* blk = nullptr;
@@ -300,7 +325,11 @@ size_t tc_smem_bytes(int kpad);
 int tc_stages(int kpad);
 bool tc_supported(int n);
 cudaError_t tc_make_maps(dd_plan_s* p);
-cudaError_t tc_init_plan(dd_plan_s* p);
+// api.cu: plan construction shared by the public entry point and the engine
+dd_status_t create_plan(dd_plan_s** plan, int64_t m, int32_t n, const dd_options_t* opt, void* workspace,
+                        size_t workspace_bytes, bool engine, cudaStream_t init);
+void destroy_plan(dd_plan_s* p, bool wait_device);
+cudaError_t tc_init_plan(dd_plan_s* p, cudaStream_t s);
 cudaError_t launch_tc_prep(dd_plan_s* p, cudaStream_t s);
 cudaError_t launch_gather_rows(dd_plan_s* p, ListRef L, cudaStream_t s);
 cudaError_t launch_scan_tc(dd_plan_s* p, const TcArgs& a, bool a_packed, cudaStream_t s);

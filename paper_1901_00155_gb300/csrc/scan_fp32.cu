@@ -67,12 +67,24 @@ __device__ __forceinline__ void stage_chunk(F32Smem& sm, int buf, const float* _
     }
 }
 
+// Rigorous upper bound on the exact squared distance d^2 (FP64 series) of a
+// pair whose FP32 value is e: inputs rounded to FP32 (|t^| <= M), FP32
+// differences, FMA accumulation of n terms -- the same bound, doubled, as the
+// FP32 screen of the exact rescoring.
+__device__ __forceinline__ float fp32_upper(float e, float n, float M) {
+    const float u = 5.9604644775390625e-08f;  // 2^-24
+    const float gn = n * u / (1.f - n * u);
+    const float mu6 = 6.f * u * M;
+    return e + 2.f * ((gn + 4.f * u) * e + 8.f * u * M * sqrtf(n * e) + n * mu6 * mu6) + 1e-30f;
+}
+
 __global__ void __launch_bounds__(NT, 2) k_scan_fp32(ScanArgs a) {
     extern __shared__ __align__(16) unsigned char smraw[];
     F32Smem& sm = *reinterpret_cast<F32Smem*>(smraw);
     const Ctrl* ctrl = a.ctrl_ro;
     if (ctrl->nonfinite || ctrl->degenerate) return;
     const int cnt = *a.rows.cnt_dev;
+    if (cnt <= a.min_rows) return;  // gated off on the device (the list is too short to be worth a wave)
     const int off = a.rows.off_dev ? *a.rows.off_dev : 0;
     if (blockIdx.x == 0 && threadIdx.x == 0 && a.wave >= 0) a.ctrl->wave_rows[a.wave] = cnt;
     const int RT = (cnt + BM - 1) / BM;
@@ -90,7 +102,7 @@ __global__ void __launch_bounds__(NT, 2) k_scan_fp32(ScanArgs a) {
             const int hi = a.col.v_hi < a.N ? a.col.v_hi : a.N;
             V = hi - a.col.v_lo;
         } else {
-            V = a.col.local_cols;
+            V = mode == 4 ? 2 * a.col.local_cols : a.col.local_cols;
         }
         if (V <= 0) return;
         CT = (V + BN - 1) / BN;
@@ -106,6 +118,9 @@ __global__ void __launch_bounds__(NT, 2) k_scan_fp32(ScanArgs a) {
     const int tx = tid & 15, ty = tid >> 4;
     const int n = a.n;
     const int nk = (n + BK - 1) / BK;
+    const bool assist = a.r32 != nullptr;
+    const float nf = (float)n;
+    const float tmax = assist ? (float)a.stats[2] : 0.f;
     unsigned long long pairs = 0, nrun = 0;
 
     for (;;) {
@@ -146,7 +161,9 @@ __global__ void __launch_bounds__(NT, 2) k_scan_fp32(ScanArgs a) {
             const int r = rt * BM + tid;
             const int ri = r < cnt ? a.rows.base[off + r] : -1;
             sm.row[tid] = ri;
-            const float v = ri >= 0 ? __uint_as_float(a.rmin[ri]) : INFINITY;
+            // assisting a Gram-form plan, the tile keeps plain FP32 minima (from +inf) and
+            // publishes their upper bounds to r32
+            const float v = (ri >= 0 && !assist) ? __uint_as_float(a.rmin[ri]) : INFINITY;
             sm.rmin[tid] = v;
             sm.last[tid] = v;
         }
@@ -163,6 +180,8 @@ __global__ void __launch_bounds__(NT, 2) k_scan_fp32(ScanArgs a) {
             L = a.col.local_cols < bsz ? a.col.local_cols : bsz;
         }
         const int nvr = __syncthreads_count(tid < BM && sm.row[tid] >= 0);
+        // time-local neighbourhood (mode 4): the tile's rows are in time order
+        const int t_first = sm.row[0], t_last = sm.row[nvr > 0 ? nvr - 1 : 0];
         bool ran = false;
 
         for (int ct = ct0; ct < ct1; ct++) {
@@ -174,7 +193,8 @@ __global__ void __launch_bounds__(NT, 2) k_scan_fp32(ScanArgs a) {
                         const float g = __uint_as_float(*((volatile const unsigned*)(a.rmin + ri)));
                         const float bsf = __uint_as_float(*((volatile const unsigned*)&ctrl->bsf));
                         const float mn = fminf(sm.rmin[tid], g);
-                        alive = !(mn < bsf);
+                        alive = assist ? !(fminf(row_ub(a.tb, ri, g), fp32_upper(sm.rmin[tid], nf, tmax)) < bsf)
+                                       : !(mn < bsf);
                     }
                 }
                 if (!__syncthreads_or(alive)) break;
@@ -188,6 +208,13 @@ __global__ void __launch_bounds__(NT, 2) k_scan_fp32(ScanArgs a) {
                 } else if (mode == 1) {
                     const int v = ct * BN + tid;
                     if (v < L) cj = a.order[bs + (startoff + v) % bsz];
+                } else if (mode == 4) {
+                    const int v = ct * BN + tid;
+                    const int K = a.col.local_cols;
+                    if (v < V) {
+                        const int j = v < K ? t_first - n - K + 1 + v : t_last + n + (v - K);
+                        cj = (j >= 0 && j < a.N) ? j : -1;
+                    }
                 } else {
                     const int p = dir > 0 ? pa + ct * BN + tid : pb - 1 - ct * BN - tid;
                     if (p >= pa && p < pb) cj = a.sig[p];
@@ -265,7 +292,10 @@ __global__ void __launch_bounds__(NT, 2) k_scan_fp32(ScanArgs a) {
                 const int ri = sm.row[tid];
                 const float v = sm.rmin[tid];
                 if (ri >= 0 && v < sm.last[tid]) {
-                    atomicMin(a.rmin + ri, __float_as_uint(v));
+                    if (assist)
+                        atomicMin(a.r32 + ri, __float_as_uint(fp32_upper(v, nf, tmax)));
+                    else
+                        atomicMin(a.rmin + ri, __float_as_uint(v));
                     sm.last[tid] = v;
                 }
             }
@@ -273,7 +303,9 @@ __global__ void __launch_bounds__(NT, 2) k_scan_fp32(ScanArgs a) {
         if (tid < BM) {
             const int ri = sm.row[tid];
             const float v = sm.rmin[tid];
-            if (ri >= 0 && v < sm.last[tid]) atomicMin(a.rmin + ri, __float_as_uint(v));
+            if (ri >= 0 && v < sm.last[tid])
+                atomicMin(assist ? a.r32 + ri : a.rmin + ri,
+                          __float_as_uint(assist ? fp32_upper(v, nf, tmax) : v));
         }
         __syncthreads();
     }

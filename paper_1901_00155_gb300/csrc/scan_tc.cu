@@ -193,8 +193,8 @@ __device__ __forceinline__ float bound_F(float D, float alpha, float gam, float 
     return alpha + beta * D + gam * sqrtf(fmaxf(D, 0.f) + q2);
 }
 
-__device__ __forceinline__ void item_geometry(const TcArgs& a, int item, int RT, int nseg0, int& rt, int& pa, int& pb,
-                                              int& dir) {
+__device__ __forceinline__ void item_geometry(const TcArgs& a, int item, int RT, int nseg0, int pos0, int& rt, int& pa,
+                                              int& pb, int& dir) {
     if (a.mode == 2) {
         const int s_rank = item / RT;
         rt = item % RT;
@@ -212,10 +212,10 @@ __device__ __forceinline__ void item_geometry(const TcArgs& a, int item, int RT,
             dir = -1;
         }
     } else if (a.mode == 3) {
-        // band: the row tile [q0, q0 + 128) of the mean-ordered list against the
-        // 256 columns [q0 - 64, q0 + 192) around it (the A rows lie inside that B tile)
+        // band: the row tile at positions [q0, q0 + 128) of the mean order (q0 = pos0 + 128 rt)
+        // against the 256 columns [q0 - 64, q0 + 192) around it (the A rows lie inside that B tile)
         rt = item;
-        pa = rt * TBM - (TBN - TBM) / 2;
+        pa = pos0 + rt * TBM - (TBN - TBM) / 2;
         pb = pa + TBN;
         dir = 1;
     } else {
@@ -251,6 +251,9 @@ __global__ void __launch_bounds__(kTcThreadsV2, 1)
     if (blockIdx.x == 0 && tid == 0 && a.wave >= 0) a.ctrl->wave_rows[a.wave] = cnt;
     const int RT = (cnt + TBM - 1) / TBM;
     if (RT <= 0) return;
+    // a list that is a slice of the mean order (a_direct) addresses its operand rows and
+    // column constants by position: row r of the list is position pos0 + r
+    const int pos0 = a.a_direct ? a.a_row0 + off : 0;
     long long items;
     int nseg0 = 1;
     if (a.mode == 2) {
@@ -338,7 +341,7 @@ __global__ void __launch_bounds__(kTcThreadsV2, 1)
                 rt[b] = 0;
                 pa[b] = pb[b] = 0;
                 dir[b] = 1;
-                if (item < items) item_geometry(a, (int)item, RT, nseg0, rt[b], pa[b], pb[b], dir[b]);
+                if (item < items) item_geometry(a, (int)item, RT, nseg0, pos0, rt[b], pa[b], pb[b], dir[b]);
                 // the row tile is known without the column range: load its rows in parallel with it
                 const int rtb = item < items ? (a.mode == 3 ? (int)item : (int)(item % RT)) : RT;
 #pragma unroll
@@ -346,8 +349,8 @@ __global__ void __launch_bounds__(kTcThreadsV2, 1)
                     const int r = rtb * TBM + q * 32 + lane;
                     rowd[b][q] = make_float4(0.f, 0.f, INFINITY, __int_as_float(-1));
                     if (r < cnt) {
-                        if (a.a_direct) {  // the list is the mean order itself: row r is column off + r
-                            const float4 cd = a.coldat[kColPad + off + r];  // (sqrt(n) mu, c, index bits, 0)
+                        if (a.a_direct) {  // a slice of the mean order: row r is column pos0 + r
+                            const float4 cd = a.coldat[kColPad + pos0 + r];  // (sqrt(n) mu, c, index bits, 0)
                             rowd[b][q] = make_float4(cd.x, cd.y, INFINITY, cd.z);
                         } else
                             rowd[b][q].w = __int_as_float(a.rows.base[off + r]);
@@ -387,7 +390,8 @@ __global__ void __launch_bounds__(kTcThreadsV2, 1)
                         fin = false;
                         continue;
                     }
-                    const float R = D + bound_F(D, a.alpha[i], a.gam[i], a.q2[i], a.beta);
+                    float R = D + bound_F(D, a.alpha[i], a.gam[i], a.q2[i], a.beta);
+                    if (a.r32) R = fminf(R, __uint_as_float(a.r32[i]));
                     // a row whose upper bound is below the best-so-far stays below it
                     if (a.abandon && R < bsf) continue;
                     bool need = true, need_far = true;
@@ -486,7 +490,7 @@ __global__ void __launch_bounds__(kTcThreadsV2, 1)
                     rph ^= 1u;
                 }
                 if (nct < 0) break;
-                const int arow = rt * TBM + (a.a_direct ? off : 0);
+                const int arow = rt * TBM + pos0;
                 for (int ct = 0; ct < nct && ok; ct++) {
                     const int p0 = dir > 0 ? pa + ct * TBN : pb - (ct + 1) * TBN;
                     // per-column constants of the tile (padded array: p0 >= -TBN, p0 + TBN <= N + TBN)
@@ -837,16 +841,16 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
 EncodeTiledFn encode_fn() {
-    static EncodeTiledFn fn = nullptr;
-    if (!fn) {
+    // resolved once (thread-safe static initialisation: plans are created from several threads)
+    static const EncodeTiledFn fn = []() -> EncodeTiledFn {
         void* ptr = nullptr;
         cudaDriverEntryPointQueryResult q;
         if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) !=
                 cudaSuccess ||
             q != cudaDriverEntryPointSuccess)
             return nullptr;
-        fn = reinterpret_cast<EncodeTiledFn>(ptr);
-    }
+        return reinterpret_cast<EncodeTiledFn>(ptr);
+    }();
     return fn;
 }
 
@@ -873,8 +877,8 @@ __global__ void k_coldat_pad(float4* coldat, int64_t N) {
     coldat[ix] = make_float4(0.f, INFINITY, __int_as_float(-(1 << 30)), 0.f);
 }
 
-cudaError_t tc_init_plan(dd_plan_s* p) {
-    k_coldat_pad<<<(2 * kColPad + 255) / 256, 256>>>(p->coldat, p->N);
+cudaError_t tc_init_plan(dd_plan_s* p, cudaStream_t s) {
+    k_coldat_pad<<<(2 * kColPad + 255) / 256, 256, 0, s>>>(p->coldat, p->N);
     return cudaGetLastError();
 }
 

@@ -17,6 +17,13 @@ __global__ void k_set_int(int* p, int v) { *p = v; }
 // best-so-far: FP32 form D < bsf (Algorithms 3/4); Gram form D + F_i(D) < bsf,
 // bsf being a proven lower bound there.  Non-negative floats order like their
 // bit patterns.
+// The value rows are ranked by for the top-k waves: the running minimum, or in
+// the Gram form the smaller of it and the row's FP32 upper bound (non-negative
+// floats order like their bit patterns).
+__device__ __forceinline__ uint32_t rank_bits(const TcBound& b, int i, uint32_t rbits) {
+    return b.r32 ? min(rbits, b.r32[i]) : rbits;
+}
+
 __device__ __forceinline__ bool is_alive(const TcBound& b, int i, uint32_t rbits, uint32_t bsf_bits) {
     if (!b.on) return rbits >= bsf_bits;
     return !(row_ub(b, i, __uint_as_float(rbits)) < __uint_as_float(bsf_bits));
@@ -25,10 +32,12 @@ __device__ __forceinline__ bool is_alive(const TcBound& b, int i, uint32_t rbits
 // Compaction pass 1: predicate per list entry + per-block counts.
 // pred 0: alive against the best-so-far; pred 1: alive and rmin >= top-k
 // threshold; pred 2: member of Cand; pred 3: alive with no finite upper bound
-// yet (the running minimum still holds its initial value).
+// yet (the running minimum still holds its initial value).  With sigpos set,
+// rows outside positions [p_lo, p_hi) of the mean order are dropped too.
 __global__ void __launch_bounds__(256) k_compact_flags(ListRef in, const uint32_t* __restrict__ rmin, TcBound tb,
                                                        const Ctrl* ctrl, int pred, const int32_t* __restrict__ code,
                                                        const int32_t* __restrict__ hist, int phase1_max,
+                                                       const int32_t* __restrict__ sigpos, int p_lo, int p_hi,
                                                        uint8_t* __restrict__ flag, int* __restrict__ blk) {
     __shared__ int sh;
     if (threadIdx.x == 0) sh = 0;
@@ -49,9 +58,10 @@ __global__ void __launch_bounds__(256) k_compact_flags(ListRef in, const uint32_
                 // Cand (Eq. 7): rows whose word has the smallest frequency
                 keep = hist[code[i]] == ctrl->fmin && ctrl->ncand <= phase1_max;
             } else {
-                const uint32_t b = rmin[i];
-                keep = is_alive(tb, i, b, bsf) && b >= thr;
+                keep = is_alive(tb, i, rmin[i], bsf) && rank_bits(tb, i, rmin[i]) >= thr;
             }
+            // sigpos: keep only rows at positions [p_lo, p_hi) of the mean order (a shard)
+            if (sigpos) keep = keep && sigpos[i] >= p_lo && sigpos[i] < p_hi;
             flag[r] = keep;
             local += keep;
         }
@@ -125,8 +135,9 @@ __global__ void __launch_bounds__(256) k_compact_scatter(ListRef in, const uint8
 // passes of 12 bits each: pass 0 histograms float bits >> 19; pass 1
 // histograms bits 7..18 of the rows inside the bin that holds the k-th row.
 __global__ void __launch_bounds__(256) k_topk_hist(ListRef in, const uint32_t* __restrict__ rmin, TcBound tb,
-                                                   Ctrl* ctrl, int pass) {
+                                                   Ctrl* ctrl, int pass, const int* gate, int k) {
     __shared__ int h[kTopkBins];
+    if (gate && *gate <= k) return;  // too few rows to be worth a separate wave
     for (int b = threadIdx.x; b < kTopkBins; b += blockDim.x) h[b] = 0;
     __syncthreads();
     const int cnt = *in.cnt_dev;
@@ -136,8 +147,8 @@ __global__ void __launch_bounds__(256) k_topk_hist(ListRef in, const uint32_t* _
     if (sel >= 0) {
         for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < cnt; r += gridDim.x * blockDim.x) {
             const int i = in.base[off + r];
-            const uint32_t b = rmin[i];
-            if (!is_alive(tb, i, b, bsf)) continue;
+            if (!is_alive(tb, i, rmin[i], bsf)) continue;
+            const uint32_t b = rank_bits(tb, i, rmin[i]);
             if (pass == 0)
                 atomicAdd(&h[b >> 19], 1);
             else if ((int)(b >> 19) == sel)
@@ -155,8 +166,15 @@ __global__ void __launch_bounds__(256) k_topk_hist(ListRef in, const uint32_t* _
 // bins (descending), a block inclusive scan, and the first thread whose run
 // crosses it.  Pass 0 records the bin and the rows still needed inside it;
 // pass 1 refines the threshold to 2^7 ulps.
-__global__ void __launch_bounds__(1024) k_topk_thr(Ctrl* ctrl, int k, int pass) {
+__global__ void __launch_bounds__(1024) k_topk_thr(Ctrl* ctrl, int k, int pass, const int* gate) {
     __shared__ int part[32];
+    if (gate && *gate <= k) {  // select no row
+        if (threadIdx.x == 0 && pass == 0) {
+            ctrl->topk_thr = 0xffffffffu;
+            ctrl->topk_bin = -1;
+        }
+        return;
+    }
     __shared__ int found;
     __shared__ int above, total;
     const int sel = pass == 0 ? 0 : ctrl->topk_bin;
@@ -333,6 +351,36 @@ __global__ void __launch_bounds__(128) k_tile_ranges(ListRef L, int kind, int K,
     }
 }
 
+// Gram form, after a direct FP32 full scan of the candidate rows (run only when
+// the list has more than min_rows rows, like that scan): every row still alive
+// scanned all the columns its lower bound admits, so its FP32 upper bound r32
+// came from its nearest column, and r32 - 2 margin(r32) is a rigorous lower
+// bound on its nearest-neighbour distance.  Raises the best-so-far with them.
+__global__ void __launch_bounds__(256) k_complete32(ListRef in, const uint32_t* __restrict__ rmin, TcBound tb,
+                                                    const double* stats, int n, int min_rows, Ctrl* ctrl) {
+    const int cnt = *in.cnt_dev;
+    if (cnt <= min_rows) return;
+    const int off = in.off_dev ? *in.off_dev : 0;
+    const uint32_t bsf = ctrl->bsf;
+    const float u = 5.9604644775390625e-08f;
+    const float nf = (float)n, M = (float)stats[2];
+    const float gn = nf * u / (1.f - nf * u);
+    const float mu6 = 6.f * u * M;
+    uint32_t best = 0;
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < cnt; r += gridDim.x * blockDim.x) {
+        const int i = in.base[off + r];
+        if (!is_alive(tb, i, rmin[i], bsf)) continue;
+        const float up = __uint_as_float(tb.r32[i]);
+        if (!(up < 1e30f)) continue;
+        const float margin = 2.f * ((gn + 4.f * u) * up + 8.f * u * M * sqrtf(nf * up) + nf * mu6 * mu6) + 1e-30f;
+        const float lb = up - 2.f * margin;
+        if (lb > 0.f) best = max(best, __float_as_uint(lb));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) best = max(best, __shfl_xor_sync(0xffffffffu, best, o));
+    if ((threadIdx.x & 31) == 0 && best > bsf) atomicMax(&ctrl->bsf, best);
+}
+
 __global__ void k_finalize(const Ctrl* ctrl, dd_result_t* out) {
     if (threadIdx.x != 0) return;
     dd_result_t r;
@@ -376,6 +424,8 @@ __global__ void k_check_rows(const int32_t* __restrict__ rows, int count, int64_
 // ---------------------------------------------------------------------------
 // Host-side sequencing (no synchronisation; counts stay on the device).
 constexpr int kSegCols = 512;
+constexpr int kSettleMin = 64;   // candidate rows above which the Gram form settles them in FP32 first
+constexpr int kTimeCols = 256;   // time-local wave: columns on each side of a row tile
 constexpr int kFillCols = 2048;  // half-width of the neighbourhood of rows the band wave left unbounded
 
 struct Seq {
@@ -396,6 +446,7 @@ struct Seq {
             tb.q2 = p->q2;
             tb.beta = 12.0f * 5.9604644775390625e-08f;  // 2 x 6 u32 (safety factor 2)
             tb.on = 1;
+            tb.r32 = p->rmin32;
         }
     }
 
@@ -416,7 +467,10 @@ struct Seq {
 
     // One wave of distance tiles for the rows of `rows`.  a_direct: the list
     // is the mean-bucketed order itself (its operand rows need no packing).
-    void scan(int kind, ListRef rows, ColSpec col, int abandon, const int* smax = nullptr, bool a_direct = false) {
+    // force_fp32: run the wave with the FP32 kernel in a Gram-form plan too (it then
+    // publishes rigorous FP32 upper bounds to rmin32, see TcBound).
+    void scan(int kind, ListRef rows, ColSpec col, int abandon, const int* smax = nullptr, bool a_direct = false,
+              bool force_fp32 = false, int min_rows = 0) {
         if (tc && col.mode == 1) return;  // the same-word wave runs in the FP32 form only
         const int slot = work_slot++;
         if (work_slot > kMaxLaunchSlots) {
@@ -428,8 +482,13 @@ struct Seq {
             wave = p->nwaves++;
             p->waves[wave] = dd_plan_s::WaveMeta{kind, p->profiling ? p->ev_used : -1};
         }
-        if (!tc) {
+        if (!tc || force_fp32) {
             ScanArgs a{};
+            if (tc) {
+                a.tb = tb;
+                a.r32 = p->rmin32;
+                a.stats = p->stats;
+            }
             a.t32 = p->t32;
             a.N = (int)p->N;
             a.n = p->n;
@@ -449,7 +508,8 @@ struct Seq {
             a.ctrl = p->ctrl;
             a.abandon = abandon;
             a.work_slot = slot;
-            a.min_seg_tiles = 4;
+            a.min_seg_tiles = col.mode == 4 ? 1 : 4;  // time-local: spread a tile's few columns over blocks
+            a.min_rows = min_rows;
             a.wave = wave;
             const int grid = scan_fp32_grid(p);
             a.target_items = grid * 2;
@@ -469,7 +529,7 @@ struct Seq {
         t.mode = col.mode == 2 || col.mode == 3 ? col.mode : 0;
         t.rows = rows;
         t.a_direct = a_direct ? 1 : 0;
-        t.a_row0 = 0;
+        t.a_row0 = a_direct ? (int)(rows.base - p->sig) : 0;  // direct lists are slices of the mean order
         t.sig = p->sig;
         t.coldat = p->coldat;
         t.rowmu = p->rowmu;
@@ -489,6 +549,7 @@ struct Seq {
         t.work_slot = slot;
         const uint32_t ty = p->opt.precision == DD_TC_BF16 ? 1u : 0u;
         t.wave = wave;
+        t.r32 = p->rmin32;
         t.idesc = (1u << 4) | (ty << 7) | (ty << 10) | ((uint32_t)(256 >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
         prof_mark(p, s, true);
         keep(launch_scan_tc(p, t, !a_direct, s));
@@ -512,7 +573,9 @@ struct Seq {
     }
 
     // Order-preserving compaction of `in` into `out`; returns the new list.
-    ListRef compact(ListRef in, int32_t* out, int pred) {
+    int p_lo = 0, p_hi = 0;  // this search's shard of the mean order
+
+    ListRef compact(ListRef in, int32_t* out, int pred, bool shard_only = false) {
         const int nblk = (int)((p->N + kCompactRows - 1) / kCompactRows);
         const int slot = cnt_slot++;
         if (cnt_slot > kMaxListSlots) {
@@ -520,7 +583,7 @@ struct Seq {
             return in;
         }
         k_compact_flags<<<nblk, 256, 0, s>>>(in, p->rmin, tb, p->ctrl, pred, p->code, p->hist, p->opt.phase1_max,
-                                             p->flag, p->blk);
+                                             shard_only ? p->sigpos : nullptr, p_lo, p_hi, p->flag, p->blk);
         k_compact_scan<<<1, 1024, 0, s>>>(p->blk, nblk, cnt_ptr(slot));
         k_compact_scatter<<<nblk, 256, 0, s>>>(in, p->flag, p->blk, out);
         p->launches += 3;
@@ -535,10 +598,12 @@ struct Seq {
         check();
     }
 
-    void topk(ListRef in, int k) {
+    // gate: skip (select nothing) unless *gate > k
+    void topk(ListRef in, int k, const int* gate = nullptr) {
+        keep(cudaMemsetAsync(p->ctrl->topk_hist, 0, sizeof(p->ctrl->topk_hist) + sizeof(p->ctrl->topk_hist2), s));
         for (int pass = 0; pass < 2; pass++) {
-            k_topk_hist<<<2 * p->sm_count, 256, 0, s>>>(in, p->rmin, tb, p->ctrl, pass);
-            k_topk_thr<<<1, 1024, 0, s>>>(p->ctrl, k, pass);
+            k_topk_hist<<<2 * p->sm_count, 256, 0, s>>>(in, p->rmin, tb, p->ctrl, pass, gate, k);
+            k_topk_thr<<<1, 1024, 0, s>>>(p->ctrl, k, pass, gate);
         }
         p->launches += 4;
         check();
@@ -562,6 +627,7 @@ cudaError_t launch_search(dd_plan_s* p, const float* T, dd_result_t* out_dev, cu
     cudaError_t e = cudaMemsetAsync(p->ctrl, 0, sizeof(Ctrl), s);
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(p->rmin, 0x7f, sizeof(uint32_t) * p->N, s);
+    if (e == cudaSuccess && p->rmin32) e = cudaMemsetAsync(p->rmin32, 0x7f, sizeof(uint32_t) * p->N, s);
     if (e != cudaSuccess) return e;
     e = launch_prep_common(p, T, s);
     if (e != cudaSuccess) return e;
@@ -578,7 +644,12 @@ cudaError_t launch_search(dd_plan_s* p, const float* T, dd_result_t* out_dev, cu
     Seq q(p, s);
     if (q.tc) q.keep(launch_tc_prep(p, s));
     const dd_options_t& o = p->opt;
-    ListRef all = q.constant_list(p->sig, (int)p->N);  // every row, mean-bucketed order
+    // every row of this shard (all rows unless sharded), in the mean-bucketed order
+    const int G = o.shard_count > 1 ? o.shard_count : 1;
+    const int64_t p_lo = p->N * o.shard_index / G, p_hi = p->N * (o.shard_index + 1) / G;
+    ListRef all = q.constant_list(p->sig + p_lo, (int)(p_hi - p_lo));
+    q.p_lo = (int)p_lo;
+    q.p_hi = (int)p_hi;
     bool joined = false;
     auto join = [&]() {
         if (!joined) q.keep(cudaStreamWaitEvent(s, p->ev_join, 0));
@@ -617,6 +688,24 @@ cudaError_t launch_search(dd_plan_s* p, const float* T, dd_result_t* out_dev, cu
             ListRef top = q.compact(alive, p->list[2], 1);
             q.full(DD_WAVE_TOP, top);
         }
+        // Algorithm 4 scans a row's other candidates in index order, which for a
+        // periodic series meets a match one period away; the mean order scatters
+        // those.  So every surviving row (in time order) first scans the columns
+        // just outside its exclusion zone, with direct FP32 differences (in the
+        // Gram form their rigorous upper bounds go to rmin32).
+        ListRef tl = q.compact(q.constant_list(p->seq_rows, (int)p->N), p->list[3], 0, true);
+        q.scan(DD_WAVE_TIME, tl, ColSpec{4, 0, 0, kTimeCols}, 1, nullptr, false, true, o.refine_k);
+        if (o.refine_k > 0) {
+            // The time-local bounds are close to each row's nearest-neighbour
+            // distance, where the first-wave bounds of a periodic series are not:
+            // rank again and fully scan the new top rows, so that the best-so-far
+            // reaches the discord before the rest.  This wave and the time-local
+            // one are skipped on the device when no more than refine_k rows are
+            // still alive (those go straight to the rest).
+            q.topk(alive, o.refine_k, tl.cnt_dev);
+            ListRef top2 = q.compact(alive, p->list[2], 1);
+            q.full(DD_WAVE_TOP, top2);
+        }
         // Algorithm 4 (RefineDiscord) over the remaining rows: rows sharing the
         // SAX word first (Index_Word), then every column the bound allows.
         if (o.word_cols > 0 && !q.tc) {
@@ -629,8 +718,23 @@ cudaError_t launch_search(dd_plan_s* p, const float* T, dd_result_t* out_dev, cu
     }
     join();
     if (q.tc) {
-        // every row the bound cannot rule out, rescored exactly in FP64
         ListRef cands = q.compact(all, p->list[3], 0);
+        if (o.early_abandon) {
+            // Many rows the Gram bound cannot rule out (data whose nearest-neighbour
+            // distances lie within the bound of each other): settle them first with
+            // direct FP32 full scans, whose error bound is far tighter, and raise the
+            // best-so-far with their FP32 lower bounds.  Skipped on the device for
+            // short lists.
+            const int* sm = q.ranges(cands, 1, 0);
+            q.scan(DD_WAVE_SETTLE, cands, ColSpec{2, 0, 0, 0}, 1, sm, false, true, kSettleMin);
+            const int g = (int)((p->N + 1023) / 1024);
+            k_complete32<<<g < 1024 ? g : 1024, 256, 0, s>>>(cands, p->rmin, q.tb, p->stats, p->n, kSettleMin,
+                                                             p->ctrl);
+            p->launches++;
+            q.check();
+            cands = q.compact(cands, p->list[2], 0);
+        }
+        // every row the bounds cannot rule out, rescored exactly in FP64
         q.keep(launch_rescore(p, cands, q.tb, q.work_slot++, out_dev, s));
     } else {
         k_finalize<<<1, 32, 0, s>>>(p->ctrl, out_dev);
@@ -647,6 +751,7 @@ cudaError_t launch_profile(dd_plan_s* p, const float* T, const int32_t* rows, in
     cudaError_t e = cudaMemsetAsync(p->ctrl, 0, sizeof(Ctrl), s);
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(p->rmin, 0x7f, sizeof(uint32_t) * p->N, s);
+    if (e == cudaSuccess && p->rmin32) e = cudaMemsetAsync(p->rmin32, 0x7f, sizeof(uint32_t) * p->N, s);
     if (e != cudaSuccess) return e;
     e = launch_prep(p, T, s);
     if (e != cudaSuccess) return e;

@@ -146,3 +146,43 @@ def workloads_medium() -> list[SeriesSpec]:
 def workload_large(seed: int = 0) -> SeriesSpec:
     """Random walk, m=2^20, n=256, five anomalies."""
     return SeriesSpec("rw", 1 << 20, 256, seed, ("burst", "flat", "spike", "phase", "burst"))
+
+
+def _log_uniform_int(rng: np.random.Generator, lo: int, hi: int) -> int:
+    return int(round(math.exp(rng.uniform(math.log(lo), math.log(hi)))))
+
+
+def workload_batch(seed: int = 0, count: int = 512) -> list[SeriesSpec]:
+    """Many uneven series for batched search: m log-uniform in [2048, 65536],
+    n in {64, 128, 256}, random walk and sine alternating, one anomaly each
+    (kind drawn from the four)."""
+    rng = np.random.default_rng(seed)
+    kinds = ("burst", "flat", "spike", "phase")
+    out = []
+    for k in range(count):
+        m = _log_uniform_int(rng, 2048, 65536)
+        n = int(rng.choice([64, 128, 256]))
+        an = (kinds[int(rng.integers(0, 4))],)
+        out.append(SeriesSpec("rw" if k % 2 == 0 else "sine", m, n, seed * 100003 + k, an))
+    return out
+
+
+def serving_requests(seed: int = 0, rate_per_s: float = 200.0, duration_s: float = 20.0,
+                     m_max: int = 1 << 20) -> list[tuple[float, SeriesSpec]]:
+    """A serving trace: Poisson arrivals at `rate_per_s` over `duration_s`
+    seconds; each request a series with m log-uniform in [4096, m_max],
+    n in {64, 128, 256, 512, 1024}, random walk or sine, one anomaly."""
+    rng = np.random.default_rng(seed)
+    kinds = ("burst", "flat", "spike", "phase")
+    t = 0.0
+    out = []
+    k = 0
+    while True:
+        t += float(rng.exponential(1.0 / rate_per_s))
+        if t >= duration_s:
+            return out
+        m = _log_uniform_int(rng, 4096, m_max)
+        n = int(rng.choice([64, 128, 256, 512, 1024]))
+        an = (kinds[int(rng.integers(0, 4))],)
+        out.append((t, SeriesSpec("rw" if rng.integers(0, 2) == 0 else "sine", m, n, seed * 1000003 + k, an)))
+        k += 1

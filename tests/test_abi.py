@@ -35,6 +35,7 @@ def test_struct_layouts():
     assert ctypes.sizeof(_lib.Result) == 40
     assert ctypes.sizeof(_lib.View) == 24 + 11 * 8
     assert ctypes.sizeof(_lib.Wave) == 32
+    assert ctypes.sizeof(_lib.Completion) == 64
 
 
 def test_options_default_and_footprint():
