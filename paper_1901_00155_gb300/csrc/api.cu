@@ -262,6 +262,7 @@ namespace dd {
 void prof_mark(dd_plan_s* p, cudaStream_t s, bool start) {
     if (!p->profiling) return;
     if (p->ev_used >= (int)p->ev.size()) return;  // pool exhausted: later launches untimed
+    if (p->in_cond) return;                       // conditional graph bodies hold no event nodes
     (void)start;
     cudaEvent_t e = p->ev[p->ev_used++];
     if (p->capturing)
@@ -363,6 +364,7 @@ dd_status_t create_plan(dd_plan_s** plan, int64_t m, int32_t n, const dd_options
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->side_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess && !engine) e = cudaStreamCreateWithFlags(&p->body_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming);
     if (e == cudaSuccess && o.precision != DD_FP32) e = dd::tc_make_maps(p);
@@ -387,6 +389,7 @@ void destroy_plan(dd_plan_s* p, bool wait_device) {
     if (p->gexec) cudaGraphExecDestroy(p->gexec);
     if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
     if (p->side_stream) cudaStreamDestroy(p->side_stream);
+    if (p->body_stream) cudaStreamDestroy(p->body_stream);
     if (p->ev_fork) cudaEventDestroy(p->ev_fork);
     if (p->ev_join) cudaEventDestroy(p->ev_join);
     for (cudaEvent_t e : p->ev) cudaEventDestroy(e);

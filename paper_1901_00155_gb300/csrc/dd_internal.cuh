@@ -287,7 +287,9 @@ struct dd_plan_s {
     int nwaves = 0;
     WaveMeta g_waves[dd::kMaxWaves];  // the same for the captured graph
     int g_nwaves = 0;
-    cudaStream_t side_stream = nullptr;  // SAX / word order run here, beside the mean order
+    cudaStream_t side_stream = nullptr;
+    cudaStream_t body_stream = nullptr;  // captures the bodies of conditional graph nodes
+    bool in_cond = false;                // capturing a conditional body (no event nodes there)  // SAX / word order run here, beside the mean order
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     cudaGraphExec_t gexec = nullptr;
     const void* g_T = nullptr;

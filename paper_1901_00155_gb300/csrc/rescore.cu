@@ -72,31 +72,38 @@ __global__ void __launch_bounds__(256) k_rescore64(ListRef cand, TcBound bound, 
         const double* x = t64 + i;
         const float* x32 = t32 + i;
         const float ub = row_ub(bound, i, D);
-        for (int p = a0 + threadIdx.x; p < a1; p += blockDim.x) {
+        // one warp per column: the lanes stride the subsequence (coalesced loads of
+        // both operands) and the partial sums meet in a shuffle reduction
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+        for (int p = a0 + wid; p < a1; p += nwarp) {
             const int j = sig[p];
             const int d = i - j;
             if (d < n && d > -n) continue;
             // FP32 screen: |s32 - s| <= (gamma_n + 4u) s32 + 8u M sqrt(n s32) + n (6 u M)^2, M = max|t^|,
-            // u = 2^-24 (inputs rounded to FP32, differences, FMA accumulation); doubled for safety.
+            // u = 2^-24 (inputs rounded to FP32, differences, FMA accumulation of at most n terms per
+            // partial sum plus the reduction); doubled for safety.
             const float* y32 = t32 + j;
             float s32 = 0.f;
-            for (int k = 0; k < n; k++) {
+            for (int k = lane; k < n; k += 32) {
                 const float df = x32[k] - y32[k];
                 s32 = fmaf(df, df, s32);
             }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) s32 += __shfl_xor_sync(0xffffffffu, s32, o);
             const float margin = 2.f * ((gn32 + 4.f * u32) * s32 + 8.f * u32 * maxabs * sqrtf(nf * s32) +
                                         nf * (6.f * u32 * maxabs) * (6.f * u32 * maxabs)) + 1e-30f;
             if (s32 - margin > ub) continue;
             const double* y = t64 + j;
             double s = 0.0;
-            for (int k = 0; k < n; k++) {
+            for (int k = lane; k < n; k += 32) {
                 const double df = x[k] - y[k];
                 s = fma(df, df, s);
             }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
             best = fmin(best, s);
         }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) best = fmin(best, __shfl_xor_sync(0xffffffffu, best, o));
+        // every lane holds its warp's minimum
         if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = best;
         __syncthreads();
         if (threadIdx.x == 0) {

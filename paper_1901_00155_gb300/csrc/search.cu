@@ -381,6 +381,19 @@ __global__ void __launch_bounds__(256) k_complete32(ListRef in, const uint32_t* 
     if ((threadIdx.x & 31) == 0 && best > bsf) atomicMax(&ctrl->bsf, best);
 }
 
+__global__ void k_copy_list(ListRef src, int32_t* __restrict__ dst, int* __restrict__ cnt_out) {
+    const int cnt = *src.cnt_dev;
+    const int off = src.off_dev ? *src.off_dev : 0;
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < cnt; r += gridDim.x * blockDim.x)
+        dst[r] = src.base[off + r];
+    if (blockIdx.x == 0 && threadIdx.x == 0) *cnt_out = cnt;
+}
+
+// Value of a conditional graph node: run its body only when *cnt > thr.
+__global__ void k_set_cond(cudaGraphConditionalHandle h, const int* cnt, int thr) {
+    cudaGraphSetConditional(h, *cnt > thr ? 1u : 0u);
+}
+
 __global__ void k_finalize(const Ctrl* ctrl, dd_result_t* out) {
     if (threadIdx.x != 0) return;
     dd_result_t r;
@@ -480,7 +493,7 @@ struct Seq {
         int wave = -1;
         if (p->nwaves < kMaxWaves) {
             wave = p->nwaves++;
-            p->waves[wave] = dd_plan_s::WaveMeta{kind, p->profiling ? p->ev_used : -1};
+            p->waves[wave] = dd_plan_s::WaveMeta{kind, (p->profiling && !p->in_cond) ? p->ev_used : -1};
         }
         if (!tc || force_fp32) {
             ScanArgs a{};
@@ -575,20 +588,82 @@ struct Seq {
     // Order-preserving compaction of `in` into `out`; returns the new list.
     int p_lo = 0, p_hi = 0;  // this search's shard of the mean order
 
-    ListRef compact(ListRef in, int32_t* out, int pred, bool shard_only = false) {
+    // Launches between begin_if and end_if run only when *cnt > thr.  Inside a
+    // graph capture they form the body of a conditional node whose value a
+    // kernel sets on the device, so a skipped block costs one node instead of
+    // one per launch.  Outside a capture they are launched as usual (each of
+    // them checks the same gate itself).  No events are recorded in a body.
+    cudaStream_t saved = nullptr;
+    bool in_if = false;
+
+    void begin_if(const int* cnt, int thr) {
+        if (!p->capturing || err != cudaSuccess) return;
+        cudaStreamCaptureStatus st;
+        cudaGraph_t g = nullptr;
+        keep(cudaStreamGetCaptureInfo(s, &st, nullptr, &g));
+        cudaGraphConditionalHandle h{};
+        keep(cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault));
+        if (err != cudaSuccess) return;
+        k_set_cond<<<1, 1, 0, s>>>(h, cnt, thr);
+        p->launches++;
+        check();
+        const cudaGraphNode_t* deps = nullptr;
+        const cudaGraphEdgeData* ed = nullptr;
+        size_t nd = 0;
+        keep(cudaStreamGetCaptureInfo(s, &st, nullptr, &g, &deps, &ed, &nd));
+        cudaGraphNodeParams np{};
+        np.type = cudaGraphNodeTypeConditional;
+        np.conditional.handle = h;
+        np.conditional.type = cudaGraphCondTypeIf;
+        np.conditional.size = 1;
+        cudaGraphNode_t cn = nullptr;
+        keep(cudaGraphAddNode(&cn, g, deps, ed, nd, &np));
+        if (err != cudaSuccess) return;
+        keep(cudaStreamUpdateCaptureDependencies(s, &cn, nullptr, 1, cudaStreamSetCaptureDependencies));
+        keep(cudaStreamBeginCaptureToGraph(p->body_stream, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                           cudaStreamCaptureModeThreadLocal));
+        if (err != cudaSuccess) return;
+        saved = s;
+        s = p->body_stream;
+        in_if = true;
+        p->in_cond = true;
+    }
+
+    void end_if() {
+        if (!in_if) return;
+        cudaGraph_t body = nullptr;
+        keep(cudaStreamEndCapture(s, &body));
+        s = saved;
+        in_if = false;
+        p->in_cond = false;
+    }
+
+    // cnt_out: write the count there instead of a new slot (refreshing a list in place)
+    ListRef compact(ListRef in, int32_t* out, int pred, bool shard_only = false, int* cnt_out = nullptr) {
         const int nblk = (int)((p->N + kCompactRows - 1) / kCompactRows);
-        const int slot = cnt_slot++;
-        if (cnt_slot > kMaxListSlots) {
-            err = cudaErrorInvalidValue;
-            return in;
+        int* cnt = cnt_out;
+        if (!cnt) {
+            const int slot = cnt_slot++;
+            if (cnt_slot > kMaxListSlots) {
+                err = cudaErrorInvalidValue;
+                return in;
+            }
+            cnt = cnt_ptr(slot);
         }
         k_compact_flags<<<nblk, 256, 0, s>>>(in, p->rmin, tb, p->ctrl, pred, p->code, p->hist, p->opt.phase1_max,
                                              shard_only ? p->sigpos : nullptr, p_lo, p_hi, p->flag, p->blk);
-        k_compact_scan<<<1, 1024, 0, s>>>(p->blk, nblk, cnt_ptr(slot));
+        k_compact_scan<<<1, 1024, 0, s>>>(p->blk, nblk, cnt);
         k_compact_scatter<<<nblk, 256, 0, s>>>(in, p->flag, p->blk, out);
         p->launches += 3;
         check();
-        return ListRef{out, nullptr, cnt_ptr(slot)};
+        return ListRef{out, nullptr, cnt};
+    }
+
+    // dst[0, *src.cnt) = src rows, count into cnt_out
+    void copy_list(ListRef src, int32_t* dst, int* cnt_out) {
+        k_copy_list<<<p->sm_count * 2, 256, 0, s>>>(src, dst, cnt_out);
+        p->launches++;
+        check();
     }
 
     void complete(ListRef in) {
@@ -599,8 +674,12 @@ struct Seq {
     }
 
     // gate: skip (select nothing) unless *gate > k
+    int topk_calls = 0;
     void topk(ListRef in, int k, const int* gate = nullptr) {
-        keep(cudaMemsetAsync(p->ctrl->topk_hist, 0, sizeof(p->ctrl->topk_hist) + sizeof(p->ctrl->topk_hist2), s));
+        // the control block starts zeroed: only later calls clear the histograms
+        if (topk_calls++ > 0)
+            keep(cudaMemsetAsync(p->ctrl->topk_hist, 0, sizeof(p->ctrl->topk_hist) + sizeof(p->ctrl->topk_hist2),
+                                 s));
         for (int pass = 0; pass < 2; pass++) {
             k_topk_hist<<<2 * p->sm_count, 256, 0, s>>>(in, p->rmin, tb, p->ctrl, pass, gate, k);
             k_topk_thr<<<1, 1024, 0, s>>>(p->ctrl, k, pass, gate);
@@ -688,32 +767,35 @@ cudaError_t launch_search(dd_plan_s* p, const float* T, dd_result_t* out_dev, cu
             ListRef top = q.compact(alive, p->list[2], 1);
             q.full(DD_WAVE_TOP, top);
         }
+        // rows still alive after the top wave (recomputed below if more waves run)
+        ListRef rest = q.compact(alive, p->list[2], 0);
         // Algorithm 4 scans a row's other candidates in index order, which for a
         // periodic series meets a match one period away; the mean order scatters
-        // those.  So every surviving row (in time order) first scans the columns
-        // just outside its exclusion zone, with direct FP32 differences (in the
-        // Gram form their rigorous upper bounds go to rmin32).
+        // those.  So when more than refine_k rows survive, every one of them (in
+        // time order) first scans the columns just outside its exclusion zone,
+        // with direct FP32 differences (in the Gram form their rigorous upper
+        // bounds go to rmin32).  Those bounds are close to each row's nearest-
+        // neighbour distance where the first-wave bounds of a periodic series are
+        // not, so the rows are ranked again and the new top rows fully scanned:
+        // the best-so-far then reaches the discord before the rest.
+        q.begin_if(rest.cnt_dev, o.refine_k);
         ListRef tl = q.compact(q.constant_list(p->seq_rows, (int)p->N), p->list[3], 0, true);
         q.scan(DD_WAVE_TIME, tl, ColSpec{4, 0, 0, kTimeCols}, 1, nullptr, false, true, o.refine_k);
         if (o.refine_k > 0) {
-            // The time-local bounds are close to each row's nearest-neighbour
-            // distance, where the first-wave bounds of a periodic series are not:
-            // rank again and fully scan the new top rows, so that the best-so-far
-            // reaches the discord before the rest.  This wave and the time-local
-            // one are skipped on the device when no more than refine_k rows are
-            // still alive (those go straight to the rest).
-            q.topk(alive, o.refine_k, tl.cnt_dev);
-            ListRef top2 = q.compact(alive, p->list[2], 1);
+            q.topk(alive, o.refine_k, rest.cnt_dev);
+            ListRef top2 = q.compact(alive, p->list[0], 1);
             q.full(DD_WAVE_TOP, top2);
         }
+        q.compact(alive, p->list[2], 0, false, const_cast<int*>(rest.cnt_dev));  // refresh `rest`
+        q.end_if();
         // Algorithm 4 (RefineDiscord) over the remaining rows: rows sharing the
         // SAX word first (Index_Word), then every column the bound allows.
         if (o.word_cols > 0 && !q.tc) {
             ListRef words = q.constant_list(p->order, (int)p->N);
             ListRef wl = q.compact(words, p->list[3], 0);
             q.scan(DD_WAVE_WORD, wl, ColSpec{1, 0, 0, o.word_cols}, 1);
+            rest = q.compact(alive, p->list[2], 0);
         }
-        ListRef rest = q.compact(alive, p->list[2], 0);
         q.full(DD_WAVE_REST, rest);
     }
     join();
@@ -725,14 +807,18 @@ cudaError_t launch_search(dd_plan_s* p, const float* T, dd_result_t* out_dev, cu
             // direct FP32 full scans, whose error bound is far tighter, and raise the
             // best-so-far with their FP32 lower bounds.  Skipped on the device for
             // short lists.
+            q.begin_if(cands.cnt_dev, kSettleMin);
             const int* sm = q.ranges(cands, 1, 0);
             q.scan(DD_WAVE_SETTLE, cands, ColSpec{2, 0, 0, 0}, 1, sm, false, true, kSettleMin);
             const int g = (int)((p->N + 1023) / 1024);
-            k_complete32<<<g < 1024 ? g : 1024, 256, 0, s>>>(cands, p->rmin, q.tb, p->stats, p->n, kSettleMin,
-                                                             p->ctrl);
+            k_complete32<<<g < 1024 ? g : 1024, 256, 0, q.s>>>(cands, p->rmin, q.tb, p->stats, p->n, kSettleMin,
+                                                               p->ctrl);
             p->launches++;
             q.check();
-            cands = q.compact(cands, p->list[2], 0);
+            // the survivors, back in place of the candidate list
+            ListRef c2 = q.compact(cands, p->list[2], 0);
+            q.copy_list(c2, p->list[3], const_cast<int*>(cands.cnt_dev));
+            q.end_if();
         }
         // every row the bounds cannot rule out, rescored exactly in FP64
         q.keep(launch_rescore(p, cands, q.tb, q.work_slot++, out_dev, s));

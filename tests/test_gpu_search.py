@@ -209,6 +209,8 @@ def test_wave_trace(precision):
             kinds = [w["kind"] for w in waves]
             assert "cand" in kinds and "rest" in kinds, kinds
             assert kinds[-1] == ("settle" if precision != "fp32" else "rest"), kinds
-            assert all(w["ms"] >= 0.0 for w in waves), waves
+            # waves inside conditional graph bodies (run only when many rows survive) are not timed
+            timed = [w for w in waves if w["ms"] >= 0.0]
+            assert {w["kind"] for w in timed} >= {first, "cand", "rest"}, waves
             assert all(w["items"] >= 0 and w["rows"] >= 0 for w in waves)
-            assert p.profile()["dist_launches"] == len(waves)
+            assert p.profile()["dist_launches"] == len(timed)
