@@ -280,6 +280,9 @@ def main():
     ap.add_argument("--precision", default="best", choices=["best", "all", "fp32", "tc_fp16", "tc_bf16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 512-series batched search")
+    ap.add_argument("--eager", action="store_true",
+                    help="enqueue each search's kernels directly instead of replaying its CUDA graph "
+                         "(per-kernel profilers cannot profile kernels of graphs with conditional nodes)")
     ap.add_argument("--no-serve", action="store_true", help="skip the Poisson serving run (p50/p99)")
     ap.add_argument("--no-exhaustive", action="store_true",
                     help="skip the exhaustive-mode (no abandon) pair-distances/s of each form")
@@ -348,6 +351,8 @@ def main():
     for prec in forms:
         plan = dd.Plan(m, n, prec)
         plan.set_profiling(True)
+        if args.eager:
+            plan.set_graph(False)
         for _ in range(args.warmup):
             plan.find_discord(Td)
         torch.cuda.synchronize()

@@ -213,6 +213,14 @@ typedef struct {
 } dd_profile_t;
 
 DD_API dd_status_t dd_plan_set_profiling(dd_plan_t plan, int32_t enable);
+
+/* Synchronous and asynchronous searches are captured once into a CUDA graph
+ * and replayed (enable = 1, the default).  enable = 0 enqueues the kernels
+ * directly on every call instead -- the same kernels, with the waves that run
+ * only when many rows survive checking their own gate on the device.  For
+ * per-kernel profilers, which cannot profile the kernels of a graph that
+ * holds conditional nodes.  Errors: DD_EINVAL, DD_EBUSY. */
+DD_API dd_status_t dd_plan_set_graph(dd_plan_t plan, int32_t enable);
 DD_API dd_status_t dd_plan_get_profile(dd_plan_t plan, dd_profile_t* out);
 
 /* Waves of distance tiles of the last call (tracing).  A search runs its

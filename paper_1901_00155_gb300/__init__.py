@@ -217,6 +217,10 @@ class Plan:
     def last_launches(self) -> int:
         return int(self._lib.dd_plan_last_launches(self._ptr))
 
+    def set_graph(self, enable: bool = True):
+        """Replay searches from a captured CUDA graph (default) or enqueue them directly."""
+        _check(self._lib.dd_plan_set_graph(self._ptr, 1 if enable else 0), "dd_plan_set_graph")
+
     def set_profiling(self, enable: bool = True):
         _check(self._lib.dd_plan_set_profiling(self._ptr, 1 if enable else 0), "dd_plan_set_profiling")
 

@@ -82,6 +82,7 @@ SIGNATURES = {
     "dd_status_string": ([ctypes.c_int], ctypes.c_char_p),
     "dd_plan_set_profiling": ([ctypes.c_void_p, ctypes.c_int32], ctypes.c_int),
     "dd_plan_get_profile": ([ctypes.c_void_p, ctypes.POINTER(Profile)], ctypes.c_int),
+    "dd_plan_set_graph": ([ctypes.c_void_p, ctypes.c_int32], ctypes.c_int),
     "dd_plan_get_waves": ([ctypes.c_void_p, ctypes.POINTER(Wave), ctypes.c_int32], ctypes.c_int32),
     "dd_nn_profile_static": ([ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p],
                              ctypes.c_int),

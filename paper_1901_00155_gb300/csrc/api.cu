@@ -612,6 +612,14 @@ int32_t dd_plan_get_waves(dd_plan_t p, dd_wave_t* out, int32_t cap) {
     return nw;
 }
 
+dd_status_t dd_plan_set_graph(dd_plan_t p, int32_t enable) {
+    if (!p) return DD_EINVAL;
+    BusyGuard g(p);
+    if (!g.ok) return DD_EBUSY;
+    p->use_graph = enable != 0;
+    return DD_OK;
+}
+
 dd_status_t dd_plan_get_profile(dd_plan_t p, dd_profile_t* out) {
     if (!p || !out) return DD_EINVAL;
     *out = p->prof;

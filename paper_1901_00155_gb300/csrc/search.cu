@@ -26,6 +26,7 @@ __device__ __forceinline__ uint32_t rank_bits(const TcBound& b, int i, uint32_t 
 
 __device__ __forceinline__ bool is_alive(const TcBound& b, int i, uint32_t rbits, uint32_t bsf_bits) {
     if (!b.on) return rbits >= bsf_bits;
+    if (bsf_bits == 0) return true;  // nothing has completed: every upper bound reaches bsf = 0
     return !(row_ub(b, i, __uint_as_float(rbits)) < __uint_as_float(bsf_bits));
 }
 
@@ -72,39 +73,30 @@ __global__ void __launch_bounds__(256) k_compact_flags(ListRef in, const uint32_
 }
 
 // Compaction pass 2: exclusive scan of the block counts (one block).
-__global__ void __launch_bounds__(1024) k_compact_scan(int* blk, int nblk, int* cnt_out) {
-    __shared__ int part[1024];
-    const int per = (nblk + 1023) / 1024;
-    const int lo = threadIdx.x * per, hi = min(nblk, lo + per);
-    int s = 0;
-    for (int b = lo; b < hi; b++) s += blk[b];
-    part[threadIdx.x] = s;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int run = 0;
-        for (int t = 0; t < 1024; t++) {
-            int x = part[t];
-            part[t] = run;
-            run += x;
-        }
-        *cnt_out = run;
-    }
-    __syncthreads();
-    int run = part[threadIdx.x];
-    for (int b = lo; b < hi; b++) {
-        int x = blk[b];
-        blk[b] = run;
-        run += x;
-    }
-}
-
-// Compaction pass 3: order-preserving scatter of the kept entries.
+// Compaction pass 2: each block adds up the counts of the blocks before it
+// (at most a few hundred, from L2) for its base, then scatters its kept rows in
+// order; block 0 also writes the total count.
 __global__ void __launch_bounds__(256) k_compact_scatter(ListRef in, const uint8_t* __restrict__ flag,
-                                                         const int* __restrict__ blk, int32_t* __restrict__ out) {
+                                                         const int* __restrict__ blk, int nblk,
+                                                         int32_t* __restrict__ out, int* __restrict__ cnt_out) {
     __shared__ int wsum[8];
+    __shared__ int red[8];
     const int cnt = *in.cnt_dev;
     const int off = in.off_dev ? *in.off_dev : 0;
     const int base = blockIdx.x * kCompactRows + threadIdx.x * 8;
+    const int lim = blockIdx.x == 0 ? nblk : blockIdx.x;  // block 0: every block, for the total
+    int pre = 0;
+    for (int b = threadIdx.x; b < lim; b += blockDim.x) pre += blk[b];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) pre += __shfl_xor_sync(0xffffffffu, pre, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = pre;
+    __syncthreads();
+    pre = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); w++) pre += red[w];
+    if (blockIdx.x == 0) {
+        if (threadIdx.x == 0) *cnt_out = pre;
+        pre = 0;
+    }
     if (blockIdx.x * kCompactRows >= cnt) return;
     int f[8], local = 0;
 #pragma unroll
@@ -124,7 +116,7 @@ __global__ void __launch_bounds__(256) k_compact_scatter(ListRef in, const uint8
     __syncthreads();
     int wbase = 0;
     for (int q = 0; q < wid; q++) wbase += wsum[q];
-    int pos = blk[blockIdx.x] + wbase + incl - local;
+    int pos = pre + wbase + incl - local;
 #pragma unroll
     for (int q = 0; q < 8; q++) {
         if (f[q]) out[pos++] = in.base[off + base + q];
@@ -652,9 +644,8 @@ struct Seq {
         }
         k_compact_flags<<<nblk, 256, 0, s>>>(in, p->rmin, tb, p->ctrl, pred, p->code, p->hist, p->opt.phase1_max,
                                              shard_only ? p->sigpos : nullptr, p_lo, p_hi, p->flag, p->blk);
-        k_compact_scan<<<1, 1024, 0, s>>>(p->blk, nblk, cnt);
-        k_compact_scatter<<<nblk, 256, 0, s>>>(in, p->flag, p->blk, out);
-        p->launches += 3;
+        k_compact_scatter<<<nblk, 256, 0, s>>>(in, p->flag, p->blk, nblk, out, cnt);
+        p->launches += 2;
         check();
         return ListRef{out, nullptr, cnt};
     }

@@ -214,3 +214,18 @@ def test_wave_trace(precision):
             assert {w["kind"] for w in timed} >= {first, "cand", "rest"}, waves
             assert all(w["items"] >= 0 and w["rows"] >= 0 for w in waves)
             assert p.profile()["dist_launches"] == len(timed)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "tc_fp16"])
+def test_eager_equals_graph(precision):
+    """dd_plan_set_graph(0): the same search enqueued directly (its conditional waves gate
+    themselves on the device) gives the graph replay's result."""
+    dd = _dd()
+    for spec in (synth.workloads_medium()[2], synth.SeriesSpec("sine", 60000, 512, 7, ("spike",))):
+        T, _ = synth.make_series(spec)
+        Td = torch.from_numpy(T).cuda()
+        with dd.Plan(T.size, spec.n, precision) as p:
+            g = p.find_discord(Td)
+            p.set_graph(False)
+            e = p.find_discord(Td)
+        assert (g.index, g.nn_distance) == (e.index, e.nn_distance), (spec, g, e)
