@@ -165,6 +165,17 @@ DD_API dd_status_t dd_find_discord_async(dd_plan_t plan, const float* T_dev, dd_
  * result back, waits.  Errors as dd_find_discord. */
 DD_API dd_status_t dd_find_discord_host(dd_plan_t plan, const float* T_host, dd_result_t* out, void* stream);
 
+/* Top-k discords (not in the paper's algorithms; the usual extension of its
+ * definition): out[0] is the discord; out[j] is the subsequence with the
+ * largest nearest-neighbour distance (ties to the smallest index) among those
+ * at least n away from out[0 .. j-1] (|i - out[l].index| >= n).  Nearest
+ * neighbours are unchanged: any non-self match counts.  k searches in turn,
+ * each excluding the rows near the discords found so far; out holds k
+ * results in host memory, and entries past the last possible discord have
+ * index -1.  Synchronous on `stream`.  Errors as dd_find_discord, DD_EINVAL
+ * for k < 1. */
+DD_API dd_status_t dd_find_discords(dd_plan_t plan, const float* T_dev, int32_t k, dd_result_t* out, void* stream);
+
 /* Independent searches over `count` series of possibly different lengths
  * and subsequence lengths (T_dev[k]: m[k] float32 values on the device,
  * n[k]); one options struct for all (NULL = defaults).  Results go to

@@ -140,6 +140,23 @@ def discord_brute(T, n: int):
     return int(idx.value), float(d2.value)
 
 
+def discords_brute(T, n: int, k: int):
+    """Top-k discords by definition: repeatedly the largest nearest non-self-match distance
+    (first maximiser = smallest index), among subsequences at least n away from those already
+    chosen.  Returns [(index, nn2)]."""
+    nn2 = nn_profile(T, n)
+    allowed = np.ones(nn2.size, dtype=bool)
+    out = []
+    for _ in range(k):
+        if not allowed.any():
+            break
+        cand = np.where(allowed, nn2, -np.inf)
+        i = int(np.argmax(cand))
+        out.append((i, float(nn2[i])))
+        allowed[max(0, i - n + 1):min(nn2.size, i + n)] = False
+    return out
+
+
 def window_stats(T, n: int):
     """(mu_w, c_w) float64[N]: mean and centred sum of squares of each row."""
     T = _f32(T)

@@ -217,6 +217,15 @@ class Plan:
     def last_launches(self) -> int:
         return int(self._lib.dd_plan_last_launches(self._ptr))
 
+    def find_discords(self, T, k: int, stream=None) -> list:
+        """Top-k discords: each the largest nearest-neighbour distance among the subsequences at
+        least n away from the previous ones (dd_find_discords); fewer than k when rows run out."""
+        _check_series(T, self.m)
+        out = (_lib.Result * int(k))()
+        _check(self._lib.dd_find_discords(self._ptr, ctypes.c_void_p(T.data_ptr()), int(k), out,
+                                          _stream_ptr(stream)), "dd_find_discords")
+        return [_as_result(r) for r in out if r.index >= 0]
+
     def set_graph(self, enable: bool = True):
         """Replay searches from a captured CUDA graph (default) or enqueue them directly."""
         _check(self._lib.dd_plan_set_graph(self._ptr, 1 if enable else 0), "dd_plan_set_graph")

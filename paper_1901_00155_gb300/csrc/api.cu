@@ -92,6 +92,7 @@ size_t carve(dd_plan_s* p, char* base) {
     p->flag = c.take<uint8_t>(N);
     p->blk = c.take<int32_t>(nblk + 1);
     p->res_dev = c.take<dd_result_t>(1);
+    p->excl = c.take<uint8_t>(N);
     p->seq_rows = c.take<int32_t>(N);
     p->mubin = c.take<int32_t>(N);
     p->hist_mu = c.take<int32_t>(dd::kMuBins);
@@ -115,6 +116,11 @@ size_t carve(dd_plan_s* p, char* base) {
         p->rmin32 = c.take<uint32_t>(N);
     }
     return (c.off + kAlign - 1) / kAlign * kAlign;
+}
+
+__global__ void k_mark(uint8_t* a, int64_t lo, int64_t hi) {
+    const int64_t i = lo + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < hi) a[i] = 1;
 }
 
 __global__ void k_iota(int32_t* a, int64_t n) {
@@ -359,6 +365,7 @@ dd_status_t create_plan(dd_plan_s** plan, int64_t m, int32_t n, const dd_options
     e = cudaMemcpyAsync(p->beta, p->beta_host, sizeof(double) * (o.alphabet - 1), cudaMemcpyHostToDevice, init);
     if (e == cudaSuccess) e = cudaMemsetAsync(p->t64 + p->m, 0, sizeof(double) * kPad, init);
     if (e == cudaSuccess) e = cudaMemsetAsync(p->t32 + p->m, 0, sizeof(float) * kPad, init);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->excl, 0, (size_t)p->N, init);
     if (e == cudaSuccess) {
         k_iota<<<(unsigned)((p->N + 255) / 256), 256, 0, init>>>(p->seq_rows, p->N);
         e = cudaGetLastError();
@@ -448,6 +455,42 @@ dd_status_t dd_find_discord(dd_plan_t p, const float* T_dev, dd_result_t* out, v
     BusyGuard g(p);
     if (!g.ok) return DD_EBUSY;
     return search_sync(p, T_dev, out, static_cast<cudaStream_t>(stream));
+}
+
+dd_status_t dd_find_discords(dd_plan_t p, const float* T_dev, int32_t k, dd_result_t* out, void* stream) {
+    if (!p || !T_dev || !out || k < 1) return DD_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int64_t N = p->N, n = p->n;
+    std::vector<uint8_t> ex((size_t)N, 0);  // host copy of the exclusion mask, to know when rows run out
+    int64_t left = N;
+    dd_status_t st = DD_OK;
+    int32_t j = 0;
+    for (; j < k && left > 0; j++) {
+        st = dd_find_discord(p, T_dev, &out[j], stream);
+        if (st != DD_OK || out[j].index < 0) {
+            j++;
+            break;
+        }
+        const int64_t d = out[j].index;
+        const int64_t lo = d - n + 1 > 0 ? d - n + 1 : 0, hi = d + n < N ? d + n : N;
+        for (int64_t i = lo; i < hi; i++) left -= ex[(size_t)i] ? 0 : 1, ex[(size_t)i] = 1;
+        k_mark<<<(unsigned)((hi - lo + 255) / 256), 256, 0, s>>>(p->excl, lo, hi);
+        if (cudaGetLastError() != cudaSuccess) {
+            st = DD_ECUDA;
+            j++;
+            break;
+        }
+    }
+    for (; j < k; j++) {
+        std::memset(&out[j], 0, sizeof(dd_result_t));
+        out[j].index = -1;
+        out[j].status = DD_OK;
+    }
+    // leave the mask cleared for ordinary searches
+    cudaError_t e = cudaMemsetAsync(p->excl, 0, (size_t)N, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess && st == DD_OK) st = DD_ECUDA;
+    return st;
 }
 
 dd_status_t dd_find_discord_async(dd_plan_t p, const float* T_dev, dd_result_t* out_dev, void* stream) {

@@ -133,6 +133,7 @@ struct TcBound {
     float beta;
     int on;
     const uint32_t* r32;  // may be null
+    const uint8_t* excl;  // rows that may not be a discord (top-k search); all zero otherwise
 };
 
 __device__ __forceinline__ float row_ub(const TcBound& b, int i, float D) {
@@ -243,7 +244,8 @@ struct dd_plan_s {
     int32_t* order = nullptr;
     int32_t* pos_of = nullptr;
     uint32_t* rmin = nullptr;
-    uint32_t* rmin32 = nullptr;  // Gram form: FP32 upper bounds from the time-local wave (TcBound::r32)
+    uint32_t* rmin32 = nullptr;
+    uint8_t* excl = nullptr;     // per row: 1 = excluded from being the discord (dd_find_discords)  // Gram form: FP32 upper bounds from the time-local wave (TcBound::r32)
     int32_t* list[4] = {nullptr, nullptr, nullptr, nullptr};
     uint8_t* flag = nullptr;
     int32_t* blk = nullptr;

@@ -25,6 +25,7 @@ __device__ __forceinline__ uint32_t rank_bits(const TcBound& b, int i, uint32_t 
 }
 
 __device__ __forceinline__ bool is_alive(const TcBound& b, int i, uint32_t rbits, uint32_t bsf_bits) {
+    if (b.excl && b.excl[i]) return false;  // may not be the discord: never a candidate, never completes
     if (!b.on) return rbits >= bsf_bits;
     if (bsf_bits == 0) return true;  // nothing has completed: every upper bound reaches bsf = 0
     return !(row_ub(b, i, __uint_as_float(rbits)) < __uint_as_float(bsf_bits));
@@ -453,6 +454,7 @@ struct Seq {
             tb.on = 1;
             tb.r32 = p->rmin32;
         }
+        tb.excl = p->excl;
     }
 
     void check() {

@@ -229,3 +229,22 @@ def test_eager_equals_graph(precision):
             p.set_graph(False)
             e = p.find_discord(Td)
         assert (g.index, g.nn_distance) == (e.index, e.nn_distance), (spec, g, e)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "tc_fp16"])
+def test_top_k_discords(precision):
+    """dd_find_discords against the oracle's definition, and the plan searches normally after."""
+    dd = _dd()
+    for spec, k in ((synth.workload_small(), 4), (synth.SeriesSpec("sine", 30000, 128, 5, ("spike", "burst", "flat")), 3)):
+        T, _ = synth.make_series(spec)
+        Td = torch.from_numpy(T).cuda()
+        ref = oracle.discords_brute(T, spec.n, k)
+        with dd.Plan(T.size, spec.n, precision) as p:
+            got = p.find_discords(Td, k)
+            again = p.find_discord(Td)
+        assert len(got) == len(ref)
+        for g, (i, d2) in zip(got, ref):
+            assert g.nn_distance == pytest.approx(math.sqrt(d2), rel=RTOL if precision == "fp32" else 1e-6)
+            if precision != "fp32":
+                assert g.index == i
+        assert again.index == ref[0][0]

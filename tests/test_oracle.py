@@ -341,3 +341,30 @@ def test_znorm_closed_form():
     np.testing.assert_allclose(t, (np.array([1, 2, 3, 4]) - 2.5) / math.sqrt(1.25), rtol=1e-15)
     t0, _, s0 = oracle.znorm(np.full(5, 2.0, np.float32))
     assert s0 == 0.0 and np.all(t0 == 0.0)
+
+
+def test_discords_brute_definition():
+    """Top-k discords: the first is the discord; every later one is the largest nn among the
+    subsequences at least n from all earlier ones (rechecked by a plain loop); distances do not
+    increase; chosen indices are pairwise at least n apart."""
+    rng = np.random.default_rng(77)
+    for trial in range(20):
+        n = int(rng.choice([2, 3, 5, 8]))
+        T = np.cumsum(rng.standard_normal(int(rng.integers(6 * n, 6 * n + 60)))).astype(np.float32)
+        k = 4
+        got = oracle.discords_brute(T, n, k)
+        i0, d0 = oracle.discord_brute(T, n)
+        assert got[0][0] == i0 and got[0][1] == d0
+        nn2 = oracle.nn_profile(T, n)
+        chosen = []
+        for idx, v in got:
+            best = None
+            for i in range(nn2.size):
+                if any(abs(i - c) < n for c in chosen):
+                    continue
+                if best is None or nn2[i] > nn2[best]:
+                    best = i
+            assert idx == best and v == nn2[best]
+            chosen.append(idx)
+        assert all(a[1] >= b[1] for a, b in zip(got, got[1:]))
+        assert all(abs(a - b) >= n for x, a in enumerate(chosen) for b in chosen[x + 1:])
