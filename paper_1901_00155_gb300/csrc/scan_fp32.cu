@@ -10,6 +10,12 @@
 // Work items are handed out dynamically through an atomic counter (the
 // GPU counterpart of the paper's dynamic OpenMP schedule).
 //
+// Column sets: see ColSpec (mean-order ranges, word buckets, lower-bound
+// segments, time-local windows).  In a Gram-form plan this kernel runs the
+// time-local and settle waves: it then tests rows against the Gram bound and
+// publishes rigorous FP32 upper bounds to r32 (see TcBound) instead of plain
+// minima.
+//
 // Tile arithmetic: 256 threads, each an 8x8 register micro-tile of
 // (row, column) pairs; k is staged through shared memory in chunks of 32 with
 // cp.async double buffering; rows and columns are gathered by index, each

@@ -4,8 +4,15 @@
 //   stream compaction of the surviving rows between waves, and the final
 //   argmax (Algorithm 1's best-so-far update, ties -> smallest index).
 //
-// Everything is enqueued on one stream with all counts kept on the device,
-// so a search needs no host round trip and can be captured in a CUDA graph.
+// Waves, in order: the first (nearest-mean) wave for every row; the fill
+// wave (Gram form) for rows it left unbounded; Cand; the rows with the largest
+// upper bounds; when many rows survive, the time-local wave (Algorithm 4's
+// index-order scan) and a second top-k; the word wave (FP32 form); the rest;
+// and in the Gram form an FP32 settle wave before the FP64 rescoring when many
+// candidates remain.  Everything is enqueued on one stream (the SAX words on
+// a side branch) with all counts kept on the device, so a search needs no
+// host round trip and is captured once into a CUDA graph, whose conditional
+// nodes skip the waves that are not needed.
 #include "dd_internal.cuh"
 
 namespace dd {
@@ -13,10 +20,6 @@ namespace {
 
 __global__ void k_set_int(int* p, int v) { *p = v; }
 
-// A row is alive unless one of its distances is proven strictly below the
-// best-so-far: FP32 form D < bsf (Algorithms 3/4); Gram form D + F_i(D) < bsf,
-// bsf being a proven lower bound there.  Non-negative floats order like their
-// bit patterns.
 // The value rows are ranked by for the top-k waves: the running minimum, or in
 // the Gram form the smaller of it and the row's FP32 upper bound (non-negative
 // floats order like their bit patterns).
@@ -24,6 +27,11 @@ __device__ __forceinline__ uint32_t rank_bits(const TcBound& b, int i, uint32_t 
     return b.r32 ? min(rbits, b.r32[i]) : rbits;
 }
 
+// A row is alive unless one of its distances is proven strictly below the
+// best-so-far: FP32 form D < bsf (Algorithms 3/4); Gram form min(D + F_i(D),
+// r32_i) < bsf, bsf being a proven lower bound there.  Rows excluded from being
+// the discord (top-k search) are never alive.  Non-negative floats order like
+// their bit patterns.
 __device__ __forceinline__ bool is_alive(const TcBound& b, int i, uint32_t rbits, uint32_t bsf_bits) {
     if (b.excl && b.excl[i]) return false;  // may not be the discord: never a candidate, never completes
     if (!b.on) return rbits >= bsf_bits;
