@@ -232,6 +232,16 @@ DD_API dd_status_t dd_plan_set_profiling(dd_plan_t plan, int32_t enable);
  * per-kernel profilers, which cannot profile the kernels of a graph that
  * holds conditional nodes.  Errors: DD_EINVAL, DD_EBUSY. */
 DD_API dd_status_t dd_plan_set_graph(dd_plan_t plan, int32_t enable);
+
+/* Fault injection for tests of the failure handling (no GPU fault is
+ * involved).  DD_INJECT_STALL_TC: the plan's next tensor-core distance launch
+ * arms its operand stages but issues no copy, so its bounded waits expire
+ * (about 2 s); the call then returns DD_ETIMEOUT, the rest of that search is
+ * skipped, and the plan stays usable.  Consumed by that launch; with graph
+ * capture on, it takes effect only when the graph is captured next, so tests
+ * turn capture off (dd_plan_set_graph(plan, 0)).  Errors: DD_EINVAL, DD_EBUSY. */
+enum { DD_INJECT_NONE = 0, DD_INJECT_STALL_TC = 1 };
+DD_API dd_status_t dd_plan_inject(dd_plan_t plan, int32_t what);
 DD_API dd_status_t dd_plan_get_profile(dd_plan_t plan, dd_profile_t* out);
 
 /* Waves of distance tiles of the last call (tracing).  A search runs its

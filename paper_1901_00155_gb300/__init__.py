@@ -226,6 +226,10 @@ class Plan:
                                           _stream_ptr(stream)), "dd_find_discords")
         return [_as_result(r) for r in out if r.index >= 0]
 
+    def inject(self, what: int):
+        """Fault injection for tests (dd_plan_inject): 1 = stall the next tensor-core launch."""
+        _check(self._lib.dd_plan_inject(self._ptr, int(what)), "dd_plan_inject")
+
     def set_graph(self, enable: bool = True):
         """Replay searches from a captured CUDA graph (default) or enqueue them directly."""
         _check(self._lib.dd_plan_set_graph(self._ptr, 1 if enable else 0), "dd_plan_set_graph")

@@ -83,6 +83,7 @@ SIGNATURES = {
     "dd_plan_set_profiling": ([ctypes.c_void_p, ctypes.c_int32], ctypes.c_int),
     "dd_plan_get_profile": ([ctypes.c_void_p, ctypes.POINTER(Profile)], ctypes.c_int),
     "dd_plan_set_graph": ([ctypes.c_void_p, ctypes.c_int32], ctypes.c_int),
+    "dd_plan_inject": ([ctypes.c_void_p, ctypes.c_int32], ctypes.c_int),
     "dd_find_discords": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(Result), ctypes.c_void_p],
                          ctypes.c_int),
     "dd_plan_get_waves": ([ctypes.c_void_p, ctypes.POINTER(Wave), ctypes.c_int32], ctypes.c_int32),

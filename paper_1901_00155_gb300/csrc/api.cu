@@ -663,6 +663,14 @@ dd_status_t dd_plan_set_graph(dd_plan_t p, int32_t enable) {
     return DD_OK;
 }
 
+dd_status_t dd_plan_inject(dd_plan_t p, int32_t what) {
+    if (!p || (what != DD_INJECT_NONE && what != DD_INJECT_STALL_TC)) return DD_EINVAL;
+    BusyGuard g(p);
+    if (!g.ok) return DD_EBUSY;
+    p->inject = what;
+    return DD_OK;
+}
+
 dd_status_t dd_plan_get_profile(dd_plan_t p, dd_profile_t* out) {
     if (!p || !out) return DD_EINVAL;
     *out = p->prof;

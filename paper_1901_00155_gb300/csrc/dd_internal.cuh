@@ -206,6 +206,7 @@ struct TcArgs {
     const uint32_t* r32;    // per orig row: FP32 upper bound of the time-local wave (see TcBound)
     const int32_t* sigpos;  // orig row -> position in the mean order
     int local_k;            // mode 2: > 0 limits row i to positions within local_k of its own
+    int stall;              // fault injection (tests): issue no operand copy
 };
 
 }  // namespace dd
@@ -291,6 +292,7 @@ struct dd_plan_s {
     int g_nwaves = 0;
     cudaStream_t side_stream = nullptr;
     cudaStream_t body_stream = nullptr;  // captures the bodies of conditional graph nodes
+    int inject = 0;                      // dd_plan_inject: consumed by the next distance launch
     bool in_cond = false;                // capturing a conditional body (no event nodes there)  // SAX / word order run here, beside the mean order
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     cudaGraphExec_t gexec = nullptr;

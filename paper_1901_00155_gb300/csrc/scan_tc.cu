@@ -245,7 +245,7 @@ __global__ void __launch_bounds__(kTcThreadsV2, 1)
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
     const Ctrl* ctrl = a.ctrl;
-    if (ctrl->nonfinite || ctrl->degenerate) return;
+    if (ctrl->nonfinite || ctrl->degenerate || ctrl->err) return;  // an earlier wave failed: fail fast
     const int cnt = *a.rows.cnt_dev;
     const int off = a.rows.off_dev ? *a.rows.off_dev : 0;
     if (blockIdx.x == 0 && tid == 0 && a.wave >= 0) a.ctrl->wave_rows[a.wave] = cnt;
@@ -511,13 +511,15 @@ __global__ void __launch_bounds__(kTcThreadsV2, 1)
                             break;
                         }
                         unsigned char* st = stages + stage * sbytes;
+                        // a.stall (fault injection for tests): arm the stage but issue no copy, so the
+                        // waits on it expire and the launch ends with DD_ETIMEOUT
                         if (band) {  // A rows come from inside the B tile
                             mbar_expect_tx(&h.b_full[stage], (uint32_t)kBBytesPerAtom);
                         } else {
                             mbar_expect_tx(&h.b_full[stage], (uint32_t)kStageBytes);
-                            tma_load_3d(st, &mapA, &h.b_full[stage], arow, ka);
+                            if (!a.stall) tma_load_3d(st, &mapA, &h.b_full[stage], arow, ka);
                         }
-                        tma_load_3d(st + boff, &mapB, &h.b_full[stage], p0, ka);
+                        if (!a.stall) tma_load_3d(st + boff, &mapB, &h.b_full[stage], p0, ka);
                         if (++stage == nst) {
                             stage = 0;
                             sph ^= 1u;

@@ -556,6 +556,8 @@ struct Seq {
         t.ranges = p->ranges;
         t.sigpos = p->sigpos;
         t.local_k = t.mode == 2 ? col.local_cols : 0;
+        t.stall = p->inject == DD_INJECT_STALL_TC ? 1 : 0;
+        p->inject = 0;
         t.smax = smax;
         t.rmin = p->rmin;
         t.ctrl = p->ctrl;

@@ -133,3 +133,22 @@ def test_long_subsequences(n, m):
     r = _search(T, n, "tc_fp16")
     i_ref, d2_ref = oracle.discord_brute(T, n)
     _check(T, n, r, i_ref, d2_ref)
+
+
+def test_expired_wait_reports_timeout_and_plan_stays_usable():
+    """Failure handling without a GPU fault: the injected stall leaves the tensor-core kernel's
+    operand stages armed but never filled, so its waits (bounded by %globaltimer) expire; the call
+    returns DD_ETIMEOUT, and the same plan then searches normally."""
+    import paper_1901_00155_gb300 as dd
+    spec = synth.workload_small()
+    T, _ = synth.make_series(spec)
+    Td = torch.from_numpy(T).cuda()
+    with dd.Plan(T.size, spec.n, "tc_fp16") as p:
+        p.set_graph(False)
+        ok = p.find_discord(Td)
+        p.inject(1)
+        with pytest.raises(dd.DDError) as ei:
+            p.find_discord(Td)
+        assert ei.value.status == 4  # DD_ETIMEOUT
+        again = p.find_discord(Td)
+        assert (again.index, again.nn_distance) == (ok.index, ok.nn_distance)
