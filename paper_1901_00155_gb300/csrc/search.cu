@@ -36,7 +36,11 @@ __device__ __forceinline__ bool is_alive(const TcBound& b, int i, uint32_t rbits
     if (b.excl && b.excl[i]) return false;  // may not be the discord: never a candidate, never completes
     if (!b.on) return rbits >= bsf_bits;
     if (bsf_bits == 0) return true;  // nothing has completed: every upper bound reaches bsf = 0
-    return !(row_ub(b, i, __uint_as_float(rbits)) < __uint_as_float(bsf_bits));
+    // min(D + F(D), r32) >= bsf, F >= 0: decided by D and r32 alone unless D < bsf <= r32
+    const float B = __uint_as_float(bsf_bits), D = __uint_as_float(rbits);
+    if (b.r32 && __uint_as_float(b.r32[i]) < B) return false;
+    if (!(D < B)) return true;
+    return !(D + (b.alpha[i] + b.beta * D + b.gam[i] * sqrtf(fmaxf(D, 0.f) + b.q2[i])) < B);
 }
 
 // Compaction pass 1: predicate per list entry + per-block counts.
@@ -57,10 +61,10 @@ __global__ void __launch_bounds__(256) k_compact_flags(ListRef in, const uint32_
     const uint32_t bsf = ctrl->bsf;
     const uint32_t thr = pred == 1 ? ctrl->topk_thr : (pred == 3 ? 0x7f000000u : 0u);
     int local = 0;
-    const int base = blockIdx.x * kCompactRows + threadIdx.x * 8;
+    // coalesced: entry q * 256 + t of the block's 2048 (the scatter pass reads the flags its own way)
 #pragma unroll
     for (int q = 0; q < 8; q++) {
-        const int r = base + q;
+        const int r = blockIdx.x * kCompactRows + q * 256 + threadIdx.x;
         if (r < cnt) {
             const int i = in.base[off + r];
             bool keep;
