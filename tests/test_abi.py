@@ -78,3 +78,35 @@ def test_product_path_does_not_import_oracle():
                 txt = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in txt and "from oracle" not in txt, f
                 assert "dd_oracle" not in txt, f
+
+
+def test_new_entry_points_reject_bad_arguments_without_device_work():
+    """Null handles and bad arguments are refused before any CUDA call."""
+    lib = _lib.load()
+    assert lib.dd_plan_get_waves(None, None, 0) == -_lib.DD_EINVAL
+    assert lib.dd_plan_set_graph(None, 1) == _lib.DD_EINVAL
+    assert lib.dd_plan_inject(None, 1) == _lib.DD_EINVAL
+    assert lib.dd_find_discords(None, None, 3, None, None) == _lib.DD_EINVAL
+    e = ctypes.c_void_p()
+    assert lib.dd_engine_create(ctypes.byref(e), 0, None, 8192, 128) == _lib.DD_EINVAL   # no workers
+    assert lib.dd_engine_create(ctypes.byref(e), 65, None, 8192, 128) == _lib.DD_EINVAL  # too many
+    assert lib.dd_engine_create(ctypes.byref(e), 2, None, 100, 40) == _lib.DD_EINVAL     # N < 2n
+    assert lib.dd_engine_create(None, 2, None, 8192, 128) == _lib.DD_EINVAL
+    assert e.value is None
+    assert lib.dd_engine_submit(None, 0, None, 10, 2, 0) == _lib.DD_EINVAL
+    assert lib.dd_engine_poll(None, None, 0, 0) == -_lib.DD_EINVAL
+    assert lib.dd_engine_outstanding(None) == 0
+    lib.dd_engine_destroy(None)
+    opts = _lib.Options()
+    lib.dd_options_default(ctypes.byref(opts))
+    assert opts.shard_count == 0 and opts.shard_index == 0
+    assert lib.dd_find_discord_batched(-1, None, None, None, None, None, None) == _lib.DD_EINVAL
+    assert lib.dd_find_discord_batched(0, None, None, None, None, None, None) == _lib.DD_OK
+
+
+def test_sharded_footprint_matches_unsharded():
+    """Sharding selects rows; the plan's device footprint does not change."""
+    import paper_1901_00155_gb300 as dd
+    for prec in ("fp32", "tc_fp16"):
+        a = dd.Plan.footprint(1 << 16, 256, prec)
+        assert a > 0 and dd.Plan.footprint(1 << 16, 256, prec, shard_count=4, shard_index=3) == a
