@@ -350,7 +350,8 @@ DD_API dd_status_t dd_engine_submit(dd_engine_t engine, int64_t id, const float*
 
 /* Moves up to cap finished requests to out[] (host memory), in the order
  * they finished.  When none is ready, waits up to wait_ms milliseconds
- * (negative: until one is).  Returns how many it moved, or -DD_EINVAL. */
+ * (negative: until one is; returns 0 at once when no request is
+ * outstanding).  Returns how many it moved, or -DD_EINVAL. */
 DD_API int32_t dd_engine_poll(dd_engine_t engine, dd_completion_t* out, int32_t cap, int32_t wait_ms);
 
 /* Requests submitted and not yet polled. */

@@ -209,6 +209,8 @@ dd_status_t dd_engine_submit(dd_engine_t E, int64_t id, const float* T, int64_t 
 int32_t dd_engine_poll(dd_engine_t E, dd_completion_t* out, int32_t cap, int32_t wait_ms) {
     if (!E || (cap > 0 && !out) || cap < 0) return -DD_EINVAL;
     std::unique_lock<std::mutex> lk(E->mu);
+    // nothing queued, running or finished: nothing to wait for
+    if (E->done.empty() && E->outstanding == 0) return 0;
     if (E->done.empty() && wait_ms != 0) {
         auto ready = [&] { return !E->done.empty(); };
         if (wait_ms < 0)
