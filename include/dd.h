@@ -207,7 +207,9 @@ DD_API dd_status_t dd_prep(dd_plan_t plan, const float* T_dev, void* stream);
 /* Device views of the preparation arrays of the last call on the plan. */
 DD_API dd_status_t dd_plan_view(dd_plan_t plan, dd_view_t* view);
 
-/* Number of this library's kernels launched by the plan's last call. */
+/* Number of this library's kernels launched by the plan's last call (a graph
+ * replay does not count the kernels of conditional waves it skipped).  Reads
+ * two device counters: call it after the call has finished. */
 DD_API int64_t dd_plan_last_launches(dd_plan_t plan);
 
 /* Per-call measurements of the distance kernels (tracing).  When enabled

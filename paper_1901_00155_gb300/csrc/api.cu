@@ -237,11 +237,13 @@ cudaError_t graph_launch(dd_plan_s* p, int kind, const float* T_dev, dd_result_t
         p->g_ev_used = used;
         p->g_nwaves = p->nwaves;
         for (int w = 0; w < p->nwaves; w++) p->g_waves[w] = p->waves[w];
+        p->g_bodies = p->bodies;
     }
     p->launches = p->g_launches;
     p->ev_used = p->g_ev_used;
     p->nwaves = p->g_nwaves;
     for (int w = 0; w < p->g_nwaves; w++) p->waves[w] = p->g_waves[w];
+    p->bodies = p->g_bodies;
     return cudaGraphLaunch(p->gexec, s);
 }
 
@@ -611,7 +613,20 @@ dd_status_t dd_plan_view(dd_plan_t p, dd_view_t* v) {
     return DD_OK;
 }
 
-int64_t dd_plan_last_launches(dd_plan_t p) { return p ? p->launches : -1; }
+int64_t dd_plan_last_launches(dd_plan_t p) {
+    if (!p) return -1;
+    // a graph replay skips the kernels of conditional bodies whose gate did not pass
+    int64_t n = p->launches;
+    for (const dd_plan_s::CondBody& b : p->bodies) {
+        int v = 1;
+        if (cudaMemcpy(&v, b.taken, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        if (v == 0) n -= b.launches;
+    }
+    return n;
+}
 
 dd_status_t dd_plan_set_profiling(dd_plan_t p, int32_t enable) {
     if (!p) return DD_EINVAL;

@@ -59,6 +59,7 @@ struct Ctrl {
     unsigned long long wave_pairs[kMaxWaves];  // per distance wave (by launch slot)
     unsigned long long wave_items[kMaxWaves];
     int wave_rows[kMaxWaves];
+    int cond[8];                  // value each conditional graph node of the search took (1 = body ran)
     int topk_bin;                 // top-k select: bin of the first pass holding the k-th row (-1: take all)
     int topk_need;                // rows still needed from that bin
     int topk_hist[kTopkBins];     // radix-select histogram, pass 1 (float bits >> 19)
@@ -293,6 +294,12 @@ struct dd_plan_s {
     cudaStream_t side_stream = nullptr;
     cudaStream_t body_stream = nullptr;  // captures the bodies of conditional graph nodes
     int inject = 0;                      // dd_plan_inject: consumed by the next distance launch
+    struct CondBody {
+        const int* taken; // device flag: the body ran (set by the node's condition kernel)
+        int64_t launches; // kernels inside the body
+    };
+    std::vector<CondBody> bodies;        // conditional bodies of the last captured call
+    std::vector<CondBody> g_bodies;      // the same for the cached graph
     bool in_cond = false;                // capturing a conditional body (no event nodes there)  // SAX / word order run here, beside the mean order
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     cudaGraphExec_t gexec = nullptr;

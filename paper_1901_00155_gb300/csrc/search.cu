@@ -395,8 +395,10 @@ __global__ void k_copy_list(ListRef src, int32_t* __restrict__ dst, int* __restr
 }
 
 // Value of a conditional graph node: run its body only when *cnt > thr.
-__global__ void k_set_cond(cudaGraphConditionalHandle h, const int* cnt, int thr) {
-    cudaGraphSetConditional(h, *cnt > thr ? 1u : 0u);
+__global__ void k_set_cond(cudaGraphConditionalHandle h, const int* cnt, int thr, int* taken) {
+    const unsigned v = *cnt > thr ? 1u : 0u;
+    cudaGraphSetConditional(h, v);
+    *taken = (int)v;
 }
 
 __global__ void k_finalize(const Ctrl* ctrl, dd_result_t* out) {
@@ -603,6 +605,9 @@ struct Seq {
     // them checks the same gate itself).  No events are recorded in a body.
     cudaStream_t saved = nullptr;
     bool in_if = false;
+    int* if_taken = nullptr;
+    int ncond = 0;
+    int64_t if_start = 0;
 
     void begin_if(const int* cnt, int thr) {
         if (!p->capturing || err != cudaSuccess) return;
@@ -612,7 +617,12 @@ struct Seq {
         cudaGraphConditionalHandle h{};
         keep(cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault));
         if (err != cudaSuccess) return;
-        k_set_cond<<<1, 1, 0, s>>>(h, cnt, thr);
+        if (ncond >= 8) {
+            err = cudaErrorInvalidValue;
+            return;
+        }
+        if_taken = &p->ctrl->cond[ncond++];
+        k_set_cond<<<1, 1, 0, s>>>(h, cnt, thr, if_taken);
         p->launches++;
         check();
         const cudaGraphNode_t* deps = nullptr;
@@ -635,6 +645,7 @@ struct Seq {
         s = p->body_stream;
         in_if = true;
         p->in_cond = true;
+        if_start = p->launches;
     }
 
     void end_if() {
@@ -644,6 +655,7 @@ struct Seq {
         s = saved;
         in_if = false;
         p->in_cond = false;
+        p->bodies.push_back(dd_plan_s::CondBody{if_taken, p->launches - if_start});
     }
 
     // cnt_out: write the count there instead of a new slot (refreshing a list in place)
@@ -710,6 +722,7 @@ struct Seq {
 cudaError_t launch_search(dd_plan_s* p, const float* T, dd_result_t* out_dev, cudaStream_t s) {
     p->launches = 0;
     p->nwaves = 0;
+    p->bodies.clear();
     cudaError_t e = cudaMemsetAsync(p->ctrl, 0, sizeof(Ctrl), s);
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(p->rmin, 0x7f, sizeof(uint32_t) * p->N, s);
@@ -841,6 +854,7 @@ cudaError_t launch_profile(dd_plan_s* p, const float* T, const int32_t* rows, in
                            cudaStream_t s) {
     p->launches = 0;
     p->nwaves = 0;
+    p->bodies.clear();
     cudaError_t e = cudaMemsetAsync(p->ctrl, 0, sizeof(Ctrl), s);
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(p->rmin, 0x7f, sizeof(uint32_t) * p->N, s);

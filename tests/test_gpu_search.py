@@ -248,3 +248,20 @@ def test_top_k_discords(precision):
             if precision != "fp32":
                 assert g.index == i
         assert again.index == ref[0][0]
+
+
+def test_launch_count_excludes_skipped_conditional_waves():
+    """A graph replay that skips the conditional waves launches fewer kernels than the same
+    search enqueued eagerly (where every gated kernel is launched and exits on its own)."""
+    dd = _dd()
+    spec = synth.workload_small()
+    T, _ = synth.make_series(spec)
+    Td = torch.from_numpy(T).cuda()
+    with dd.Plan(T.size, spec.n, "tc_fp16") as p:
+        p.find_discord(Td)
+        p.find_discord(Td)
+        g = p.last_launches()
+        p.set_graph(False)
+        p.find_discord(Td)
+        e = p.last_launches()
+    assert 0 < g < e
