@@ -59,7 +59,8 @@ typedef enum {
     DD_ETIMEOUT = 4,    /* a bounded device-side wait expired */
     DD_ECUDA = 5,       /* any other CUDA runtime error */
     DD_EBUSY = 6,       /* the plan is in use by another host thread */
-    DD_ENOTSUP = 7      /* option combination not supported for these sizes */
+    DD_ENOTSUP = 7      /* option combination not supported for these sizes (tensor-core
+                           forms for n > 65536) */
 } dd_status_t;
 
 /* Arithmetic of the distance tiles.
@@ -80,11 +81,17 @@ typedef struct {
                               1 = PAA of the globally normalised values */
     int32_t phase1_max;    /* at most this many Cand rows run in phase 1 (default 4096) */
     int32_t refine_k;      /* rows with the largest first-wave upper bounds that get a full scan
-                              before the other survivors, to raise the best-so-far (default 128) */
+                              before the other survivors, to raise the best-so-far (default 128).
+                              When more than refine_k rows then survive, they also run the
+                              time-local wave and refine_k of them, ranked again, a second full
+                              scan; 0 = skip both */
     int32_t local_cols;    /* first wave: every row scans the rows of nearest window mean, this many
-                              on each side of its tile (default 128) */
-    int32_t word_cols;     /* same-word wave: survivors scan this many rows sharing their SAX word
-                              (Index_Word, Eq. 10) before their full scans; 0 = skip (default 512) */
+                              on each side of its tile (default 128; FP32 form -- the tensor-core
+                              form's first wave is one 128 x 256 band tile per row tile); 0 = no
+                              first wave */
+    int32_t word_cols;     /* same-word wave (FP32 form): survivors scan this many rows sharing their
+                              SAX word (Index_Word, Eq. 10) before their full scans; 0 = skip
+                              (default 512) */
     int32_t shard_count;   /* row sharding (multi-GPU, one process per GPU): 0 or 1 = every row.
                               With G > 1 the search considers only the rows of shard shard_index:
                               positions [floor(k N / G), floor((k + 1) N / G)) of the mean-bucketed
