@@ -18,6 +18,11 @@ Functions and the passages of the paper they follow:
 * :func:`sax`            -- Eq. 3 + Eq. 4 + Eq. 9
 * :func:`index`          -- Eq. 7, Eq. 8, Eq. 10
 * :func:`hotsax`         -- Algorithms 2-4 on the CPU ("O2")
+* :func:`window_mu_sigma`, :func:`dist2` and ``znorm="window"`` in
+  :func:`nn_rows` / :func:`nn_profile` / :func:`discord_brute` /
+  :func:`discords_brute` -- the per-window z-normalised variant (every
+  subsequence normalised on its own, a constant one to the zero vector; one
+  reading of Algorithm 2's Znormalize step)
 """
 from __future__ import annotations
 
@@ -78,6 +83,10 @@ def _load():
             "dd_oracle_sax": ([P, i64, i32, i32, i32, i32, P, P], ctypes.c_int),
             "dd_oracle_index": ([P, i64, i32, P, P, P, P, P], ctypes.c_int),
             "dd_oracle_hotsax": ([P, i64, i32, i32, i32, i32, P, P, P], ctypes.c_int),
+            "dd_oracle_window_mu_sigma": ([P, i64, i32, P, P], ctypes.c_int),
+            "dd_oracle_dist2": ([P, i64, i32, i32, i64, i64, P], ctypes.c_int),
+            "dd_oracle_nn_rows_w": ([P, i64, i32, P, i64, P, P], ctypes.c_int),
+            "dd_oracle_nn_profile_w": ([P, i64, i32, P], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(lib, name)
@@ -113,38 +122,69 @@ def znorm(T):
     return out, mu.value, sg.value
 
 
-def nn_rows(T, n: int, rows):
+def _znorm_code(znorm: str) -> int:
+    if znorm not in ("global", "window"):
+        raise ValueError(f"znorm must be 'global' or 'window', not {znorm!r}")
+    return 0 if znorm == "global" else 1
+
+
+def nn_rows(T, n: int, rows, znorm: str = "global"):
     """Squared nearest non-self-match distance (and its argument) of the given rows."""
     T = _f32(T)
     rows = np.ascontiguousarray(np.asarray(rows, dtype=np.int64))
     nn2 = np.empty(rows.size, dtype=np.float64)
     arg = np.empty(rows.size, dtype=np.int64)
-    _chk(_load().dd_oracle_nn_rows(_ptr(T), T.size, n, _ptr(rows), rows.size, _ptr(nn2), _ptr(arg)), "nn_rows")
+    f = _load().dd_oracle_nn_rows if _znorm_code(znorm) == 0 else _load().dd_oracle_nn_rows_w
+    _chk(f(_ptr(T), T.size, n, _ptr(rows), rows.size, _ptr(nn2), _ptr(arg)), "nn_rows")
     return nn2, arg
 
 
-def nn_profile(T, n: int) -> np.ndarray:
+def nn_profile(T, n: int, znorm: str = "global") -> np.ndarray:
     """Squared nearest non-self-match distance of every subsequence (float64[N])."""
     T = _f32(T)
     N = T.size - n + 1
     out = np.empty(max(N, 0), dtype=np.float64)
-    _chk(_load().dd_oracle_nn_profile(_ptr(T), T.size, n, _ptr(out)), "nn_profile")
+    f = _load().dd_oracle_nn_profile if _znorm_code(znorm) == 0 else _load().dd_oracle_nn_profile_w
+    _chk(f(_ptr(T), T.size, n, _ptr(out)), "nn_profile")
     return out
 
 
-def discord_brute(T, n: int):
+def discord_brute(T, n: int, znorm: str = "global"):
     """O1: (index, nn^2) of the discord; ties -> smallest index."""
     T = _f32(T)
+    if _znorm_code(znorm) == 1:
+        nn2 = nn_profile(T, n, znorm)
+        i = int(np.argmax(nn2))  # first maximiser = smallest index
+        return i, float(nn2[i])
     idx, d2 = ctypes.c_int64(), ctypes.c_double()
     _chk(_load().dd_oracle_discord_brute(_ptr(T), T.size, n, ctypes.byref(idx), ctypes.byref(d2)), "discord_brute")
     return int(idx.value), float(d2.value)
 
 
-def discords_brute(T, n: int, k: int):
+def window_mu_sigma(T, n: int):
+    """Per-window mean and population sigma of the input series (two-pass FP64)."""
+    T = _f32(T)
+    N = T.size - n + 1
+    mu = np.empty(max(N, 0), dtype=np.float64)
+    sg = np.empty(max(N, 0), dtype=np.float64)
+    _chk(_load().dd_oracle_window_mu_sigma(_ptr(T), T.size, n, _ptr(mu), _ptr(sg)), "window_mu_sigma")
+    return mu, sg
+
+
+def dist2(T, n: int, i: int, j: int, znorm: str = "global") -> float:
+    """Squared distance between subsequences i and j under either normalisation."""
+    T = _f32(T)
+    out = ctypes.c_double()
+    _chk(_load().dd_oracle_dist2(_ptr(T), T.size, n, _znorm_code(znorm), int(i), int(j), ctypes.byref(out)),
+         "dist2")
+    return float(out.value)
+
+
+def discords_brute(T, n: int, k: int, znorm: str = "global"):
     """Top-k discords by definition: repeatedly the largest nearest non-self-match distance
     (first maximiser = smallest index), among subsequences at least n away from those already
     chosen.  Returns [(index, nn2)]."""
-    nn2 = nn_profile(T, n)
+    nn2 = nn_profile(T, n, znorm)
     allowed = np.ones(nn2.size, dtype=bool)
     out = []
     for _ in range(k):

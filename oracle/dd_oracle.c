@@ -22,6 +22,10 @@
  *   dd_oracle_index         Freq (Eq. 8), Cand (Eq. 7), Index_Word (Eq. 10)
  *   dd_oracle_hotsax        Algorithms 2-4 (PhiDD: PotentialDiscord followed by
  *                           RefineDiscord) on the CPU ("O2")
+ *   dd_oracle_window_mu_sigma, dd_oracle_dist2, dd_oracle_nn_rows_w,
+ *   dd_oracle_nn_profile_w  the per-window z-normalised variant (each
+ *                           subsequence normalised on its own; one reading of
+ *                           Algorithm 2's Znormalize step), brute force
  *
  * Readings of the paper taken here (where it is silent, ambiguous or garbled):
  *   - Distances are plain Euclidean distances between subsequences of the
@@ -42,6 +46,9 @@
  *     values as they stand -- mode 1.  SAX only orders the search; it never
  *     changes its result.
  *   - Indices are 0-based.
+ *   - Per-window variant: window mean and population sigma two-pass in FP64
+ *     on the input values; a constant window (centred sum of squares exactly
+ *     0) normalises to the zero vector.
  *
  * Parity pins for every function live in tests/ (hand examples, closed forms,
  * invariants, exact integer brute force, O1 == O2).  Nothing here is
@@ -491,4 +498,156 @@ done:
     free(members);
     free(is_cand);
     return st;
+}
+
+/* ---------------------------------------------------------------------------
+ * Per-window z-normalisation: the variant in which every subsequence is
+ * normalised on its own (the usual HOTSAX convention, and one reading of
+ * Algorithm 2's Znormalize step) instead of the whole series (Eq. 2).
+ *
+ * For the subsequence x_i = T[i .. i+n) of the INPUT series (float32 widened
+ * exactly to FP64):
+ *   mu_i    = (1/n) sum_k x_{i,k}                    (sum in k order)
+ *   c_i     = sum_k (x_{i,k} - mu_i)^2               (two-pass, k order)
+ *   sigma_i = sqrt(c_i / n)
+ *   z_{i,k} = (x_{i,k} - mu_i) / sigma_i, and z_i = 0 when c_i == 0
+ * (a constant subsequence becomes the zero vector; the paper is silent on
+ * it).  The distance is Eq. 1 on z, squared: sum_k (z_{i,k} - z_{j,k})^2 in k
+ * order.  Consequences used by the pins: 0 <= d^2 <= 4n; d^2 = 2n(1 - r_ij)
+ * with r_ij the Pearson correlation of two non-constant subsequences; d^2 = n
+ * between a constant and a non-constant one; d^2 = 0 between two constant
+ * ones; d^2 is unchanged when T is replaced by a*T + b (a != 0).
+ * ------------------------------------------------------------------------- */
+static void window_mu_sigma(const float* T, int64_t N, int32_t n, double* mu, double* sg) {
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < N; i++) {
+        double s = 0.0;
+        for (int32_t k = 0; k < n; k++) s += (double)T[i + k];
+        double mi = s / (double)n;
+        double c = 0.0;
+        for (int32_t k = 0; k < n; k++) {
+            double d = (double)T[i + k] - mi;
+            c += d * d;
+        }
+        mu[i] = mi;
+        sg[i] = sqrt(c / (double)n); /* 0 exactly iff c == 0 */
+    }
+}
+
+static double zval(const float* T, const double* mu, const double* sg, int64_t i, int32_t k) {
+    return sg[i] > 0.0 ? ((double)T[i + k] - mu[i]) / sg[i] : 0.0;
+}
+
+static double ed2_w(const float* T, const double* mu, const double* sg, int64_t i, int64_t j, int32_t n) {
+    double s = 0.0;
+    for (int32_t k = 0; k < n; k++) {
+        double d = zval(T, mu, sg, i, k) - zval(T, mu, sg, j, k);
+        s += d * d;
+    }
+    return s;
+}
+
+static double nn2_of_row_w(const float* T, const double* mu, const double* sg, int64_t N, int32_t n, int64_t i,
+                           int64_t* arg) {
+    double best = INFINITY;
+    int64_t barg = -1;
+    for (int64_t j = 0; j < N; j++) {
+        int64_t d = i > j ? i - j : j - i;
+        if (d < n) continue;
+        double s = ed2_w(T, mu, sg, i, j, n);
+        if (s < best) {
+            best = s;
+            barg = j;
+        }
+    }
+    if (arg) *arg = barg;
+    return best;
+}
+
+/* Window statistics of the input series as defined above: mu_i and sigma_i. */
+int dd_oracle_window_mu_sigma(const float* T, int64_t m, int32_t n, double* mu, double* sg) {
+    if (!T || !mu || !sg || n < 1 || (int64_t)n > m) return OR_EINVAL;
+    for (int64_t i = 0; i < m; i++)
+        if (!isfinite(T[i])) return OR_ENONFINITE;
+    window_mu_sigma(T, m - n + 1, n, mu, sg);
+    return OR_OK;
+}
+
+/* Squared distance between subsequences i and j (any i, j in [0, N)).
+ * znorm 0: Eq. 1 on the globally normalised series (Eq. 2); znorm 1: per
+ * window, as defined above. */
+int dd_oracle_dist2(const float* T, int64_t m, int32_t n, int32_t znorm, int64_t i, int64_t j, double* out) {
+    if (!T || !out || n < 1 || (int64_t)n > m || (znorm != 0 && znorm != 1)) return OR_EINVAL;
+    int64_t N = m - n + 1;
+    if (i < 0 || j < 0 || i >= N || j >= N) return OR_EINVAL;
+    for (int64_t q = 0; q < m; q++)
+        if (!isfinite(T[q])) return OR_ENONFINITE;
+    if (znorm == 0) {
+        double* t = (double*)malloc(sizeof(double) * (size_t)m);
+        if (!t) return OR_ENOMEM;
+        dd_oracle_znorm(T, m, t, NULL, NULL);
+        *out = ed2(t + i, t + j, n);
+        free(t);
+        return OR_OK;
+    }
+    double mu[2], sg[2];
+    int64_t idx[2] = {i, j};
+    for (int r = 0; r < 2; r++) window_mu_sigma(T + idx[r], 1, n, mu + r, sg + r);
+    /* ed2_w on a two-entry table: entry 0 holds row i, entry 1 row j */
+    double s = 0.0;
+    for (int32_t k = 0; k < n; k++) {
+        double a = sg[0] > 0.0 ? ((double)T[i + k] - mu[0]) / sg[0] : 0.0;
+        double b = sg[1] > 0.0 ? ((double)T[j + k] - mu[1]) / sg[1] : 0.0;
+        double d = a - b;
+        s += d * d;
+    }
+    *out = s;
+    return OR_OK;
+}
+
+/* Section 2.1 definitions with the per-window distance: nearest non-self
+ * match (|i - j| >= n) of selected rows, brute force over every j. */
+int dd_oracle_nn_rows_w(const float* T, int64_t m, int32_t n, const int64_t* rows, int64_t k, double* nn2,
+                        int64_t* argnn) {
+    int st = check_args(T, m, n);
+    if (st) return st;
+    int64_t N = m - n + 1;
+    for (int64_t r = 0; r < k; r++)
+        if (rows[r] < 0 || rows[r] >= N) return OR_EINVAL;
+    double* mu = (double*)malloc(sizeof(double) * (size_t)N);
+    double* sg = (double*)malloc(sizeof(double) * (size_t)N);
+    if (!mu || !sg) {
+        free(mu);
+        free(sg);
+        return OR_ENOMEM;
+    }
+    window_mu_sigma(T, N, n, mu, sg);
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t r = 0; r < k; r++) {
+        int64_t a = -1;
+        nn2[r] = nn2_of_row_w(T, mu, sg, N, n, rows[r], &a);
+        if (argnn) argnn[r] = a;
+    }
+    free(mu);
+    free(sg);
+    return OR_OK;
+}
+
+int dd_oracle_nn_profile_w(const float* T, int64_t m, int32_t n, double* nn2) {
+    int st = check_args(T, m, n);
+    if (st) return st;
+    int64_t N = m - n + 1;
+    double* mu = (double*)malloc(sizeof(double) * (size_t)N);
+    double* sg = (double*)malloc(sizeof(double) * (size_t)N);
+    if (!mu || !sg) {
+        free(mu);
+        free(sg);
+        return OR_ENOMEM;
+    }
+    window_mu_sigma(T, N, n, mu, sg);
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t i = 0; i < N; i++) nn2[i] = nn2_of_row_w(T, mu, sg, N, n, i, NULL);
+    free(mu);
+    free(sg);
+    return OR_OK;
 }
