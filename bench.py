@@ -165,6 +165,55 @@ def _exhaustive(dd, Td, m: int, n: int, forms, peaks, rows: int = 8192, reps: in
     return out
 
 
+def _window(dd, Td, m: int, n: int, peaks, reps: int = 3) -> dict:
+    """Per-window z-normalised discords and the diagonal-recurrence profile (exhaustive, every
+    pair once): time to the exact per-window discord, and the global-form profile rate next to
+    the direct FP32 exhaustive rate.  The recurrence kernel is bound by the FP32/ALU issue rate;
+    its algorithmic work is 6 lane instructions per pair (2 FMA of the recurrence, 2 for the
+    score, the row and the column minimum)."""
+    import torch
+    N = m - n + 1
+    pairs = _pairs_unordered(N, n)
+    peak = SM_COUNT * FP32_LANES_PER_SM * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+    out = {}
+    with dd.Plan(m, n, znorm="window") as p:
+        p.set_profiling(True)
+        r = p.find_discord(Td)
+        ts, kms = [], []
+        for _ in range(reps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            r = p.find_discord(Td)
+            e1.record()
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+            kms.append(p.profile()["dist_ms"])
+        ms, kd = statistics.median(ts), statistics.median(kms)
+        ach = 6.0 * pairs / (kd * 1e-3) / 1e12
+        out["window_discord"] = {"time_to_discord_ms": ms, "index": r.index, "nn_distance": r.nn_distance,
+                                 "exact": r.exact, "candidates_rescored": r.candidates,
+                                 "pairs_per_s": pairs / (ms * 1e-3), "k_diag_ms": kd,
+                                 "roofline": {"bound": "alu", "achieved": ach, "peak": peak, "unit": "Tinstr/s",
+                                              "frac": ach / peak, "kernel": "k_diag<window>",
+                                              "work": "6 lane instructions per pair"}}
+    with dd.Plan(m, n, diag=True) as p:
+        p.set_profiling(True)
+        y = p.nn_profile_diag(Td)
+        ts, kms = [], []
+        for _ in range(reps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            p.nn_profile_diag(Td, out=y)
+            e1.record()
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        ms = statistics.median(ts)
+        out["global_diag_profile"] = {"ms": ms, "pairs": pairs, "pairs_per_s": pairs / (ms * 1e-3)}
+    return out
+
+
 def _batch(dd, precision: str, count: int = 512) -> dict:
     """Many uneven series (m log-uniform in [2048, 65536], n in {64, 128, 256}) resident on
     the device, searched by one dd_find_discord_batched call (an engine of 8 workers)."""
@@ -284,6 +333,8 @@ def main():
                     help="enqueue each search's kernels directly instead of replaying its CUDA graph "
                          "(per-kernel profilers cannot profile kernels of graphs with conditional nodes)")
     ap.add_argument("--no-serve", action="store_true", help="skip the Poisson serving run (p50/p99)")
+    ap.add_argument("--no-window", action="store_true",
+                    help="skip the per-window discord and diagonal-recurrence profile")
     ap.add_argument("--no-exhaustive", action="store_true",
                     help="skip the exhaustive-mode (no abandon) pair-distances/s of each form")
     ap.add_argument("--workload", default="large", choices=["large", "medium"],
@@ -424,6 +475,12 @@ def main():
     exh = None
     if not args.no_exhaustive:
         exh = _exhaustive(dd, Td, m, n, [f for f in ("tc_fp16", "fp32") if f in supported], peaks)
+    win = None
+    if not args.no_window:
+        win = _window(dd, Td, m, n, peaks)
+        if exh and "fp32" in exh:
+            win["global_diag_profile"]["vs_direct_fp32_exhaustive"] = \
+                win["global_diag_profile"]["pairs_per_s"] / exh["fp32"]["pairs_per_s"]
     if rank == 0:
         cpu = None if args.no_cpu_baseline else _cpu_baseline()
         line = {"metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -442,7 +499,7 @@ def main():
                 "forms": {k: {kk: vv for kk, vv in v.items() if kk != "roofline"} | {"roofline_frac": v["roofline"]["frac"]}
                           for k, v in results.items()},
                 "discord": {"index": head["index"], "nn_distance": head["nn_distance"]},
-                "exhaustive": exh, "batch": batch, "serve": serve}
+                "exhaustive": exh, "window": win, "batch": batch, "serve": serve}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

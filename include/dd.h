@@ -60,7 +60,8 @@ typedef enum {
     DD_ECUDA = 5,       /* any other CUDA runtime error */
     DD_EBUSY = 6,       /* the plan is in use by another host thread */
     DD_ENOTSUP = 7      /* option combination not supported for these sizes (tensor-core
-                           forms for n > 65536) */
+                           forms for n > 65536; per-window with a tensor-core precision or
+                           shards; diagonal-recurrence workspace for N > 2^26) */
 } dd_status_t;
 
 /* Arithmetic of the distance tiles.
@@ -99,7 +100,20 @@ typedef struct {
                               is the shard result with the largest nn_distance, ties to the
                               smallest index -- one all-gather of (nn_distance, index) */
     int32_t shard_index;   /* k in [0, G) (default 0) */
-    int32_t reserved[5];   /* must be zero */
+    int32_t znorm;         /* 0 = the whole series is z-normalised (Eq. 2; default).
+                              1 = every subsequence is z-normalised on its own (window mean and
+                              population sigma of the input values, two-pass FP64; a constant
+                              subsequence becomes the zero vector), the usual HOTSAX convention.
+                              Every window then has mean 0, so the mean-order lower bound of the
+                              search is void: per-window plans find the discord from the
+                              exhaustive diagonal-recurrence profile (see dd_nn_profile_diag), a
+                              rigorous FP32 bound per row and exact FP64 rescoring of every row
+                              the bound cannot rule out -- exact index and FP64 distance.
+                              Requires DD_FP32 and shard_count <= 1 (else DD_ENOTSUP); the SAX
+                              and wave options do not apply */
+    int32_t diag;          /* 1 = also hold the workspace of dd_nn_profile_diag (implied by
+                              znorm = 1; default 0) */
+    int32_t reserved[3];   /* must be zero */
 } dd_options_t;
 
 typedef struct {
@@ -196,15 +210,36 @@ DD_API dd_status_t dd_find_discord_batched(int32_t count, const float* const* T_
 /* Exhaustive nearest-neighbour profile (no abandon): nn2_dev[i] = squared
  * distance from subsequence i to its nearest non-self match, i in [0, N),
  * computed with the plan's precision (tensor-core forms: the FP32 Gram value,
- * within the per-row bound, not rescored).  nn2_dev: N floats on the device.
+ * within the per-row bound, not rescored; per-window plans: what
+ * dd_nn_profile_diag computes).  nn2_dev: N floats on the device.
  * Enqueued on `stream`, not waited for.  Errors: DD_EINVAL, DD_ECUDA. */
 DD_API dd_status_t dd_nn_profile(dd_plan_t plan, const float* T_dev, float* nn2_dev, void* stream);
 
 /* Exhaustive nearest-neighbour distances of selected rows: rows_dev[k]
  * (device int32, 0 <= row < N, k < count) -> nn2_dev[k] (device float).
+ * Per-window plans (znorm = 1): exact FP64 values rounded to float.
  * Enqueued on `stream`.  Errors: DD_EINVAL, DD_ECUDA. */
 DD_API dd_status_t dd_nn_rows(dd_plan_t plan, const float* T_dev, const int32_t* rows_dev, int32_t count, float* nn2_dev,
                        void* stream);
+
+/* Exhaustive nearest-neighbour profile by the diagonal recurrence of centred
+ * dot products: C(i+1, j+1) = C(i, j) + df_i dg_j + df_j dg_i along every
+ * diagonal j - i >= n (O(1) work per pair instead of the O(n) of Eq. 1),
+ * FP32, every diagonal re-seeded with a direct dot product every 2048 rows.
+ * For each row i it finds an argument j_i (|i - j_i| >= n) whose recurrence
+ * distance is minimal up to FP32 rounding, then reports the distance to it
+ * computed directly:
+ *   global plans (znorm = 0): FP32 direct differences on the normalised
+ *     series (Eq. 1 squared, as the FP32 form computes them);
+ *   per-window plans (znorm = 1): the exact FP64 per-window distance.
+ * So nn2_dev[i] is the distance to a real non-self match, >= the true
+ * nearest-neighbour distance (up to that rounding) and above it only where
+ * the recurrence's rounding picked a near-tie.  nn2_dev: N floats;
+ * nn_index_dev: N int32 arguments, or NULL.  Device memory, enqueued on
+ * `stream`.  Needs a plan created with diag = 1 or znorm = 1 (else
+ * DD_ENOTSUP); N <= 2^26.  Errors: DD_EINVAL, DD_ENOTSUP, DD_EBUSY, DD_ECUDA. */
+DD_API dd_status_t dd_nn_profile_diag(dd_plan_t plan, const float* T_dev, float* nn2_dev, int32_t* nn_index_dev,
+                                      void* stream);
 
 /* Runs only the preparation stage of Algorithm 2 (Eq. 2 normalisation,
  * prefix sums, window statistics, PAA/SAX words, Freq, Cand, Index_Word) on
@@ -272,7 +307,8 @@ typedef enum {
     DD_WAVE_WORD = 5,
     DD_WAVE_REST = 6,
     DD_WAVE_TIME = 7,
-    DD_WAVE_SETTLE = 8
+    DD_WAVE_SETTLE = 8,
+    DD_WAVE_DIAG = 9   /* every pair by the diagonal recurrence (dd_nn_profile_diag, per-window plans) */
 } dd_wave_kind_t;
 
 typedef struct {

@@ -20,6 +20,8 @@ from . import _lib
 __all__ = ["Plan", "Engine", "Completion", "DiscordResult", "DDError", "find_discord", "find_discord_batched", "PRECISIONS"]
 
 PRECISIONS = {"fp32": _lib.DD_FP32, "tc_fp16": _lib.DD_TC_FP16, "tc_bf16": _lib.DD_TC_BF16}
+# "global": the whole series z-normalised (Eq. 2); "window": every subsequence on its own
+ZNORMS = {"global": 0, "window": 1}
 
 
 class DDError(RuntimeError):
@@ -56,7 +58,8 @@ def _check(st: int, what: str):
 
 
 def _options(precision="fp32", paa_w=4, alphabet=4, early_abandon=True, paa_mode=0, phase1_max=4096,
-             refine_k=128, local_cols=128, word_cols=512, shard_count=1, shard_index=0) -> _lib.Options:
+             refine_k=128, local_cols=128, word_cols=512, shard_count=1, shard_index=0, znorm="global",
+             diag=False) -> _lib.Options:
     o = _lib.Options()
     _lib.load().dd_options_default(ctypes.byref(o))
     o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
@@ -70,6 +73,10 @@ def _options(precision="fp32", paa_w=4, alphabet=4, early_abandon=True, paa_mode
     o.word_cols = word_cols
     o.shard_count = shard_count
     o.shard_index = shard_index
+    if znorm not in ZNORMS:
+        raise ValueError(f"znorm must be one of {sorted(ZNORMS)}, not {znorm!r}")
+    o.znorm = ZNORMS[znorm]
+    o.diag = 1 if diag else 0
     return o
 
 
@@ -183,6 +190,21 @@ class Plan:
         _check(self._lib.dd_nn_profile(self._ptr, ctypes.c_void_p(T.data_ptr()), ctypes.c_void_p(out.data_ptr()),
                                        _stream_ptr(stream)), "dd_nn_profile")
         return out
+
+    def nn_profile_diag(self, T, out=None, index=None, stream=None):
+        """Exhaustive nearest-neighbour profile by the diagonal recurrence (plans made with
+        ``diag=True`` or ``znorm="window"``): the squared distance of every row to its argument
+        (CUDA float32[N]) and, if ``index`` is True or a CUDA int32[N] tensor, the argument."""
+        torch = _torch()
+        _check_series(T, self.m)
+        if out is None:
+            out = torch.empty(self.N, dtype=torch.float32, device=T.device)
+        if index is True:
+            index = torch.empty(self.N, dtype=torch.int32, device=T.device)
+        ip = ctypes.c_void_p(index.data_ptr()) if index is not None and index is not False else None
+        _check(self._lib.dd_nn_profile_diag(self._ptr, ctypes.c_void_p(T.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                            ip, _stream_ptr(stream)), "dd_nn_profile_diag")
+        return (out, index) if ip is not None else out
 
     def nn_rows(self, T, rows, out=None, stream=None):
         """Exhaustive squared nearest-neighbour distances of the given rows (int32 CUDA tensor)."""

@@ -19,7 +19,8 @@ class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("paa_w", ctypes.c_int32), ("alphabet", ctypes.c_int32),
                 ("early_abandon", ctypes.c_int32), ("paa_mode", ctypes.c_int32), ("phase1_max", ctypes.c_int32),
                 ("refine_k", ctypes.c_int32), ("local_cols", ctypes.c_int32), ("word_cols", ctypes.c_int32),
-                ("shard_count", ctypes.c_int32), ("shard_index", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
+                ("shard_count", ctypes.c_int32), ("shard_index", ctypes.c_int32), ("znorm", ctypes.c_int32),
+                ("diag", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
 
 
 class Result(ctypes.Structure):
@@ -54,7 +55,8 @@ class Wave(ctypes.Structure):
                 ("pairs", ctypes.c_int64), ("ms", ctypes.c_double)]
 
 
-WAVE_KINDS = {0: "exhaustive", 1: "local", 2: "band", 3: "cand", 4: "top", 5: "word", 6: "rest", 7: "time", 8: "settle"}
+WAVE_KINDS = {0: "exhaustive", 1: "local", 2: "band", 3: "cand", 4: "top", 5: "word", 6: "rest", 7: "time", 8: "settle",
+              9: "diag"}
 
 _lock = threading.Lock()
 _lib = None
@@ -74,6 +76,8 @@ SIGNATURES = {
                                  ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(Options), ctypes.POINTER(Result),
                                  ctypes.c_void_p], ctypes.c_int),
     "dd_nn_profile": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
+    "dd_nn_profile_diag": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
+                           ctypes.c_int),
     "dd_nn_rows": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
                     ctypes.c_void_p], ctypes.c_int),
     "dd_prep": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),

@@ -37,10 +37,15 @@ bool valid_options(const dd_options_t& o) {
     if (o.phase1_max < 0 || o.refine_k < 0 || o.local_cols < 0 || o.word_cols < 0) return false;
     if (o.shard_count < 0 || o.shard_index < 0 || o.shard_index >= (o.shard_count > 1 ? o.shard_count : 1))
         return false;
-    for (int i = 0; i < 5; i++)
+    if (o.znorm != 0 && o.znorm != 1) return false;
+    if (o.diag != 0 && o.diag != 1) return false;
+    for (int i = 0; i < 3; i++)
         if (o.reserved[i] != 0) return false;
     return true;
 }
+
+// The diagonal-recurrence workspace (and per-window search) is held.
+bool has_diag(const dd_options_t& o) { return o.znorm == 1 || o.diag == 1; }
 
 bool valid_sizes(int64_t m, int32_t n) {
     if (n < 1 || m < 1 || (int64_t)n > m) return false;
@@ -114,6 +119,16 @@ size_t carve(dd_plan_s* p, char* base) {
         p->q2 = c.take<float>(N);
         p->ex64 = c.take<double>(N);
         p->rmin32 = c.take<uint32_t>(N);
+    }
+    if (has_diag(p->opt)) {
+        if (!p->ex64) p->ex64 = c.take<double>(N);
+        p->wmu64 = c.take<double>(N);
+        p->wr64 = c.take<double>(N);
+        p->wdat = c.take<float4>(N + dd::kDgPad);
+        p->wmu32 = c.take<float>(N + dd::kDgPad);
+        p->wscr = c.take<float2>(N);
+        p->dkey = c.take<unsigned long long>(N);
+        p->dub = c.take<float>(N);
     }
     return (c.off + kAlign - 1) / kAlign * kAlign;
 }
@@ -304,6 +319,8 @@ dd_status_t create_plan(dd_plan_s** plan, int64_t m, int32_t n, const dd_options
     if (!valid_options(o) || !valid_sizes(m, n)) return DD_EINVAL;
     clamp_word(o, n);
     if (o.precision != DD_FP32 && !dd::tc_supported(n)) return DD_ENOTSUP;
+    if (o.znorm == 1 && (o.precision != DD_FP32 || o.shard_count > 1)) return DD_ENOTSUP;
+    if (has_diag(o) && m - n + 1 > ((int64_t)1 << 26)) return DD_ENOTSUP;
     if (workspace && (reinterpret_cast<uintptr_t>(workspace) % kAlign) != 0) return DD_EINVAL;
     if (engine && !workspace) return DD_EINVAL;
     dd_plan_s* p = new (std::nothrow) dd_plan_s();
@@ -368,6 +385,8 @@ dd_status_t create_plan(dd_plan_s** plan, int64_t m, int32_t n, const dd_options
     if (e == cudaSuccess) e = cudaMemsetAsync(p->t64 + p->m, 0, sizeof(double) * kPad, init);
     if (e == cudaSuccess) e = cudaMemsetAsync(p->t32 + p->m, 0, sizeof(float) * kPad, init);
     if (e == cudaSuccess) e = cudaMemsetAsync(p->excl, 0, (size_t)p->N, init);
+    if (e == cudaSuccess && p->wdat) e = cudaMemsetAsync(p->wdat + p->N, 0, sizeof(float4) * dd::kDgPad, init);
+    if (e == cudaSuccess && p->wmu32) e = cudaMemsetAsync(p->wmu32 + p->N, 0, sizeof(float) * dd::kDgPad, init);
     if (e == cudaSuccess) {
         k_iota<<<(unsigned)((p->N + 255) / 256), 256, 0, init>>>(p->seq_rows, p->N);
         e = cudaGetLastError();
@@ -566,6 +585,14 @@ dd_status_t dd_nn_profile(dd_plan_t p, const float* T_dev, float* nn2_dev, void*
     BusyGuard g(p);
     if (!g.ok) return DD_EBUSY;
     return from_cuda(dd::launch_profile(p, T_dev, nullptr, 0, nn2_dev, static_cast<cudaStream_t>(stream)));
+}
+
+dd_status_t dd_nn_profile_diag(dd_plan_t p, const float* T_dev, float* nn2_dev, int32_t* nn_index_dev, void* stream) {
+    if (!p || !T_dev || !nn2_dev) return DD_EINVAL;
+    if (!p->dkey) return DD_ENOTSUP;
+    BusyGuard g(p);
+    if (!g.ok) return DD_EBUSY;
+    return from_cuda(dd::launch_profile_diag(p, T_dev, nn2_dev, nn_index_dev, static_cast<cudaStream_t>(stream)));
 }
 
 dd_status_t dd_nn_rows(dd_plan_t p, const float* T_dev, const int32_t* rows_dev, int32_t count, float* nn2_dev,

@@ -25,6 +25,7 @@ constexpr int kMuBins = 4096;            // bins of the mean-bucketed row order
 constexpr int kMaxLaunchSlots = 512;     // work counters per search
 constexpr int kMaxListSlots = 256;       // list counts per search
 constexpr int kMaxWaves = 64;            // distance waves traced per call
+constexpr int kDgPad = 2048 + 64;        // padding entries after the diagonal-recurrence data (>= one CTA's diagonals)
 
 // FP32 direct-difference tile kernel
 constexpr int kF32BM = 128;  // rows per tile
@@ -53,6 +54,7 @@ struct Ctrl {
     int ncandidates;              // rows rescored in FP64
     int best_idx;                 // smallest index attaining best64
     unsigned long long best64;    // exact nn^2 of the discord (double bits)
+    unsigned long long wlb;       // per-window search: exact nn^2 of the row with the largest bound (double bits)
     int smax[64];                 // largest per-tile segment count of each tile-range launch
     int cnt[kMaxListSlots];       // list counts written by compactions
     int work[kMaxLaunchSlots];    // dynamic-schedule work counters, one per launch
@@ -276,6 +278,15 @@ struct dd_plan_s {
     float* gam = nullptr;
     float* q2 = nullptr;
     double* ex64 = nullptr;           // [N] exact FP64 nn^2 of the rescored rows
+
+    // diagonal-recurrence profile and per-window form (opt.diag or opt.znorm == 1)
+    double* wmu64 = nullptr;          // [N] window means, two-pass FP64
+    double* wr64 = nullptr;           // [N] per window: 1 / sigma (0 for a constant window)
+    float4* wdat = nullptr;           // [N + kDgPad] (df, dg, 1/sqrt(c), e) per window, (df, dg, c, sqrt(n) mu) globally
+    float* wmu32 = nullptr;           // [N + kDgPad] window means rounded to FP32
+    float2* wscr = nullptr;           // [N] per window: (fl32(1 / sigma), E) of the FP32 screen
+    unsigned long long* dkey = nullptr;  // [N] nearest-neighbour key: float bits << 32 | partner
+    float* dub = nullptr;             // [N] per-window search: rigorous upper bound of nn^2
     CUtensorMap mapS_A, mapS_B, mapP_A;
 
     double beta_host[dd::kMaxAlphabet];
@@ -352,6 +363,15 @@ cudaError_t launch_rescore(dd_plan_s* p, ListRef cand, TcBound bound, int work_s
 // api.cu: event pair around a distance launch when profiling (start=true before, false after)
 void prof_mark(dd_plan_s* p, cudaStream_t s, bool start);
 int scan_fp32_grid(const dd_plan_s* p);
+
+// rescore.cu: argmax over a rescored list (ties -> smallest index) into the result
+cudaError_t launch_best(dd_plan_s* p, ListRef cand, dd_result_t* out_dev, cudaStream_t s);
+// diag.cu: diagonal-recurrence profile (dd_nn_profile_diag, and dd_nn_profile of a
+// per-window plan), per-window rows and the per-window discord search
+cudaError_t launch_profile_diag(dd_plan_s* p, const float* T, float* nn2, int32_t* idx, cudaStream_t s);
+cudaError_t launch_rows_window(dd_plan_s* p, const float* T, const int32_t* rows, int count, float* nn2,
+                               cudaStream_t s);
+cudaError_t launch_search_window(dd_plan_s* p, const float* T, dd_result_t* out_dev, cudaStream_t s);
 
 void host_breakpoints(int A, double* beta);
 

@@ -176,6 +176,16 @@ __global__ void k_init_best(Ctrl* ctrl) {
 
 }  // namespace
 
+cudaError_t launch_best(dd_plan_s* p, ListRef cand, dd_result_t* out_dev, cudaStream_t s) {
+    const unsigned long long* ex = reinterpret_cast<const unsigned long long*>(p->ex64);
+    k_init_best<<<1, 32, 0, s>>>(p->ctrl);
+    k_best64<<<p->sm_count, 256, 0, s>>>(cand, ex, p->ctrl);
+    k_pick64<<<p->sm_count, 256, 0, s>>>(cand, ex, p->ctrl);
+    k_finalize_tc<<<1, 32, 0, s>>>(p->ctrl, out_dev);
+    p->launches += 4;
+    return cudaGetLastError();
+}
+
 cudaError_t launch_rescore(dd_plan_s* p, ListRef cand, TcBound bound, int work_slot, dd_result_t* out_dev,
                            cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(p->ex64, 0x7f, sizeof(double) * p->N, s);

@@ -720,6 +720,7 @@ struct Seq {
 }  // namespace
 
 cudaError_t launch_search(dd_plan_s* p, const float* T, dd_result_t* out_dev, cudaStream_t s) {
+    if (p->opt.znorm == 1) return launch_search_window(p, T, out_dev, s);
     p->launches = 0;
     p->nwaves = 0;
     p->bodies.clear();
@@ -852,6 +853,8 @@ cudaError_t launch_search(dd_plan_s* p, const float* T, dd_result_t* out_dev, cu
 
 cudaError_t launch_profile(dd_plan_s* p, const float* T, const int32_t* rows, int count, float* nn2,
                            cudaStream_t s) {
+    if (p->opt.znorm == 1)
+        return rows ? launch_rows_window(p, T, rows, count, nn2, s) : launch_profile_diag(p, T, nn2, nullptr, s);
     p->launches = 0;
     p->nwaves = 0;
     p->bodies.clear();

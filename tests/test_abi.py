@@ -50,8 +50,36 @@ def test_options_default_and_footprint():
     o.alphabet = 1
     assert lib.dd_plan_footprint(1 << 16, 64, ctypes.byref(o)) == 0
     lib.dd_options_default(ctypes.byref(o))
-    o.reserved[3] = 1
+    o.reserved[2] = 1
     assert lib.dd_plan_footprint(1 << 16, 64, ctypes.byref(o)) == 0
+    for field in ("znorm", "diag"):
+        lib.dd_options_default(ctypes.byref(o))
+        setattr(o, field, 2)
+        assert lib.dd_plan_footprint(1 << 16, 64, ctypes.byref(o)) == 0
+
+
+def test_window_and_diag_options():
+    """Per-window plans and plans with the diagonal-recurrence workspace: footprints, and the
+    combinations refused before any device work."""
+    import paper_1901_00155_gb300 as dd
+    lib = _lib.load()
+    base = dd.Plan.footprint(1 << 16, 256)
+    win = dd.Plan.footprint(1 << 16, 256, znorm="window")
+    dg = dd.Plan.footprint(1 << 16, 256, diag=True)
+    assert win == dg > base
+    N = (1 << 16) - 255
+    assert win - base >= N * (8 + 8 + 16 + 4 + 8 + 8 + 4 + 8)  # window stats, data, keys, bounds, FP64 results
+    assert dd.Plan.footprint(1 << 16, 256, "tc_fp16", diag=True) > dd.Plan.footprint(1 << 16, 256, "tc_fp16")
+    with pytest.raises(ValueError):
+        dd.Plan.footprint(1 << 16, 256, znorm="per-window")
+    p = ctypes.c_void_p()
+    for kw in ({"precision": "tc_fp16", "znorm": "window"}, {"znorm": "window", "shard_count": 2}):
+        o = dd._options(**kw)
+        assert lib.dd_plan_create(ctypes.byref(p), 1 << 16, 256, ctypes.byref(o), None, 0) == _lib.DD_ENOTSUP
+    o = dd._options(diag=True)
+    assert lib.dd_plan_create(ctypes.byref(p), (1 << 26) + 300, 100, ctypes.byref(o), None, 0) == _lib.DD_ENOTSUP
+    assert p.value is None
+    assert lib.dd_nn_profile_diag(None, None, None, None, None) == _lib.DD_EINVAL
 
 
 def test_status_strings():
