@@ -59,6 +59,8 @@ constexpr int kDgWarpDiags = 32 * kDgD;          // 256
 constexpr int kDgTD = kDgWarps * kDgWarpDiags;   // 2048 diagonals per CTA
 constexpr int kDgRS = 2048;                      // rows per CTA (one re-seed each)
 constexpr int kDgRing = 2 * kDgTD;               // column-key ring (power of two)
+constexpr int kDgFlush = 4;                      // groups of 8 rows between CTA-wide merges
+constexpr size_t kDgSmem = sizeof(float4) * kDgRS + sizeof(unsigned long long) * kDgRing;
 constexpr float kDgNone = 3.0e38f;               // score of a pair outside the triangle
 constexpr unsigned long long kEmpty = ~0ull;
 constexpr int kWChunk = 512;                     // columns per rescoring work item
@@ -169,16 +171,20 @@ struct DiagLane {
 };
 
 // Eight steps (rows rbase .. rbase+7) of one lane.  kFull: every pair of the
-// CTA lies inside the triangle r + k < N (no masking).
+// CTA lies inside the triangle r + k < N (no masking).  rows: the CTA's row
+// data in shared memory (row r at rows[r - r0]).
 template <bool kWindow, bool kFull>
-__device__ __forceinline__ void diag_group(DiagLane& L, float (&rk)[8], const float4* __restrict__ wdat, int rbase,
-                                           long long kb, int N, int lane, float* colst) {
+__device__ __forceinline__ void diag_group(DiagLane& L, float (&rk)[8], const float4* __restrict__ wdat,
+                                           const float4* rows, int rbase, int r0, long long kw, long long kb, int N,
+                                           int lane, float* colst) {
 #pragma unroll
     for (int u = 0; u < 8; u++) {
         const int r = rbase + u;
-        const float4 R = wdat[r];
+        // the column entering the warp at the end of this step (same address in
+        // every lane: one broadcast load, issued a step's work ahead of its use)
+        const float4 R = rows[r - r0];
         const float rowfac = -2.f * R.z;
-        float rmin = kDgNone;
+        float ra = kDgNone, rb = kDgNone;  // the row minimum in two chains (shorter dependency)
 #pragma unroll
         for (int d = 0; d < kDgD; d++) {
             const int p = (u + d) & 7;
@@ -191,12 +197,15 @@ __device__ __forceinline__ void diag_group(DiagLane& L, float (&rk)[8], const fl
             }
             if (!kFull && (long long)r + kb + d >= (long long)N) sc = kDgNone;
             const float kf = dg_key(sc, (uint32_t)(lane * kDgD + d));
-            rmin = fminf(rmin, kf);
+            if (d & 1)
+                rb = fminf(rb, kf);
+            else
+                ra = fminf(ra, kf);
             L.ck[p] = fminf(L.ck[p], kf);
             L.C[d] = fmaf(R.x, L.cdg[p], L.C[d]);
             L.C[d] = fmaf(L.cdf[p], R.y, L.C[d]);
         }
-        rk[u] = rmin;
+        rk[u] = fminf(ra, rb);
         // the column of diagonal 0 leaves this lane for lane - 1; lane + 1's
         // enters as diagonal 7 (lane 31 loads the warp's new column)
         const int pl = u & 7;
@@ -255,39 +264,48 @@ __device__ __forceinline__ void rows_reduce(float (&rk)[8], int lane) {
     }
 }
 
+// The CTA's rows, in groups of 8; rows and the columns that left the CTA are
+// merged into the global keys every kDgFlush groups (one CTA barrier each).
 template <bool kWindow, bool kFull>
-__device__ __forceinline__ void diag_rows(DiagLane& L, const float4* __restrict__ wdat, int r0, int S, int k0,
-                                          long long kw, long long kb, int N, int w, int lane,
-                                          unsigned long long* ring, unsigned long long (*rowst)[8],
+__device__ __forceinline__ void diag_rows(DiagLane& L, const float4* __restrict__ wdat, const float4* rows, int r0,
+                                          int S, int k0, long long kw, long long kb, int N, int w, int lane,
+                                          unsigned long long* ring, unsigned long long (*rowst)[8 * kDgFlush],
                                           float (*colst)[8], unsigned long long* __restrict__ key) {
     const int ngrp = S >> 3;
     for (int grp = 0; grp < ngrp; grp++) {
         const int rbase = r0 + grp * 8;
+        const int buf = (grp / kDgFlush) & 1;
         float rk[8];
-        diag_group<kWindow, kFull>(L, rk, wdat, rbase, kb, N, lane, colst[w]);
+        diag_group<kWindow, kFull>(L, rk, wdat, rows, rbase, r0, kw, kb, N, lane, colst[w]);
         rows_reduce(rk, lane);
         __syncwarp();
         if (lane < 8) {
             unsigned long long v;
             // row rbase + lane: partner = row + diagonal
-            if (key64(rk[0], (int)kw, (long long)rbase + lane, 1, v)) atomicMin(&rowst[grp & 1][lane], v);
+            if (key64(rk[0], (int)kw, (long long)rbase + lane, 1, v))
+                atomicMin(&rowst[buf][(grp % kDgFlush) * 8 + lane], v);
             // the column that left lane 0 at step `lane`: partner = column - diagonal
             const long long c = (long long)rbase + lane + kw;
             if (key64(colst[w][lane], (int)kw, c, -1, v)) atomicMin(&ring[c & (kDgRing - 1)], v);
         }
-        __syncthreads();
-        const int t = threadIdx.x;
-        if (t < 8) {
-            const unsigned long long v = rowst[grp & 1][t];
-            if (v != kEmpty) atomicMin(&key[rbase + t], v);
-            rowst[grp & 1][t] = kEmpty;
-        } else if (t < 16) {
-            // columns that left the CTA (warp 0's lane 0) during this group
-            const long long c = (long long)rbase + (t - 8) + k0;
-            const int slot = (int)(c & (kDgRing - 1));
-            const unsigned long long v = ring[slot];
-            if (v != kEmpty) atomicMin(&key[c], v);
-            ring[slot] = kEmpty;
+        if (grp % kDgFlush == kDgFlush - 1 || grp == ngrp - 1) {
+            __syncthreads();
+            const int first = grp - grp % kDgFlush;  // first group of this flush window
+            const int nrow = (grp - first + 1) * 8;
+            const int wbase = r0 + first * 8;
+            const int t = threadIdx.x;
+            if (t < nrow) {
+                const unsigned long long v = rowst[buf][t];
+                if (v != kEmpty) atomicMin(&key[wbase + t], v);
+                rowst[buf][t] = kEmpty;
+            } else if (t >= 128 && t - 128 < nrow) {
+                // columns that left the CTA (warp 0's lane 0) during the window
+                const long long c = (long long)wbase + (t - 128) + k0;
+                const int slot = (int)(c & (kDgRing - 1));
+                const unsigned long long v = ring[slot];
+                if (v != kEmpty) atomicMin(&key[c], v);
+                ring[slot] = kEmpty;
+            }
         }
     }
 }
@@ -298,8 +316,10 @@ __global__ void __launch_bounds__(kDgThreads, 2) k_diag(const float* __restrict_
                                                         const float4* __restrict__ wdat,
                                                         const float* __restrict__ wmu32, int nseg,
                                                         unsigned long long* __restrict__ key, const Ctrl* ctrl) {
-    __shared__ unsigned long long ring[kDgRing];
-    __shared__ unsigned long long rowst[2][8];
+    extern __shared__ float4 dg_smem[];
+    float4* rows = dg_smem;                                                              // [kDgRS]
+    unsigned long long* ring = reinterpret_cast<unsigned long long*>(dg_smem + kDgRS);   // [kDgRing]
+    __shared__ unsigned long long rowst[2][8 * kDgFlush];
     __shared__ float colst[kDgWarps][8];
     if (ctrl->nonfinite) return;
     const int b = blockIdx.x / nseg, g = blockIdx.x % nseg;
@@ -311,7 +331,8 @@ __global__ void __launch_bounds__(kDgThreads, 2) k_diag(const float* __restrict_
     const bool full = (long long)r0 + S + k0 + kDgTD - 1 <= (long long)N;
     const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
     for (int i = tid; i < kDgRing; i += kDgThreads) ring[i] = kEmpty;
-    if (tid < 16) rowst[tid >> 3][tid & 7] = kEmpty;
+    if (tid < 16 * kDgFlush) rowst[tid / (8 * kDgFlush)][tid % (8 * kDgFlush)] = kEmpty;
+    for (int i = tid; i < S; i += kDgThreads) rows[i] = wdat[r0 + i];
     const long long kw = (long long)k0 + (long long)w * kDgWarpDiags;  // the warp's first diagonal
     const long long kb = kw + (long long)lane * kDgD;                   // this lane's first diagonal
 
@@ -360,9 +381,9 @@ __global__ void __launch_bounds__(kDgThreads, 2) k_diag(const float* __restrict_
     }
     __syncthreads();
     if (full)
-        diag_rows<kWindow, true>(L, wdat, r0, S, k0, kw, kb, N, w, lane, ring, rowst, colst, key);
+        diag_rows<kWindow, true>(L, wdat, rows, r0, S, k0, kw, kb, N, w, lane, ring, rowst, colst, key);
     else
-        diag_rows<kWindow, false>(L, wdat, r0, S, k0, kw, kb, N, w, lane, ring, rowst, colst, key);
+        diag_rows<kWindow, false>(L, wdat, rows, r0, S, k0, kw, kb, N, w, lane, ring, rowst, colst, key);
     // columns still inside the lanes' windows: slot p holds diagonal p (S is a
     // multiple of 8), column r0 + S + kb + p
 #pragma unroll
@@ -627,10 +648,18 @@ cudaError_t diag_core(dd_plan_s* p, const float* y, bool window, int wave, cudaS
     const long long grid = (long long)B * G;
     if (grid < 1 || grid > 0x7fffffffll) return cudaErrorInvalidValue;
     if (wave >= 0) prof_mark(p, s, true);
+    // 64 KiB of dynamic shared memory (row data + column ring): opt in on the current device
+    cudaError_t attr = window ? cudaFuncSetAttribute(k_diag<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                     (int)kDgSmem)
+                              : cudaFuncSetAttribute(k_diag<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                     (int)kDgSmem);
+    if (attr != cudaSuccess) return attr;
     if (window)
-        k_diag<true><<<(unsigned)grid, kDgThreads, 0, s>>>(y, p->m, N, n, p->wdat, p->wmu32, G, p->dkey, p->ctrl);
+        k_diag<true><<<(unsigned)grid, kDgThreads, kDgSmem, s>>>(y, p->m, N, n, p->wdat, p->wmu32, G, p->dkey,
+                                                                 p->ctrl);
     else
-        k_diag<false><<<(unsigned)grid, kDgThreads, 0, s>>>(y, p->m, N, n, p->wdat, p->wmu32, G, p->dkey, p->ctrl);
+        k_diag<false><<<(unsigned)grid, kDgThreads, kDgSmem, s>>>(y, p->m, N, n, p->wdat, p->wmu32, G, p->dkey,
+                                                                  p->ctrl);
     if (wave >= 0) prof_mark(p, s, false);
     p->launches += 3;
     return cudaGetLastError();
