@@ -61,7 +61,9 @@ typedef enum {
     DD_EBUSY = 6,       /* the plan is in use by another host thread */
     DD_ENOTSUP = 7      /* option combination not supported for these sizes (tensor-core
                            forms for n > 65536; per-window with a tensor-core precision or
-                           shards; diagonal-recurrence workspace for N > 2^26) */
+                           shards; diagonal-recurrence workspace for N > 2^26), or a wave
+                           with more than 2^31 work items (its 32-bit work counter would
+                           wrap; the wave stops and the call reports this status) */
 } dd_status_t;
 
 /* Arithmetic of the distance tiles.

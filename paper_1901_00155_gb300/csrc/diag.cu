@@ -542,7 +542,11 @@ __global__ void __launch_bounds__(256) k_wrescore(ListRef rows, const float* __r
         if (threadIdx.x == 0) sh_item = atomicAdd(&ctrl->work[slot], 1);
         __syncthreads();
         const long long item = sh_item;
-        if (item >= items) break;
+        if (item < 0 || item >= items) {
+            // a negative claim: the 32-bit work counter wrapped (more than 2^31 items)
+            if (item < 0 && threadIdx.x == 0) atomicExch(&ctrl->err, DD_ENOTSUP);
+            break;
+        }
         const int r = (int)(item / nchunk), c = (int)(item % nchunk);
         const int x = rows.base[off + r];
         if (x < 0 || x >= N) {
@@ -597,10 +601,15 @@ __global__ void __launch_bounds__(256) k_wcand(const float* __restrict__ ub, con
     if (ctrl->nonfinite) return;
     const unsigned long long lbb = *lbbits;
     const double lb = lbb == 0x7ff0000000000000ull ? 0.0 : __longlong_as_double((long long)lbb) * (1.0 - 1e-9);
+    // every upper bound 0 (e.g. only constant windows): every row's distance is 0 and the
+    // row with the largest key, the smallest index, is the discord -- rescore it alone
+    const unsigned long long k = ctrl->key;
+    const bool all_zero = k != 0 && (k >> 32) == 0;
+    const int r0 = (int)(0xffffffffu - (uint32_t)(k & 0xffffffffull));
     const int lane = threadIdx.x & 31;
     for (int base = blockIdx.x * blockDim.x; base < N; base += gridDim.x * blockDim.x) {
         const int x = base + threadIdx.x;
-        const bool take = x < N && !excl[x] && (double)ub[x] >= lb;
+        const bool take = x < N && !excl[x] && (all_zero ? x == r0 : (double)ub[x] >= lb);
         const unsigned mask = __ballot_sync(0xffffffffu, take);
         if (!mask) continue;
         int at = 0;

@@ -59,7 +59,11 @@ __global__ void __launch_bounds__(256) k_rescore64(ListRef cand, TcBound bound, 
         if (threadIdx.x == 0) sh_item = atomicAdd(&ctrl->work[slot], 1);
         __syncthreads();
         const int item = sh_item;
-        if (item >= items) break;
+        if (item < 0 || item >= items) {
+            // a negative claim: the 32-bit work counter wrapped (more than 2^31 items)
+            if (item < 0 && threadIdx.x == 0) atomicExch(&ctrl->err, DD_ENOTSUP);
+            break;
+        }
         const int r = item / nchunk, c = item % nchunk;
         const int i = cand.base[off + r];
         const float D = __uint_as_float(rmin[i]);

@@ -134,7 +134,11 @@ __global__ void __launch_bounds__(NT, 2) k_scan_fp32(ScanArgs a) {
         if (tid == 0) sm.item = atomicAdd(&a.ctrl->work[a.work_slot], 1);
         __syncthreads();
         const int item = sm.item;
-        if (item >= items) break;
+        if (item < 0 || item >= items) {
+            // a negative claim: the 32-bit work counter wrapped (more than 2^31 items)
+            if (item < 0 && tid == 0) atomicExch(&a.ctrl->err, DD_ENOTSUP);
+            break;
+        }
         // item -> row tile + column tiles
         int rt, ct0, ct1;
         int pa = 0, pb = 0, dir = 1;  // mode 2: positions [pa, pb) of sig, walked up (dir 1) or down

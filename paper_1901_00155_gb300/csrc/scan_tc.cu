@@ -330,7 +330,7 @@ __global__ void __launch_bounds__(kTcThreadsV2, 1)
         int base = 0;
         if (lane == 0) base = atomicAdd(&a.ctrl->work[a.work_slot], claim);
         base = __shfl_sync(0xffffffffu, base, 0);
-        while (ok && base < items && !*abort) {
+        while (ok && base >= 0 && base < items && !*abort) {
             int rt[kClaim], pa[kClaim], pb[kClaim], dir[kClaim];
             float4 rowd[kClaim][4];  // per row: (sqrt(n) mu, c, running minimum, orig index bits)
             float segL[kClaim], segH[kClaim];
@@ -458,6 +458,8 @@ __global__ void __launch_bounds__(kTcThreadsV2, 1)
             if (!ok) {
                 atomicExch(&a.ctrl->err, DD_ETIMEOUT);
                 *abort = 1;
+            } else if (base < 0) {
+                atomicExch(&a.ctrl->err, DD_ENOTSUP);  // the 32-bit work counter wrapped
             }
             // end marker (bounded wait; on abort the consumers leave on their own)
             if (mbar_wait(&h.it_empty[ring], rph ^ 1u, abort)) {

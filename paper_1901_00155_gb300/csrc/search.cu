@@ -417,6 +417,10 @@ __global__ void k_finalize(const Ctrl* ctrl, dd_result_t* out) {
         r.status = DD_OK;
         r.index = 0;
         r.nn_distance = 0.0;
+    } else if (ctrl->err) {
+        r.status = ctrl->err;
+        r.index = -1;
+        r.nn_distance = 0.0;
     } else if (ctrl->key == 0ull) {
         r.status = DD_ECUDA;
         r.index = -1;
