@@ -201,6 +201,11 @@ class Plan:
             out = torch.empty(self.N, dtype=torch.float32, device=T.device)
         if index is True:
             index = torch.empty(self.N, dtype=torch.int32, device=T.device)
+        if index is not None and index is not False:
+            if index.dtype != torch.int32 or not index.is_cuda or not index.is_contiguous() or index.numel() < self.N:
+                raise TypeError(f"index must be a contiguous int32 CUDA tensor of at least {self.N} elements")
+        if out.dtype != torch.float32 or not out.is_cuda or not out.is_contiguous() or out.numel() < self.N:
+            raise TypeError(f"out must be a contiguous float32 CUDA tensor of at least {self.N} elements")
         ip = ctypes.c_void_p(index.data_ptr()) if index is not None and index is not False else None
         _check(self._lib.dd_nn_profile_diag(self._ptr, ctypes.c_void_p(T.data_ptr()), ctypes.c_void_p(out.data_ptr()),
                                             ip, _stream_ptr(stream)), "dd_nn_profile_diag")
