@@ -477,8 +477,11 @@ def main():
         exh = _exhaustive(dd, Td, m, n, [f for f in ("tc_fp16", "fp32") if f in supported], peaks)
     win = None
     if not args.no_window:
-        win = _window(dd, Td, m, n, peaks)
-        if exh and "fp32" in exh:
+        try:
+            win = _window(dd, Td, m, n, peaks)
+        except Exception as e:  # an optional object: report it, keep the headline line
+            win = {"error": f"{type(e).__name__}: {e}"}
+        if exh and "fp32" in exh and "global_diag_profile" in win:
             win["global_diag_profile"]["vs_direct_fp32_exhaustive"] = \
                 win["global_diag_profile"]["pairs_per_s"] / exh["fp32"]["pairs_per_s"]
     if rank == 0:

@@ -16,18 +16,19 @@
 // normalised form is the zero vector (then the C term is absent).  So a pair
 // costs O(1) work instead of the O(n) of Eq. 1.
 //
-// k_diag: one CTA = 2048 consecutive diagonals x 2048 consecutive rows.  Each
-// lane owns 8 consecutive diagonals and walks the rows, all lanes of the CTA
-// on the same row at a time; every diagonal is re-seeded with a direct FP32
-// dot product at the CTA's first row, so rounding accumulates over at most
-// 2048 steps.  A pair's score goes into a 32-bit key whose low 8 bits hold the
+// k_diag: one CTA = 2048 consecutive diagonals x 2048 consecutive rows, whose
+// row data it stages once in shared memory.  Each lane owns 8 consecutive
+// diagonals and walks the rows, all lanes of the CTA on the same row at a
+// time; every diagonal is re-seeded with a direct FP32 dot product at the
+// CTA's first row, so rounding accumulates over at most 2048 steps.  A pair's score goes into a 32-bit key whose low 8 bits hold the
 // diagonal inside the warp, so one float minimum tracks the value and its
 // argument.  Per step:
 //   - row minimum: each lane keeps one key per row for 8 steps; a transposing
 //     shuffle reduction then leaves row r's minimum over the warp's 256
 //     diagonals in one lane, which merges it across the CTA's warps in shared
-//     memory and then, once per row and CTA, into the global 64-bit key
-//     (value bits << 32 | partner index) with atomicMin;
+//     memory and then (every 32 rows, one CTA barrier) into the global 64-bit
+//     key (value bits << 32 | partner index) with atomicMin, once per row and
+//     CTA;
 //   - column minimum: a column moves through a lane's 8 diagonals in 8 steps
 //     and then into the next lower lane; its running key and column data pass
 //     down with __shfl_down_sync, leave the warp at lane 0, merge across
