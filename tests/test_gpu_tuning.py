@@ -1,0 +1,29 @@
+"""Option autotuner on the GPU: every candidate finds the oracle's discord, and the table's
+winner is one of them (timing order is not asserted)."""
+import math
+
+import pytest
+
+import oracle
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def test_tune_small_shape_against_oracle(tmp_path):
+    from paper_1901_00155_gb300 import synth, tuning
+    cands = [{"precision": "fp32", "local_cols": 128, "refine_k": 128},
+             {"precision": "tc_fp16", "local_cols": 128, "refine_k": 64}]
+    table = tuning.tune([(8192, 64)], cands, reps=2, seed=3)
+    e = table["entries"]["n64/m8192"]
+    assert e["options"] in cands and e["ms"] > 0
+    assert all(t["ms"] is not None and t["ms"] > 0 for t in e["trials"])
+    T, _ = synth.make_series(synth.SeriesSpec("rw", 8192, 64, 3, ("burst",)))
+    i_ref, d2_ref = oracle.discord_brute(T, 64)
+    assert e["nn_distance"] == pytest.approx(math.sqrt(d2_ref), rel=1e-4)
+    if e["index"] != i_ref:
+        nn, _ = oracle.nn_rows(T, 64, [e["index"]])
+        assert nn[0] == pytest.approx(d2_ref, rel=1e-4)
+    path = str(tmp_path / "t.json")
+    tuning.save(table, path)
+    assert tuning.lookup(tuning.load(path), 8000, 64) == e["options"]

@@ -1,0 +1,101 @@
+"""Option autotuner (host logic): bucketing, selection of the fastest option set, unsupported
+forms, the agreement check, and the JSON table.  The GPU timer is replaced by a fake here; the
+real one is exercised in tests/test_gpu_tuning.py."""
+import math
+
+import pytest
+
+from paper_1901_00155_gb300 import tuning
+
+
+class Unsupported(Exception):
+    pass
+
+
+def test_bucket_and_key():
+    assert tuning.bucket(1) == 2048 and tuning.bucket(2048) == 2048 and tuning.bucket(2049) == 4096
+    assert tuning.bucket(1 << 20) == 1 << 20 and tuning.bucket((1 << 20) + 1) == 1 << 21
+    assert tuning.bucket(1 << 40) == 1 << 31
+    assert tuning.key(1000000, 256) == "n256/m1048576"
+    with pytest.raises(ValueError):
+        tuning.bucket(0)
+
+
+def _fake(times, results, unsupported=()):
+    calls = []
+
+    def timer(opts, T, n, reps):
+        calls.append((tuple(sorted(opts.items())), T, n, reps))
+        k = (opts["precision"], opts["local_cols"])
+        if k in unsupported:
+            raise Unsupported(k)
+        return times[k], results.get(k, (7, 2.5))[0], results.get(k, (7, 2.5))[1]
+    return timer, calls
+
+
+CANDS = [{"precision": p, "local_cols": lc} for p in ("tc_fp16", "fp32") for lc in (64, 128)]
+
+
+def test_tune_picks_fastest_and_records_trials():
+    times = {("tc_fp16", 64): 3.0, ("tc_fp16", 128): 1.5, ("fp32", 64): 9.0, ("fp32", 128): 8.0}
+    timer, calls = _fake(times, {})
+    series = lambda m, n, seed: ("series", m, n, seed)  # noqa: E731
+    table = tuning.tune([(5000, 64), (1 << 20, 256)], CANDS, reps=2, seed=4, timer=timer, series=series,
+                        unsupported=Unsupported)
+    assert set(table["entries"]) == {"n64/m8192", "n256/m1048576"}
+    e = table["entries"]["n64/m8192"]
+    assert e["options"] == {"precision": "tc_fp16", "local_cols": 128} and e["ms"] == 1.5
+    assert len(e["trials"]) == 4 and (e["index"], e["nn_distance"]) == (7, 2.5)
+    assert all(c[1] == ("series", 5000, 64, 4) for c in calls[:4]) and all(c[3] == 2 for c in calls)
+    assert tuning.lookup(table, 6000, 64) == {"precision": "tc_fp16", "local_cols": 128}
+    assert tuning.lookup(table, 9000, 64) == {}      # another m bucket
+    assert tuning.lookup(table, 6000, 128) == {}     # another n
+    assert tuning.lookup({}, 6000, 64) == {}
+
+
+def test_unsupported_forms_are_skipped_and_all_unsupported_raises():
+    times = {("tc_fp16", 64): 1.0, ("tc_fp16", 128): 1.0, ("fp32", 64): 5.0, ("fp32", 128): 4.0}
+    timer, _ = _fake(times, {}, unsupported={("tc_fp16", 64), ("tc_fp16", 128)})
+    t = tuning.tune([(4096, 100000 // 64)], CANDS, timer=timer, series=lambda m, n, s: None,
+                    unsupported=Unsupported)
+    e = next(iter(t["entries"].values()))
+    assert e["options"]["precision"] == "fp32" and e["ms"] == 4.0
+    assert sum(1 for tr in e["trials"] if tr["ms"] is None) == 2
+    timer2, _ = _fake(times, {}, unsupported=set(times))
+    with pytest.raises(tuning.TuningError):
+        tuning.tune([(4096, 8)], CANDS, timer=timer2, series=lambda m, n, s: None, unsupported=Unsupported)
+
+
+def test_disagreeing_candidates_raise_and_ties_pass():
+    times = {k: 1.0 for k in [("tc_fp16", 64), ("tc_fp16", 128), ("fp32", 64), ("fp32", 128)]}
+    # a different index with an equal distance (a tie) is accepted
+    timer, _ = _fake(times, {("fp32", 64): (9, 2.5 * (1 + 1e-6))})
+    tuning.tune([(4096, 8)], CANDS, timer=timer, series=lambda m, n, s: None, unsupported=Unsupported)
+    # a different distance is a bug
+    timer, _ = _fake(times, {("fp32", 128): (7, 2.6)})
+    with pytest.raises(tuning.TuningError):
+        tuning.tune([(4096, 8)], CANDS, timer=timer, series=lambda m, n, s: None, unsupported=Unsupported)
+    with pytest.raises(ValueError):
+        tuning.tune([(4096, 8)], [], timer=timer, series=lambda m, n, s: None, unsupported=Unsupported)
+
+
+def test_table_round_trip(tmp_path):
+    times = {("tc_fp16", 64): 2.0, ("tc_fp16", 128): 1.0, ("fp32", 64): 3.0, ("fp32", 128): 3.0}
+    timer, _ = _fake(times, {})
+    table = tuning.tune([(3000, 16)], CANDS, timer=timer, series=lambda m, n, s: None, unsupported=Unsupported)
+    path = str(tmp_path / "tuned.json")
+    tuning.save(table, path)
+    back = tuning.load(path)
+    assert back == table and tuning.lookup(back, 4000, 16)["local_cols"] == 128
+    back["version"] = 99
+    tuning.save(back, path)
+    with pytest.raises(tuning.TuningError):
+        tuning.load(path)
+    assert tuning.lookup(back, 4000, 16) == {}
+
+
+def test_default_candidates_cover_the_speed_options():
+    c = tuning.DEFAULT_CANDIDATES
+    assert len(c) == 27 and len({tuple(sorted(d.items())) for d in c}) == 27
+    assert {d["precision"] for d in c} == {"tc_fp16", "tc_bf16", "fp32"}
+    assert all(math.log2(d["local_cols"]).is_integer() and d["refine_k"] in (64, 128, 256) for d in c)
