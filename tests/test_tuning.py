@@ -99,3 +99,11 @@ def test_default_candidates_cover_the_speed_options():
     assert len(c) == 27 and len({tuple(sorted(d.items())) for d in c}) == 27
     assert {d["precision"] for d in c} == {"tc_fp16", "tc_bf16", "fp32"}
     assert all(math.log2(d["local_cols"]).is_integer() and d["refine_k"] in (64, 128, 256) for d in c)
+
+
+def test_candidates_are_valid_plan_options():
+    """Every default candidate is an option set the library accepts (checked host-side)."""
+    import paper_1901_00155_gb300 as dd
+    for c in tuning.DEFAULT_CANDIDATES:
+        dd._options(**c)
+        assert dd.Plan.footprint(1 << 16, 256, **c) > 0
