@@ -289,8 +289,35 @@ def find_discord(T, n: int, precision="fp32", stream=None, **opts) -> DiscordRes
         return p.find_discord(T, stream)
 
 
-def find_discord_batched(series, ns, precision="fp32", stream=None, **opts):
-    """Independent searches over CUDA float32 tensors of possibly different lengths."""
+def group_by_tuned_options(ms, ns, table, precision="fp32", **opts):
+    """Split a batch by the options a tuning table (see tuning.py) gives each (m, n): returns
+    [(options dict, [positions in the batch])], in first-appearance order.  Series without an
+    entry keep (precision, opts)."""
+    from . import tuning
+
+    groups, where = [], {}
+    for pos, (m, n) in enumerate(zip(ms, ns)):
+        o = {"precision": precision, **opts, **tuning.lookup(table, int(m), int(n))}
+        key = tuple(sorted(o.items()))
+        if key not in where:
+            where[key] = len(groups)
+            groups.append((o, []))
+        groups[where[key]][1].append(pos)
+    return groups
+
+
+def find_discord_batched(series, ns, precision="fp32", stream=None, table=None, **opts):
+    """Independent searches over CUDA float32 tensors of possibly different lengths.  With a
+    tuning table, each series runs with the options tuned for its (n, m bucket): one batched call
+    per distinct option set, results in the input order."""
+    if table is not None:
+        results = [None] * len(series)
+        for o, pos in group_by_tuned_options([s.numel() for s in series], ns, table, precision, **opts):
+            prec = o.pop("precision")
+            part = find_discord_batched([series[i] for i in pos], [ns[i] for i in pos], prec, stream, None, **o)
+            for i, r in zip(pos, part):
+                results[i] = r
+        return results
     lib = _lib.load()
     k = len(series)
     ptrs = (ctypes.c_void_p * k)(*[ctypes.c_void_p(s.data_ptr()) for s in series])

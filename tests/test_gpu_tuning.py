@@ -27,3 +27,23 @@ def test_tune_small_shape_against_oracle(tmp_path):
     path = str(tmp_path / "t.json")
     tuning.save(table, path)
     assert tuning.lookup(tuning.load(path), 8000, 64) == e["options"]
+
+
+def test_batched_with_table_matches_solo():
+    import numpy as np
+
+    import paper_1901_00155_gb300 as dd
+    from paper_1901_00155_gb300 import synth, tuning
+    table = {"version": tuning.TABLE_VERSION, "entries": {
+        "n64/m8192": {"options": {"precision": "tc_fp16", "local_cols": 64, "refine_k": 64}}}}
+    rng = np.random.default_rng(11)
+    series = [np.cumsum(rng.standard_normal(m)).astype(np.float32) for m in (8000, 3000, 7000)]
+    ns = [64, 64, 32]
+    got = dd.find_discord_batched([torch.from_numpy(T).cuda() for T in series], ns, table=table)
+    for T, n, g in zip(series, ns, got):
+        i_ref, d2_ref = oracle.discord_brute(T, n)
+        assert g.nn_distance == pytest.approx(math.sqrt(d2_ref), rel=1e-4)
+        if g.index != i_ref:
+            nn, _ = oracle.nn_rows(T, n, [g.index])
+            assert nn[0] == pytest.approx(d2_ref, rel=1e-4)
+    assert got[0].exact and not got[1].exact  # the tuned (tensor-core) and the default (FP32) forms

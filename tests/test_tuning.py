@@ -107,3 +107,18 @@ def test_candidates_are_valid_plan_options():
     for c in tuning.DEFAULT_CANDIDATES:
         dd._options(**c)
         assert dd.Plan.footprint(1 << 16, 256, **c) > 0
+
+
+def test_batch_groups_follow_the_table():
+    import paper_1901_00155_gb300 as dd
+    table = {"version": tuning.TABLE_VERSION, "entries": {
+        "n64/m4096": {"options": {"precision": "tc_fp16", "local_cols": 64, "refine_k": 64}},
+        "n128/m65536": {"options": {"precision": "fp32", "local_cols": 256, "refine_k": 128}}}}
+    ms = [3000, 50000, 4000, 9000, 60000]
+    ns = [64, 128, 64, 64, 128]
+    groups = dd.group_by_tuned_options(ms, ns, table, "fp32", word_cols=256)
+    assert [g[1] for g in groups] == [[0, 2], [1, 4], [3]]
+    assert groups[0][0] == {"precision": "tc_fp16", "local_cols": 64, "refine_k": 64, "word_cols": 256}
+    assert groups[1][0] == {"precision": "fp32", "local_cols": 256, "refine_k": 128, "word_cols": 256}
+    assert groups[2][0] == {"precision": "fp32", "word_cols": 256}  # m=9000 has no entry
+    assert dd.group_by_tuned_options(ms, ns, {}, "fp32") == [({"precision": "fp32"}, [0, 1, 2, 3, 4])]
