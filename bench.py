@@ -16,7 +16,9 @@ roofline = the distance-tile kernel, algorithmic work / its CUDA-event time
          against the GB300 peak of the pipe that bounds it.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-       [--precision fp32|tc_fp16|tc_bf16|all]
+       [--precision all|best|fp32|tc_fp16|tc_bf16]
+By default every form is timed (the metric compares the tensor-core forms with the
+plain FP32 form); the headline value is the fastest exact (tensor-core) form.
 Under torchrun each rank runs an independent replica (the search does not
 exchange data between GPUs); rank 0 prints one JSON line.
 """
@@ -37,8 +39,44 @@ sys.path.insert(0, ROOT)
 
 METRIC = "pair-distances/s & time-to-discord (m=2^20,n=256), TC vs FP32; serve p99 ms"
 UNIT = "pair-distances/s"
-SM_COUNT = 152
-FP32_LANES_PER_SM = 128
+FP32_LANES_PER_SM = 128  # FP32 FMA lanes per SM (Blackwell)
+
+
+def _alu_peak(sms: int, peaks) -> float:
+    """FP32 lane instructions per second: SMs x 128 lanes x the maximum SM clock (T/s)."""
+    return sms * FP32_LANES_PER_SM * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+
+
+def _probe_peaks(dd, dev) -> dict:
+    """The FP16 and FP32 / FP64 peaks the driver does not measure: cuBLAS FP16 (and BF16, for
+    the ratio) dense 8192^3 GEMMs, best of 10 after warm-up, and the library's own FMA-rate
+    probes of the CUDA cores."""
+    import torch
+    out = {}
+    for name, dt in (("fp16", torch.float16), ("bf16", torch.bfloat16)):
+        a = torch.randn(8192, 8192, device=dev, dtype=dt)
+        b = torch.randn(8192, 8192, device=dev, dtype=dt)
+        for _ in range(3):
+            torch.matmul(a, b)
+        ts = []
+        for _ in range(10):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            torch.matmul(a, b)
+            e1.record()
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        out[f"{name}_tflops_cublas"] = 2.0 * 8192 ** 3 / (min(ts) * 1e-3) / 1e12
+        del a, b
+    out["fp32_fma_per_s"] = dd.probe_fma_rate(False)
+    out["fp64_fma_per_s"] = dd.probe_fma_rate(True)
+    out["fp32_tflops"] = 2.0 * out["fp32_fma_per_s"] / 1e12
+    out["fp64_tflops"] = 2.0 * out["fp64_fma_per_s"] / 1e12
+    out["how"] = ("torch.matmul 8192^3 fp16 / bf16, best of 10 (CUDA events); dd_probe_fma_rate: independent "
+                  "FFMA / DFMA chains on every SM for ~20 ms")
+    torch.cuda.empty_cache()
+    return out
 
 
 def _peaks():
@@ -128,7 +166,7 @@ def _kernel_traffic(precision: str):
     return ent["dram_bytes_per_launch"] if h == ent.get("source_sha256_16") else None
 
 
-def _exhaustive(dd, Td, m: int, n: int, forms, peaks, rows: int = 8192, reps: int = 3) -> dict:
+def _exhaustive(dd, Td, m: int, n: int, forms, peaks, sms: int, rows: int = 8192, reps: int = 3) -> dict:
     """Exhaustive mode (no abandon, metric (i)): dd_nn_rows over `rows` evenly spaced
     rows against all N columns, CUDA events around each call on its stream."""
     import torch
@@ -154,7 +192,7 @@ def _exhaustive(dd, Td, m: int, n: int, forms, peaks, rows: int = 8192, reps: in
         pairs = R.numel() * N
         if prec == "fp32":
             work = 2.0 * n * pairs / (ms * 1e-3) / 1e12
-            peak = SM_COUNT * FP32_LANES_PER_SM * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+            peak = _alu_peak(sms, peaks)
             unit = "Tinstr/s"
         else:
             work = 2.0 * plan_nkpad(n) * pairs / (ms * 1e-3) / 1e12
@@ -165,7 +203,7 @@ def _exhaustive(dd, Td, m: int, n: int, forms, peaks, rows: int = 8192, reps: in
     return out
 
 
-def _window(dd, Td, m: int, n: int, peaks, reps: int = 3) -> dict:
+def _window(dd, Td, m: int, n: int, peaks, sms: int, reps: int = 3) -> dict:
     """Per-window z-normalised discords and the diagonal-recurrence profile (exhaustive, every
     pair once): time to the exact per-window discord, and the global-form profile rate next to
     the direct FP32 exhaustive rate.  The recurrence kernel is bound by the FP32/ALU issue rate;
@@ -174,7 +212,7 @@ def _window(dd, Td, m: int, n: int, peaks, reps: int = 3) -> dict:
     import torch
     N = m - n + 1
     pairs = _pairs_unordered(N, n)
-    peak = SM_COUNT * FP32_LANES_PER_SM * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+    peak = _alu_peak(sms, peaks)
     out = {}
     with dd.Plan(m, n, znorm="window") as p:
         p.set_profiling(True)
@@ -304,11 +342,13 @@ def _reference_arm(args, rank: int):
 
 
 def _cpu_baseline():
+    """The FP64 oracle's CPU HOTSAX on a bounded prefix of the benchmark series (about 10-30 s on
+    the host's cores), as it stands."""
     import oracle
     from paper_1901_00155_gb300 import synth
     spec = synth.workload_large(0)
     T, _ = synth.make_series(spec)
-    m_s = 1 << 17
+    m_s = 1 << 18
     Ts = T[:m_s].copy()
     oracle.build()
     t0 = time.perf_counter()
@@ -326,7 +366,10 @@ def main():
     ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="best", choices=["best", "all", "fp32", "tc_fp16", "tc_bf16"])
+    ap.add_argument("--precision", default="all", choices=["all", "best", "fp32", "tc_fp16", "tc_bf16"],
+                    help="all (default): every form, headline on the fastest exact one; best: the first "
+                         "supported tensor-core form only")
+    ap.add_argument("--no-probe", action="store_true", help="skip the FP16 / FP32 / FP64 peak probes")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 512-series batched search")
     ap.add_argument("--eager", action="store_true",
@@ -359,6 +402,7 @@ def main():
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
     if world > 1:
         dist.init_process_group("nccl", device_id=dev)
 
@@ -446,10 +490,11 @@ def main():
         if prec == "fp32":
             work = 2.0 * n * pairs  # one FP32 subtract + one FFMA per element of each pair
             achieved = work / (dist_ms * 1e-3) / 1e12 if dist_ms > 0 else 0.0
-            peak = SM_COUNT * FP32_LANES_PER_SM * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+            peak = _alu_peak(sms, peaks)
             roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tinstr/s",
                     "frac": achieved / peak if peak else None, "traffic": _kernel_traffic(prec),
-                    "kernel": "k_scan_fp32", "peak_source": "derived: 152 SM x 128 FP32 lanes x max SM clock",
+                    "kernel": "k_scan_fp32",
+                    "peak_source": f"derived: {sms} SMs (device query) x 128 FP32 lanes x max SM clock",
                     "launches_per_step": dlaunch / args.steps}
         else:
             work = 2.0 * plan_nkpad(n) * pairs
@@ -466,33 +511,44 @@ def main():
                          "dist_kernel_ms_per_step": dist_ms / args.steps}
         plan.close()
 
-    head = results[forms[0]]
+    exact = [f for f in forms if f != "fp32"]
+    head_form = min(exact or forms, key=lambda f: results[f]["time_to_discord_ms"])
+    head = results[head_form]
     batch = serve = None
     if not args.no_batch:
-        batch = _batch(dd, forms[0])
+        batch = _batch(dd, head_form)
     if not args.no_serve:
-        serve = _serve(dd, forms[0])
+        serve = _serve(dd, head_form)
     exh = None
     if not args.no_exhaustive:
-        exh = _exhaustive(dd, Td, m, n, [f for f in ("tc_fp16", "fp32") if f in supported], peaks)
+        exh = _exhaustive(dd, Td, m, n, [f for f in ("tc_fp16", "tc_bf16", "fp32") if f in supported], peaks, sms)
     win = None
     if not args.no_window:
         try:
-            win = _window(dd, Td, m, n, peaks)
+            win = _window(dd, Td, m, n, peaks, sms)
         except Exception as e:  # an optional object: report it, keep the headline line
             win = {"error": f"{type(e).__name__}: {e}"}
         if exh and "fp32" in exh and "global_diag_profile" in win:
             win["global_diag_profile"]["vs_direct_fp32_exhaustive"] = \
                 win["global_diag_profile"]["pairs_per_s"] / exh["fp32"]["pairs_per_s"]
+    probed = None
+    if not args.no_probe:
+        try:
+            probed = _probe_peaks(dd, dev)
+            probed["alu_peak_derived_tinstr"] = _alu_peak(sms, peaks)
+            probed["sms"] = sms
+        except Exception as e:
+            probed = {"error": f"{type(e).__name__}: {e}"}
     if rank == 0:
         cpu = None if args.no_cpu_baseline else _cpu_baseline()
         line = {"metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": head["time_to_discord_ms"], "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f32" if forms[0] == "fp32" else "f16xf16->f32+f64",
+                "scaling": "weak", "vs_baseline": None,
+                "dtype": {"fp32": "f32", "tc_fp16": "f16xf16->f32+f64", "tc_bf16": "bf16xbf16->f32+f64"}[head_form],
                 "data": "synthetic",
                 "config": {"workload": f"{spec.kind} m={m} n={n}, {len(spec.anomalies)} anomalies, seed {spec.seed} "
                                        f"(synthetic stand-in for SCD-1M)",
-                           "m": m, "n": n, "precision": forms[0], "parallelism": f"replicas x{world}",
+                           "m": m, "n": n, "precision": head_form, "parallelism": f"replicas x{world}",
                            "l2": "flushed between steps (256 MiB write)"},
                 "time_to_discord_ms": head["time_to_discord_ms"],
                 "roofline": head["roofline"], "cpu_baseline": cpu,
@@ -502,7 +558,9 @@ def main():
                 "forms": {k: {kk: vv for kk, vv in v.items() if kk != "roofline"} | {"roofline_frac": v["roofline"]["frac"]}
                           for k, v in results.items()},
                 "discord": {"index": head["index"], "nn_distance": head["nn_distance"]},
-                "exhaustive": exh, "window": win, "batch": batch, "serve": serve}
+                "tc_vs_fp32_time_to_discord": (results["fp32"]["time_to_discord_ms"] / head["time_to_discord_ms"]
+                                               if "fp32" in results and head_form != "fp32" else None),
+                "exhaustive": exh, "window": win, "batch": batch, "serve": serve, "peaks_probed": probed}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

@@ -148,6 +148,27 @@ typedef struct {
     const float* t32;          /* [m] t^ rounded to FP32 */
 } dd_view_t;
 
+/* Per-row error bound of the tensor-core Gram form, for inspection and
+ * testing.  The Gram tiles compute, for a row i and a column j, a distance D
+ * from FP16/BF16 operands with FP32 accumulation (Eq. 1 squared, rewritten as
+ * c_i + c_j + n (mu_i - mu_j)^2 - 2 <x'_i, x'_j> over mean-centred rows); the
+ * library proves |D - d^2_ij| <= F_i(D) with
+ *     F_i(D) = alpha_i + beta D + gam_i sqrt(max(D, 0) + q2_i),
+ * which makes the row's running minimum D_i bracket its nearest-neighbour
+ * distance: D_i - F_i(D_i) - gam_i^2 <= nn^2_i <= D_i + F_i(D_i) once every
+ * column has been scanned.  The early abandon of Algorithm 4 relies on it.
+ * Pointers are device addresses owned by the plan (N floats each, indexed by
+ * the original row), filled by each call on a tensor-core plan (dd_prep
+ * excluded) and valid until dd_plan_destroy. */
+typedef struct {
+    int64_t N;
+    int32_t precision;   /* dd_precision_t of the plan */
+    float beta;          /* relative term, the same for every row */
+    const float* alpha;  /* [N] absolute term */
+    const float* gam;    /* [N] coefficient of the square-root term */
+    const float* q2;     /* [N] offset under the square root */
+} dd_bound_view_t;
+
 /* ---- plans ------------------------------------------------------------- */
 
 /* Fills the defaults listed above. */
@@ -251,6 +272,11 @@ DD_API dd_status_t dd_prep(dd_plan_t plan, const float* T_dev, void* stream);
 /* Device views of the preparation arrays of the last call on the plan. */
 DD_API dd_status_t dd_plan_view(dd_plan_t plan, dd_view_t* view);
 
+/* The per-row error-bound terms of a tensor-core plan (dd_bound_view_t).
+ * Errors: DD_EINVAL (null arguments), DD_ENOTSUP (an FP32 plan has no Gram
+ * bound). */
+DD_API dd_status_t dd_plan_bound_view(dd_plan_t plan, dd_bound_view_t* view);
+
 /* Number of this library's kernels launched by the plan's last call (a graph
  * replay does not count the kernels of conditional waves it skipped).  Reads
  * two device counters: call it after the call has finished. */
@@ -349,8 +375,20 @@ DD_API int32_t dd_plan_get_waves(dd_plan_t plan, dd_wave_t* out, int32_t cap);
  *     host threads) race.  Order them on one stream.
  *   - The first call on a device looks up the scratch address with that
  *     device current; make it before any stream capture.
- *   - A series holding NaN or Inf yields NaN in every output element. */
+ *   - A series holding NaN or Inf yields NaN in every output element.
+ *   - A CUDA error already pending on the calling thread (cudaPeekAtLastError)
+ *     makes the call return DD_ECUDA at once, launching nothing and leaving
+ *     that error pending for its owner. */
 DD_API dd_status_t dd_nn_profile_static(const float* T_dev, int64_t m, int32_t n, float* nn2_dev, void* stream);
+
+/* Measured peak rate of this device's CUDA-core FMA pipe, for roofline
+ * denominators (no counterpart in the paper).  fp64 = 0: FP32 FFMA; fp64 = 1:
+ * FP64 DFMA.  Every SM runs independent FMA chains for about 20 ms (CUDA events
+ * on `stream`, after a warm-up launch); *fma_per_s receives FMA lane operations
+ * per second (two flops each).  Synchronous.  Allocates and frees a 256-byte
+ * device buffer.  Errors: DD_EINVAL (bad fp64, null output), DD_ENOMEM,
+ * DD_ECUDA. */
+DD_API dd_status_t dd_probe_fma_rate(int32_t fp64, double* fma_per_s, void* stream);
 
 /* Static text for a status code. */
 DD_API const char* dd_status_string(dd_status_t status);

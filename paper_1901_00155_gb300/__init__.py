@@ -241,6 +241,20 @@ class Plan:
                 "word_start": t(v.word_start, (D,), "<i4"), "ncand": t(v.ncand, (1,), "<i4"),
                 "t32": t(v.t32, (m,), "<f4")}
 
+    def bound_terms(self, like) -> dict:
+        """Per-row terms of the Gram form's error bound F_i(D) = alpha_i + beta D + gam_i
+        sqrt(max(D, 0) + q2_i) (dd_plan_bound_view), filled by the plan's last call: zero-copy
+        CUDA views on the device of the tensor ``like``, plus beta."""
+        torch = _torch()
+        v = _lib.BoundView()
+        _check(self._lib.dd_plan_bound_view(self._ptr, ctypes.byref(v)), "dd_plan_bound_view")
+        N = int(v.N)
+
+        def t(ptr):
+            return torch.as_tensor(_DevArray(ptr, (N,), "<f4"), device=like.device)
+
+        return {"alpha": t(v.alpha), "gam": t(v.gam), "q2": t(v.q2), "beta": float(v.beta)}
+
     def last_launches(self) -> int:
         return int(self._lib.dd_plan_last_launches(self._ptr))
 
@@ -283,21 +297,44 @@ class Plan:
                  "items": int(w.items), "pairs": int(w.pairs), "ms": float(w.ms)} for w in buf[:min(nw, cap)]]
 
 
+def probe_fma_rate(fp64: bool = False, stream=None) -> float:
+    """Measured FMA lane operations per second of this device's CUDA cores, FP32 (default) or
+    FP64 (dd_probe_fma_rate): a roofline denominator for the kernels off the tensor cores."""
+    r = ctypes.c_double()
+    _check(_lib.load().dd_probe_fma_rate(1 if fp64 else 0, ctypes.byref(r), _stream_ptr(stream)),
+           "dd_probe_fma_rate")
+    return float(r.value)
+
+
 def find_discord(T, n: int, precision="fp32", stream=None, **opts) -> DiscordResult:
     """One-shot search (creates and destroys a plan)."""
     with Plan(T.numel(), n, precision, **opts) as p:
         return p.find_discord(T, stream)
 
 
-def group_by_tuned_options(ms, ns, table, precision="fp32", **opts):
+# option values under which a tuning table applies: the tuner times globally normalised,
+# unsharded searches only
+_TUNED_ONLY = {"znorm": ("global",), "shard_count": (0, 1)}
+
+
+def group_by_tuned_options(ms, ns, table, precision=None, **opts):
     """Split a batch by the options a tuning table (see tuning.py) gives each (m, n): returns
-    [(options dict, [positions in the batch])], in first-appearance order.  Series without an
-    entry keep (precision, opts)."""
+    [(options dict, [positions in the batch])], in first-appearance order.
+
+    Options passed explicitly (``precision`` when not None, and every keyword) win over the
+    table's; the table fills in only the rest.  Per-window (znorm="window") or sharded searches
+    ignore the table, which was tuned on neither.  Series without an entry run with the explicit
+    options, precision "fp32" unless one was given."""
     from . import tuning
 
+    explicit = dict(opts)
+    if precision is not None:
+        explicit["precision"] = precision
+    use_table = all(explicit.get(k, ok[0]) in ok for k, ok in _TUNED_ONLY.items())
     groups, where = [], {}
     for pos, (m, n) in enumerate(zip(ms, ns)):
-        o = {"precision": precision, **opts, **tuning.lookup(table, int(m), int(n))}
+        tuned = tuning.lookup(table, int(m), int(n)) if use_table else {}
+        o = {"precision": "fp32", **tuned, **explicit}
         key = tuple(sorted(o.items()))
         if key not in where:
             where[key] = len(groups)
@@ -306,10 +343,11 @@ def group_by_tuned_options(ms, ns, table, precision="fp32", **opts):
     return groups
 
 
-def find_discord_batched(series, ns, precision="fp32", stream=None, table=None, **opts):
+def find_discord_batched(series, ns, precision=None, stream=None, table=None, **opts):
     """Independent searches over CUDA float32 tensors of possibly different lengths.  With a
-    tuning table, each series runs with the options tuned for its (n, m bucket): one batched call
-    per distinct option set, results in the input order."""
+    tuning table, each series runs with the options tuned for its (n, m bucket), explicit options
+    taking precedence: one batched call per distinct option set, results in the input order.
+    ``precision`` defaults to "fp32" (with a table: to the tuned form)."""
     if table is not None:
         results = [None] * len(series)
         for o, pos in group_by_tuned_options([s.numel() for s in series], ns, table, precision, **opts):
@@ -318,6 +356,8 @@ def find_discord_batched(series, ns, precision="fp32", stream=None, table=None, 
             for i, r in zip(pos, part):
                 results[i] = r
         return results
+    if precision is None:
+        precision = "fp32"
     lib = _lib.load()
     k = len(series)
     ptrs = (ctypes.c_void_p * k)(*[ctypes.c_void_p(s.data_ptr()) for s in series])

@@ -36,6 +36,11 @@ class View(ctypes.Structure):
                 ("ncand", ctypes.c_void_p), ("t32", ctypes.c_void_p)]
 
 
+class BoundView(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int64), ("precision", ctypes.c_int32), ("beta", ctypes.c_float),
+                ("alpha", ctypes.c_void_p), ("gam", ctypes.c_void_p), ("q2", ctypes.c_void_p)]
+
+
 class Profile(ctypes.Structure):
     _fields_ = [("dist_launches", ctypes.c_int32), ("precision", ctypes.c_int32), ("dist_ms", ctypes.c_double),
                 ("computed_pairs", ctypes.c_int64), ("call_ms", ctypes.c_double), ("reserved", ctypes.c_int64 * 4)]
@@ -82,8 +87,10 @@ SIGNATURES = {
                     ctypes.c_void_p], ctypes.c_int),
     "dd_prep": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
     "dd_plan_view": ([ctypes.c_void_p, ctypes.POINTER(View)], ctypes.c_int),
+    "dd_plan_bound_view": ([ctypes.c_void_p, ctypes.POINTER(BoundView)], ctypes.c_int),
     "dd_plan_last_launches": ([ctypes.c_void_p], ctypes.c_int64),
     "dd_status_string": ([ctypes.c_int], ctypes.c_char_p),
+    "dd_probe_fma_rate": ([ctypes.c_int32, ctypes.POINTER(ctypes.c_double), ctypes.c_void_p], ctypes.c_int),
     "dd_plan_set_profiling": ([ctypes.c_void_p, ctypes.c_int32], ctypes.c_int),
     "dd_plan_get_profile": ([ctypes.c_void_p, ctypes.POINTER(Profile)], ctypes.c_int),
     "dd_plan_set_graph": ([ctypes.c_void_p, ctypes.c_int32], ctypes.c_int),

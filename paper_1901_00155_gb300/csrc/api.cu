@@ -640,6 +640,18 @@ dd_status_t dd_plan_view(dd_plan_t p, dd_view_t* v) {
     return DD_OK;
 }
 
+dd_status_t dd_plan_bound_view(dd_plan_t p, dd_bound_view_t* v) {
+    if (!p || !v) return DD_EINVAL;
+    if (p->opt.precision == DD_FP32 || !p->alpha) return DD_ENOTSUP;
+    v->N = p->N;
+    v->precision = p->opt.precision;
+    v->beta = dd::kTcBeta;
+    v->alpha = p->alpha;
+    v->gam = p->gam;
+    v->q2 = p->q2;
+    return DD_OK;
+}
+
 int64_t dd_plan_last_launches(dd_plan_t p) {
     if (!p) return -1;
     // a graph replay skips the kernels of conditional bodies whose gate did not pass

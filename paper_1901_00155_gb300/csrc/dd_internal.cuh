@@ -27,6 +27,10 @@ constexpr int kMaxListSlots = 256;       // list counts per search
 constexpr int kMaxWaves = 64;            // distance waves traced per call
 constexpr int kDgPad = 2048 + 64;        // padding entries after the diagonal-recurrence data (>= one CTA's diagonals)
 
+// Relative term beta of the Gram form's per-row bound F_i(D): 2 x 6 u32 (u32 = 2^-24,
+// safety factor 2) for the FP32 rounding of the epilogue's sum D.
+constexpr float kTcBeta = 12.0f * 5.9604644775390625e-08f;
+
 // FP32 direct-difference tile kernel
 constexpr int kF32BM = 128;  // rows per tile
 constexpr int kF32BN = 128;  // columns per tile

@@ -207,6 +207,9 @@ extern "C" dd_status_t dd_nn_profile_static(const float* T_dev, int64_t m, int32
     }
     StaticScratch* s = static_cast<StaticScratch*>(addr);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    // An error left pending by earlier work on this thread is the caller's: report it without
+    // launching and leave it pending, so that the launch check below sees only this call's errors.
+    if (cudaPeekAtLastError() != cudaSuccess) return DD_ECUDA;
     k_s_sum<<<kStaticParts, 256, 0, st>>>(T_dev, m, s);
     k_s_mu<<<1, kStaticParts, 0, st>>>(m, s);
     k_s_var<<<kStaticParts, 256, 0, st>>>(T_dev, m, s);

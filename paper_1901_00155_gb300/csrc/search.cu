@@ -468,7 +468,7 @@ struct Seq {
             tb.alpha = p->alpha;
             tb.gam = p->gam;
             tb.q2 = p->q2;
-            tb.beta = 12.0f * 5.9604644775390625e-08f;  // 2 x 6 u32 (safety factor 2)
+            tb.beta = kTcBeta;
             tb.on = 1;
             tb.r32 = p->rmin32;
         }

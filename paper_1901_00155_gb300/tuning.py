@@ -4,9 +4,12 @@ A search's options (arithmetic form, first-wave width, number of top rows fully 
 change only how fast it reaches the discord, never which discord it returns (Algorithms 2-4 always
 finish with exact distances of every row that can still win).  The tuner times every candidate
 option set on a seeded synthetic series of each requested shape and keeps the fastest.  It also
-checks that all candidates return the same discord (same index, or distances equal to 1e-4
-relative where the arithmetic forms differ); a disagreement is a bug, not a tuning result, and
-raises.
+checks that all candidates return the same discord (the same index and distance within 1e-4
+relative for candidates of one arithmetic form; across forms, distances within 1e-4 relative, a
+different index then being a tie); a disagreement is a bug, not a tuning result, and raises.
+
+Entries are tuned on globally normalised, unsharded searches only, so a batch applies them only to
+such searches, and options the caller passes explicitly always win over an entry.
 
 Shapes are bucketed by m to the next power of two (2^11 .. 2^31), so one tuned entry serves every
 series of that length class with the same n.  Tables are plain JSON.
@@ -56,8 +59,13 @@ class Trial:
 
 
 def _agree(a: Trial, b: Trial, rtol: float) -> bool:
-    """Same discord: the distances agree (a different index is then a tie of the distances)."""
-    return math.isclose(a.nn_distance, b.nn_distance, rel_tol=rtol, abs_tol=1e-9)
+    """Same discord.  Two option sets of the same arithmetic form take the same decisions, so they
+    must return the same index and distances within rtol.  Across forms (FP32 vs a tensor-core
+    form) a different index is accepted only as a tie: the distances agree within rtol."""
+    same_dist = math.isclose(a.nn_distance, b.nn_distance, rel_tol=rtol, abs_tol=1e-9)
+    if a.options.get("precision", "fp32") == b.options.get("precision", "fp32"):
+        return a.index == b.index and same_dist
+    return same_dist
 
 
 def time_search(options: dict, T, n: int, reps: int = 3, warmup: int = 2):

@@ -60,28 +60,6 @@ def test_small_workload_exact():
     assert r.nn_distance == pytest.approx(math.sqrt(d2_ref), rel=RTOL)
 
 
-@pytest.mark.parametrize("spec", synth.workloads_medium(), ids=lambda s: s.name())
-def test_medium_workloads_vs_hotsax(spec):
-    T, _ = synth.make_series(spec)
-    r = _search(T, spec.n)
-    i_ref, d2_ref, _ = oracle.hotsax(T, spec.n)
-    _check_against(T, spec.n, r, i_ref, d2_ref)
-
-
-def test_large_workload_sampled():
-    """m = 2^20, n = 256: the GPU's discord distance equals the oracle's
-    brute-force distance of that row, and no sampled row has a larger one."""
-    spec = synth.workload_large(0)
-    T, _ = synth.make_series(spec)
-    r = _search(T, spec.n)
-    nn, _ = oracle.nn_rows(T, spec.n, [r.index])
-    assert r.nn_distance == pytest.approx(math.sqrt(nn[0]), rel=RTOL)
-    rng = np.random.default_rng(1)
-    rows = rng.integers(0, T.size - spec.n + 1, size=24)
-    nns, _ = oracle.nn_rows(T, spec.n, rows)
-    assert np.all(np.sqrt(nns) <= r.nn_distance * (1 + RTOL))
-
-
 @pytest.mark.parametrize("n,m", [(16, 3000), (64, 64 * 3 - 1), (128, 128 * 3 + 77), (1, 50)])
 def test_profile_matches_oracle(n, m):
     dd = _dd()
@@ -248,6 +226,29 @@ def test_top_k_discords(precision):
             if precision != "fp32":
                 assert g.index == i
         assert again.index == ref[0][0]
+
+
+@pytest.mark.parametrize("precision", ["fp32", "tc_fp16", "tc_bf16"])
+def test_top_k_hand_examples(precision):
+    """dd_find_discords on the hand-worked top-k examples of tests/golden/topk_examples.txt."""
+    import os
+    dd = _dd()
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "topk_examples.txt")
+    cases = []
+    with open(path) as f:
+        for line in f:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                T, n, k, picks, _ = [x.strip() for x in line.split("|")]
+                cases.append((np.array([float(v) for v in T.split(",")], dtype=np.float32), int(n), int(k),
+                              [(int(a), float(b)) for a, b in (p.split(":") for p in picks.split(","))]))
+    assert len(cases) == 2
+    for T, n, k, want in cases:
+        with dd.Plan(T.size, n, precision) as p:
+            got = p.find_discords(torch.from_numpy(T).cuda(), k)
+        assert [g.index for g in got] == [w[0] for w in want], (precision, got, want)
+        for g, (_, d) in zip(got, want):
+            assert g.nn_distance == pytest.approx(d, rel=RTOL if precision == "fp32" else 1e-6, abs=1e-6)
 
 
 def test_launch_count_excludes_skipped_conditional_waves():

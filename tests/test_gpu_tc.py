@@ -63,26 +63,6 @@ def test_small_workload(prec):
     _check(T, spec.n, r, i_ref, d2_ref)
 
 
-@pytest.mark.parametrize("spec", synth.workloads_medium(), ids=lambda s: s.name())
-def test_medium_workloads_vs_hotsax(spec):
-    T, _ = synth.make_series(spec)
-    r = _search(T, spec.n, "tc_fp16")
-    i_ref, d2_ref, _ = oracle.hotsax(T, spec.n)
-    _check(T, spec.n, r, i_ref, d2_ref)
-
-
-def test_large_workload_sampled():
-    spec = synth.workload_large(0)
-    T, _ = synth.make_series(spec)
-    r = _search(T, spec.n, "tc_fp16")
-    nn, _ = oracle.nn_rows(T, spec.n, [r.index])
-    assert r.nn_distance == pytest.approx(math.sqrt(nn[0]), rel=RTOL)
-    rng = np.random.default_rng(2)
-    rows = rng.integers(0, T.size - spec.n + 1, size=24)
-    nns, _ = oracle.nn_rows(T, spec.n, rows)
-    assert np.all(np.sqrt(nns) <= r.nn_distance * (1 + RTOL))
-
-
 @pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("n,m", [(16, 3000), (64, 64 * 3 - 1), (128, 128 * 3 + 77), (200, 5000)])
 def test_profile_within_bound(prec, n, m):
@@ -125,12 +105,13 @@ def test_edge_cases(prec):
     _check(T, 6, r, i_ref, d2_ref)
 
 
+@pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("n,m", [(700, 2200), (1000, 5000), (1024, 3100)])
-def test_long_subsequences(n, m):
+def test_long_subsequences(n, m, prec):
     """k = n spans many 64-element operand chunks (and ragged tails)."""
     rng = np.random.default_rng(n)
     T = np.cumsum(rng.standard_normal(m)).astype(np.float32)
-    r = _search(T, n, "tc_fp16")
+    r = _search(T, n, prec)
     i_ref, d2_ref = oracle.discord_brute(T, n)
     _check(T, n, r, i_ref, d2_ref)
 

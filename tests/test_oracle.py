@@ -343,6 +343,34 @@ def test_znorm_closed_form():
     assert s0 == 0.0 and np.all(t0 == 0.0)
 
 
+def _topk_examples():
+    out = []
+    with open(os.path.join(GOLDEN, "topk_examples.txt")) as f:
+        for line in f:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            T, n, k, picks, var = [x.strip() for x in line.split("|")]
+            want = [(int(a), float(b)) for a, b in (p.split(":") for p in picks.split(","))]
+            out.append((np.array([float(v) for v in T.split(",")], dtype=np.float32), int(n), int(k), want,
+                        float(var)))
+    return out
+
+
+@pytest.mark.parametrize("case", _topk_examples(), ids=lambda c: f"m{c[0].size}_n{c[1]}")
+def test_discords_brute_hand_examples(case):
+    """Top-k pinned to hand-worked values: an overlapping row with the second-largest nn is
+    skipped, a row exactly n away stays allowed, and nearest neighbours keep the earlier
+    discords as candidates."""
+    T, n, k, want, var = case
+    got = oracle.discords_brute(T, n, k)
+    assert [g[0] for g in got] == [w[0] for w in want]
+    for (_, d2), (_, d) in zip(got, want):
+        assert math.sqrt(d2) == pytest.approx(d, rel=1e-14, abs=1e-15)
+    _, _, sg = oracle.znorm(T)
+    assert sg * sg == pytest.approx(var, rel=1e-14)
+
+
 def test_discords_brute_definition():
     """Top-k discords: the first is the discord; every later one is the largest nn among the
     subsequences at least n from all earlier ones (rechecked by a plain loop); distances do not

@@ -68,8 +68,8 @@ def test_unsupported_forms_are_skipped_and_all_unsupported_raises():
 
 def test_disagreeing_candidates_raise_and_ties_pass():
     times = {k: 1.0 for k in [("tc_fp16", 64), ("tc_fp16", 128), ("fp32", 64), ("fp32", 128)]}
-    # a different index with an equal distance (a tie) is accepted
-    timer, _ = _fake(times, {("fp32", 64): (9, 2.5 * (1 + 1e-6))})
+    # a different index with an equal distance is accepted across forms (a tie)
+    timer, _ = _fake(times, {("fp32", 64): (9, 2.5 * (1 + 1e-6)), ("fp32", 128): (9, 2.5)})
     tuning.tune([(4096, 8)], CANDS, timer=timer, series=lambda m, n, s: None, unsupported=Unsupported)
     # a different distance is a bug
     timer, _ = _fake(times, {("fp32", 128): (7, 2.6)})
@@ -116,9 +116,50 @@ def test_batch_groups_follow_the_table():
         "n128/m65536": {"options": {"precision": "fp32", "local_cols": 256, "refine_k": 128}}}}
     ms = [3000, 50000, 4000, 9000, 60000]
     ns = [64, 128, 64, 64, 128]
-    groups = dd.group_by_tuned_options(ms, ns, table, "fp32", word_cols=256)
+    groups = dd.group_by_tuned_options(ms, ns, table, word_cols=256)
     assert [g[1] for g in groups] == [[0, 2], [1, 4], [3]]
     assert groups[0][0] == {"precision": "tc_fp16", "local_cols": 64, "refine_k": 64, "word_cols": 256}
     assert groups[1][0] == {"precision": "fp32", "local_cols": 256, "refine_k": 128, "word_cols": 256}
     assert groups[2][0] == {"precision": "fp32", "word_cols": 256}  # m=9000 has no entry
-    assert dd.group_by_tuned_options(ms, ns, {}, "fp32") == [({"precision": "fp32"}, [0, 1, 2, 3, 4])]
+    assert dd.group_by_tuned_options(ms, ns, {}) == [({"precision": "fp32"}, [0, 1, 2, 3, 4])]
+    assert dd.group_by_tuned_options(ms, ns, {}, "tc_bf16") == [({"precision": "tc_bf16"}, [0, 1, 2, 3, 4])]
+
+
+def test_explicit_options_win_over_the_table():
+    """A caller who names a precision (or any option) keeps it, whatever the table holds."""
+    import paper_1901_00155_gb300 as dd
+    table = {"version": tuning.TABLE_VERSION, "entries": {
+        "n64/m4096": {"options": {"precision": "tc_fp16", "local_cols": 64, "refine_k": 64}}}}
+    groups = dd.group_by_tuned_options([3000, 4000], [64, 64], table, "fp32", refine_k=32)
+    assert groups == [({"precision": "fp32", "local_cols": 64, "refine_k": 32}, [0, 1])]
+    groups = dd.group_by_tuned_options([3000], [64], table, "tc_bf16")
+    assert groups[0][0]["precision"] == "tc_bf16"
+
+
+def test_table_is_ignored_for_per_window_and_sharded_searches():
+    """The tuner times globally normalised, unsharded searches only: a tensor-core entry must not
+    reach a per-window search (which takes FP32 only) nor a shard of a search."""
+    import paper_1901_00155_gb300 as dd
+    table = {"version": tuning.TABLE_VERSION, "entries": {
+        "n64/m4096": {"options": {"precision": "tc_fp16", "local_cols": 64, "refine_k": 64}}}}
+    groups = dd.group_by_tuned_options([3000, 4000], [64, 64], table, znorm="window")
+    assert groups == [({"precision": "fp32", "znorm": "window"}, [0, 1])]
+    dd._options(**groups[0][0])  # a valid per-window option set
+    groups = dd.group_by_tuned_options([3000], [64], table, shard_count=2, shard_index=1)
+    assert groups == [({"precision": "fp32", "shard_count": 2, "shard_index": 1}, [0])]
+    # the defaults (global, one shard) still use it
+    groups = dd.group_by_tuned_options([3000], [64], table, znorm="global", shard_count=1)
+    assert groups[0][0]["precision"] == "tc_fp16"
+
+
+def test_same_form_candidates_must_agree_on_the_index():
+    """Within one arithmetic form a different index is a bug even when the distances are close;
+    across forms it is accepted as a tie of equal distances."""
+    times = {k: 1.0 for k in [("tc_fp16", 64), ("tc_fp16", 128), ("fp32", 64), ("fp32", 128)]}
+    timer, _ = _fake(times, {("tc_fp16", 128): (9, 2.5)})  # same form as ("tc_fp16", 64): index 7
+    with pytest.raises(tuning.TuningError):
+        tuning.tune([(4096, 8)], CANDS, timer=timer, series=lambda m, n, s: None, unsupported=Unsupported)
+    a = tuning.Trial({"precision": "fp32"}, 1.0, 3, 2.0)
+    b = tuning.Trial({"precision": "tc_bf16"}, 1.0, 4, 2.0 * (1 + 1e-6))
+    assert tuning._agree(a, b, 1e-4)
+    assert not tuning._agree(a, tuning.Trial({"precision": "fp32"}, 1.0, 4, 2.0), 1e-4)

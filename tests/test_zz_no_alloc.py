@@ -5,7 +5,8 @@ device memory is already fully handed to another allocator, or an allocation
 would stall a latency-critical loop).  This entry point serves them from a
 fixed scratch array inside the library.  The test calls it through the C ABI
 twice in a row, on two different series, and checks each result against the
-plan-based dd_nn_profile within the FP32 form's tolerance.  It lives in its
+FP64 oracle's nearest-neighbour profile and against the plan-based
+dd_nn_profile, within the FP32 form's tolerance.  It lives in its
 own file, collected last, and passes both alone and after the other tests.
 """
 import ctypes
@@ -13,6 +14,7 @@ import ctypes
 import numpy as np
 import pytest
 
+import oracle
 from paper_1901_00155_gb300 import _lib
 
 torch = pytest.importorskip("torch")
@@ -44,6 +46,8 @@ def test_static_profile_matches_plan_profile_twice():
         torch.cuda.synchronize()
         got, want = out.cpu().numpy(), ref.cpu().numpy()
         np.testing.assert_allclose(got, want, rtol=RTOL, atol=1e-6 * max(1.0, float(want.max())))
+        exact = oracle.nn_profile(T, n)
+        np.testing.assert_allclose(got, exact, rtol=RTOL, atol=1e-5 * max(1.0, float(exact.max())))
 
 
 def test_static_profile_rejects_oversized_series():
