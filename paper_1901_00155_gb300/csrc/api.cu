@@ -94,8 +94,8 @@ size_t carve(dd_plan_s* p, char* base) {
     p->pos_of = c.take<int32_t>(N);
     p->rmin = c.take<uint32_t>(N);
     for (int k = 0; k < 4; k++) p->list[k] = c.take<int32_t>(N);
-    p->flag = c.take<uint8_t>(N);
-    p->blk = c.take<int32_t>(nblk + 1);
+    p->cstat_stride = nblk;
+    p->cstat = c.take<unsigned long long>((size_t)dd::kCompactSites * nblk);
     p->res_dev = c.take<dd_result_t>(1);
     p->excl = c.take<uint8_t>(N);
     p->seq_rows = c.take<int32_t>(N);

@@ -20,6 +20,7 @@ constexpr int kStatBlocks = 1024;        // partial-sum blocks of the Eq. 2 stat
 constexpr int kScanElems = 4096;         // elements per block of the FP64 prefix scan
 constexpr int kHistRows = 4096;          // rows per block of the word histogram / scatter
 constexpr int kCompactRows = 2048;       // list entries per block of the compaction
+constexpr int kCompactSites = 16;        // compactions per search (one look-back status array each)
 constexpr int kTopkBins = 4096;          // bins of the top-k radix select (float bits >> 19)
 constexpr int kMuBins = 4096;            // bins of the mean-bucketed row order
 constexpr int kMaxLaunchSlots = 512;     // work counters per search
@@ -66,6 +67,9 @@ struct Ctrl {
     unsigned long long wave_items[kMaxWaves];
     int wave_rows[kMaxWaves];
     int cond[8];                  // value each conditional graph node of the search took (1 = body ran)
+    int cticket[kCompactSites];   // block tickets of each compaction (blocks take their place in start order)
+    int stat_ticket[2];           // blocks done with the two passes of the Eq. 2 statistics
+    int resc_nch;                 // FP64 rescoring: column chunks of the longest candidate range
     int topk_bin;                 // top-k select: bin of the first pass holding the k-th row (-1: take all)
     int topk_need;                // rows still needed from that bin
     int topk_hist[kTopkBins];     // radix-select histogram, pass 1 (float bits >> 19)
@@ -255,8 +259,8 @@ struct dd_plan_s {
     uint32_t* rmin32 = nullptr;
     uint8_t* excl = nullptr;     // per row: 1 = excluded from being the discord (dd_find_discords)  // Gram form: FP32 upper bounds from the time-local wave (TcBound::r32)
     int32_t* list[4] = {nullptr, nullptr, nullptr, nullptr};
-    uint8_t* flag = nullptr;
-    int32_t* blk = nullptr;
+    unsigned long long* cstat = nullptr;  // [kCompactSites][nblk] look-back status words of the compactions
+    int cstat_stride = 0;                 // nblk = ceil(N / kCompactRows)
     dd_result_t* res_dev = nullptr;
     dd_result_t* res_host = nullptr;  // pinned
     int32_t* seq_rows = nullptr;      // 0..N-1

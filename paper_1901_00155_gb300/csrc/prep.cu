@@ -59,41 +59,53 @@ __device__ double block_max_d(double v, double* sh) {
 }
 
 // ---- Eq. 2, pass 1: per-block sums of T, min/max, finiteness ----------------
+// The extremes are taken in FP32 (exact: they are input values); the sum in
+// FP64.  The last block to finish reduces the partials in a fixed order:
+// mu = (1/m) sum t.
+__device__ bool last_block(int* ticket) {
+    __shared__ bool last;
+    __threadfence();  // this block's partials are visible before its ticket
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(ticket, 1) == (int)gridDim.x - 1;
+    __syncthreads();
+    return last;
+}
+
 __global__ void __launch_bounds__(256) k_stats_sum(const float* __restrict__ T, int64_t m, double* part,
-                                                   Ctrl* ctrl) {
+                                                   double* stats, Ctrl* ctrl) {
     __shared__ double sh[32];
-    double s = 0.0, mx = -INFINITY, mn = INFINITY;
+    double s = 0.0;
+    float mx = -INFINITY, mn = INFINITY;
     int bad = 0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
         float v = T[i];
         if (!isfinite(v)) bad = 1;
         s += (double)v;
-        mx = fmax(mx, (double)v);
-        mn = fmin(mn, (double)v);
+        mx = fmaxf(mx, v);
+        mn = fminf(mn, v);
     }
     if (__syncthreads_or(bad) && threadIdx.x == 0) atomicExch(&ctrl->nonfinite, 1);
     double bs = block_sum_d<256>(s, sh);
-    double bmx = block_max_d<256>(mx, sh);
-    double bmn = -block_max_d<256>(-mn, sh);
+    double bmx = block_max_d<256>((double)mx, sh);
+    double bmn = -block_max_d<256>(-(double)mn, sh);
     if (threadIdx.x == 0) {
         part[blockIdx.x] = bs;
         part[kStatBlocks + blockIdx.x] = bmx;
         part[2 * kStatBlocks + blockIdx.x] = bmn;
     }
-}
-
-// mu = (1/m) sum t ; fixed-order reduction over the block partials.
-__global__ void __launch_bounds__(256) k_stats_mu(const double* part, int nb, int64_t m, double* stats) {
-    __shared__ double sh[32];
-    double s = 0.0, mx = -INFINITY, mn = INFINITY;
+    if (!last_block(&ctrl->stat_ticket[0])) return;
+    const int nb = (int)gridDim.x;
+    const volatile double* vp = part;
+    s = 0.0;
+    double gmx = -INFINITY, gmn = INFINITY;
     for (int b = threadIdx.x; b < nb; b += blockDim.x) {
-        s += part[b];
-        mx = fmax(mx, part[kStatBlocks + b]);
-        mn = fmin(mn, part[2 * kStatBlocks + b]);
+        s += vp[b];
+        gmx = fmax(gmx, vp[kStatBlocks + b]);
+        gmn = fmin(gmn, vp[2 * kStatBlocks + b]);
     }
-    double bs = block_sum_d<256>(s, sh);
-    double bmx = block_max_d<256>(mx, sh);
-    double bmn = -block_max_d<256>(-mn, sh);
+    bs = block_sum_d<256>(s, sh);
+    bmx = block_max_d<256>(gmx, sh);
+    bmn = -block_max_d<256>(-gmn, sh);
     if (threadIdx.x == 0) {
         stats[0] = bs / (double)m;
         stats[4] = bmx;
@@ -102,8 +114,10 @@ __global__ void __launch_bounds__(256) k_stats_mu(const double* part, int nb, in
 }
 
 // ---- Eq. 2, pass 2: sum of squared deviations (two-pass variance) ------------
-__global__ void __launch_bounds__(256) k_stats_var(const float* __restrict__ T, int64_t m, const double* stats,
-                                                   double* part) {
+// The last block to finish reduces the partials in a fixed order: sigma, the
+// largest |t^|, and the geometry of the mean bins.
+__global__ void __launch_bounds__(256) k_stats_var(const float* __restrict__ T, int64_t m, double* stats,
+                                                   double* part, Ctrl* ctrl) {
     __shared__ double sh[32];
     const double mu = stats[0];
     double s = 0.0;
@@ -113,18 +127,15 @@ __global__ void __launch_bounds__(256) k_stats_var(const float* __restrict__ T, 
     }
     double bs = block_sum_d<256>(s, sh);
     if (threadIdx.x == 0) part[blockIdx.x] = bs;
-}
-
-__global__ void __launch_bounds__(256) k_stats_sigma(const double* part, int nb, int64_t m, double* stats,
-                                                     Ctrl* ctrl) {
-    __shared__ double sh[32];
-    double s = 0.0;
-    for (int b = threadIdx.x; b < nb; b += blockDim.x) s += part[b];
-    double bs = block_sum_d<256>(s, sh);
+    if (!last_block(&ctrl->stat_ticket[1])) return;
+    const int nb = (int)gridDim.x;
+    const volatile double* vp = part;
+    s = 0.0;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) s += vp[b];
+    bs = block_sum_d<256>(s, sh);
     if (threadIdx.x == 0) {
         double sigma = sqrt(bs / (double)m);
         stats[1] = sigma;
-        double mu = stats[0];
         // max |t^| over the series
         double a = fmax(fabs(stats[4] - mu), fabs(stats[5] - mu));
         stats[2] = sigma > 0.0 ? a / sigma : 0.0;
@@ -579,17 +590,15 @@ cudaError_t launch_prep_common(dd_plan_s* p, const float* T, cudaStream_t s) {
     int nb = (int)((m + 2047) / 2048);
     if (nb > kStatBlocks) nb = kStatBlocks;
     if (nb < 1) nb = 1;
-    k_stats_sum<<<nb, 256, 0, s>>>(T, m, p->part, p->ctrl);
-    k_stats_mu<<<1, 256, 0, s>>>(p->part, nb, m, p->stats);
-    k_stats_var<<<nb, 256, 0, s>>>(T, m, p->stats, p->part);
-    k_stats_sigma<<<1, 256, 0, s>>>(p->part, nb, m, p->stats, p->ctrl);
+    k_stats_sum<<<nb, 256, 0, s>>>(T, m, p->part, p->stats, p->ctrl);
+    k_stats_var<<<nb, 256, 0, s>>>(T, m, p->stats, p->part, p->ctrl);
     const int nscan = (int)((m + kScanElems - 1) / kScanElems);
     k_norm_blocks<<<nscan, 1024, 0, s>>>(T, m, p->stats, p->t64, p->t32, p->bsum, nscan);
     k_norm_scan_totals<<<1, 1024, 0, s>>>(p->bsum, nscan);
     k_norm_prefix<<<nscan, 1024, 0, s>>>(p->t64, m, p->bsum, nscan, p->P1, p->P2);
     const int gN = (int)((N + 255) / 256);
     k_window_stats<<<gN, 256, 0, s>>>(p->P1, p->P2, N, n, 1.0 / (double)n, p->mu_w, p->c_w);
-    p->launches += 8;
+    p->launches += 6;
     return cudaGetLastError();
 }
 

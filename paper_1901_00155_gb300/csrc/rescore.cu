@@ -18,7 +18,7 @@
 namespace dd {
 namespace {
 
-constexpr int kChunk = 512;
+constexpr int kChunk = 64;  // columns per work item: a candidate's range spreads over many blocks
 
 __device__ __forceinline__ void lb_range(float R, int i, int n, int N, const double* stats, const int32_t* mubin,
                                          const int32_t* binstart, int& L, int& H) {
@@ -41,8 +41,9 @@ __global__ void __launch_bounds__(256) k_rescore64(ListRef cand, TcBound bound, 
                                                    const int32_t* __restrict__ mubin,
                                                    const int32_t* __restrict__ binstart, const double* stats,
                                                    const double* __restrict__ t64, const float* __restrict__ t32,
-                                                   int n, int N, unsigned long long* __restrict__ ex64, Ctrl* ctrl,
-                                                   int slot) {
+                                                   int n, int N, const int32_t* __restrict__ rL,
+                                                   const int32_t* __restrict__ rH,
+                                                   unsigned long long* __restrict__ ex64, Ctrl* ctrl, int slot) {
     __shared__ int sh_item;
     __shared__ double red[8];
     if (ctrl->nonfinite || ctrl->degenerate) return;
@@ -52,7 +53,7 @@ __global__ void __launch_bounds__(256) k_rescore64(ListRef cand, TcBound bound, 
     const float maxabs = (float)stats[2];
     const int cnt = *cand.cnt_dev;
     const int off = cand.off_dev ? *cand.off_dev : 0;
-    const int nchunk = (N + kChunk - 1) / kChunk;
+    const int nchunk = ctrl->resc_nch;  // chunks of the longest candidate range
     const long long items = (long long)cnt * nchunk;
     for (;;) {
         __syncthreads();
@@ -67,8 +68,7 @@ __global__ void __launch_bounds__(256) k_rescore64(ListRef cand, TcBound bound, 
         const int r = item / nchunk, c = item % nchunk;
         const int i = cand.base[off + r];
         const float D = __uint_as_float(rmin[i]);
-        int L, H;
-        lb_range(row_ub(bound, i, D), i, n, N, stats, mubin, binstart, L, H);
+        const int L = rL[r], H = rH[r];
         const int a0 = L + c * kChunk;
         if (a0 >= H) continue;
         const int a1 = min(H, a0 + kChunk);
@@ -178,6 +178,30 @@ __global__ void k_init_best(Ctrl* ctrl) {
     if (threadIdx.x == 0) ctrl->best_idx = 0x7fffffff;
 }
 
+// Per candidate: its exact value starts at +inf, and its column range [L, H) of
+// the mean order (the lower-bound range of its upper bound) is stored; the
+// largest number of kChunk-column chunks of any range sizes the work items.
+__global__ void k_init_rescore(ListRef cand, TcBound bound, const uint32_t* __restrict__ rmin,
+                               const int32_t* __restrict__ mubin, const int32_t* __restrict__ binstart,
+                               const double* stats, int n, int N, unsigned long long* __restrict__ ex64,
+                               int32_t* __restrict__ rL, int32_t* __restrict__ rH, Ctrl* ctrl) {
+    const int cnt = *cand.cnt_dev;
+    const int off = cand.off_dev ? *cand.off_dev : 0;
+    if (blockIdx.x == 0 && threadIdx.x == 0) ctrl->best_idx = 0x7fffffff;
+    int nch = 0;
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < cnt; r += gridDim.x * blockDim.x) {
+        const int i = cand.base[off + r];
+        int L, H;
+        lb_range(row_ub(bound, i, __uint_as_float(rmin[i])), i, n, N, stats, mubin, binstart, L, H);
+        rL[r] = L;
+        rH[r] = H;
+        ex64[r] = 0x7ff0000000000000ull;
+        nch = max(nch, (H - L + kChunk - 1) / kChunk);
+    }
+    nch = __reduce_max_sync(0xffffffffu, nch);
+    if ((threadIdx.x & 31) == 0 && nch > 0) atomicMax(&ctrl->resc_nch, nch);
+}
+
 }  // namespace
 
 cudaError_t launch_best(dd_plan_s* p, ListRef cand, dd_result_t* out_dev, cudaStream_t s) {
@@ -192,12 +216,13 @@ cudaError_t launch_best(dd_plan_s* p, ListRef cand, dd_result_t* out_dev, cudaSt
 
 cudaError_t launch_rescore(dd_plan_s* p, ListRef cand, TcBound bound, int work_slot, dd_result_t* out_dev,
                            cudaStream_t s) {
-    cudaError_t e = cudaMemsetAsync(p->ex64, 0x7f, sizeof(double) * p->N, s);
-    if (e != cudaSuccess) return e;
-    k_init_best<<<1, 32, 0, s>>>(p->ctrl);
+    // the column ranges of the candidates live in two row lists that are free by now
+    k_init_rescore<<<p->sm_count, 256, 0, s>>>(cand, bound, p->rmin, p->mubin, p->binstart, p->stats, p->n,
+                                               (int)p->N, reinterpret_cast<unsigned long long*>(p->ex64), p->list[0],
+                                               p->list[1], p->ctrl);
     k_rescore64<<<2 * p->sm_count, 256, 0, s>>>(cand, bound, p->rmin, p->sig, p->mubin, p->binstart, p->stats, p->t64,
-                                                 p->t32, p->n, (int)p->N, reinterpret_cast<unsigned long long*>(p->ex64),
-                                                 p->ctrl, work_slot);
+                                                 p->t32, p->n, (int)p->N, p->list[0], p->list[1],
+                                                 reinterpret_cast<unsigned long long*>(p->ex64), p->ctrl, work_slot);
     k_best64<<<p->sm_count, 256, 0, s>>>(cand, reinterpret_cast<const unsigned long long*>(p->ex64), p->ctrl);
     k_pick64<<<p->sm_count, 256, 0, s>>>(cand, reinterpret_cast<const unsigned long long*>(p->ex64), p->ctrl);
     k_finalize_tc<<<1, 32, 0, s>>>(p->ctrl, out_dev);

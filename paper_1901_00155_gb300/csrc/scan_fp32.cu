@@ -17,7 +17,8 @@
 // minima.
 //
 // Tile arithmetic: 256 threads, each an 8x8 register micro-tile of
-// (row, column) pairs; k is staged through shared memory in chunks of 32 with
+// (row, column) pairs in packed FP32 pairs (one f32x2 subtract and one f32x2
+// FMA per two pairs and k); k is staged through shared memory in chunks of 32 with
 // cp.async double buffering; rows and columns are gathered by index, each
 // being n consecutive values of the normalised series t^ (FP32).
 #include "dd_internal.cuh"
@@ -72,6 +73,29 @@ __device__ __forceinline__ void stage_chunk(F32Smem& sm, int buf, const float* _
         cp_async4(&sm.b[buf][lane][c], ok ? (const void*)(t32 + cj + k) : (const void*)t32, ok);
     }
 }
+
+// Packed FP32 pairs (sm_100+ f32x2 arithmetic): every lane of a pair is rounded
+// exactly as the scalar instruction would round it, so a pair's distance is the
+// same sum of the same terms in the same k order; one instruction does two.
+typedef unsigned long long f2_t;
+__device__ __forceinline__ f2_t f2_dup(float x) {
+    f2_t r;
+    asm("mov.b64 %0, {%1, %1};" : "=l"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ f2_t f2_sub(f2_t a, f2_t b) {
+    f2_t r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+// c + d * d, lane by lane
+__device__ __forceinline__ f2_t f2_fma_sq(f2_t d, f2_t c) {
+    f2_t r;
+    asm("fma.rn.f32x2 %0, %1, %1, %2;" : "=l"(r) : "l"(d), "l"(c));
+    return r;
+}
+__device__ __forceinline__ float f2_lo(f2_t v) { return __uint_as_float((unsigned)(v & 0xffffffffull)); }
+__device__ __forceinline__ float f2_hi(f2_t v) { return __uint_as_float((unsigned)(v >> 32)); }
 
 // Rigorous upper bound on the exact squared distance d^2 (FP64 series) of a
 // pair whose FP32 value is e: inputs rounded to FP32 (|t^| <= M), FP32
@@ -240,11 +264,12 @@ __global__ void __launch_bounds__(NT, 2) k_scan_fp32(ScanArgs a) {
                 nrun++;
             }
 
-            float acc[8][8];
+            // acc2[i][q] holds columns 2q, 2q + 1 of row i
+            f2_t acc2[8][4];
 #pragma unroll
             for (int i = 0; i < 8; i++)
 #pragma unroll
-                for (int j = 0; j < 8; j++) acc[i][j] = 0.f;
+                for (int q = 0; q < 4; q++) acc2[i][q] = 0ull;
 
             stage_chunk(sm, 0, a.t32, 0, n);
             cp_async_commit();
@@ -262,17 +287,16 @@ __global__ void __launch_bounds__(NT, 2) k_scan_fp32(ScanArgs a) {
                 for (int kk = 0; kk < BK; kk++) {
                     const float4 a0 = *reinterpret_cast<const float4*>(&sm.a[buf][kk][ty * 4]);
                     const float4 a1 = *reinterpret_cast<const float4*>(&sm.a[buf][kk][64 + ty * 4]);
-                    const float4 b0 = *reinterpret_cast<const float4*>(&sm.b[buf][kk][tx * 4]);
-                    const float4 b1 = *reinterpret_cast<const float4*>(&sm.b[buf][kk][64 + tx * 4]);
+                    const ulonglong2 b0 = *reinterpret_cast<const ulonglong2*>(&sm.b[buf][kk][tx * 4]);
+                    const ulonglong2 b1 = *reinterpret_cast<const ulonglong2*>(&sm.b[buf][kk][64 + tx * 4]);
                     const float x[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-                    const float y[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+                    const f2_t y2[4] = {b0.x, b0.y, b1.x, b1.y};
 #pragma unroll
-                    for (int i = 0; i < 8; i++)
+                    for (int i = 0; i < 8; i++) {
+                        const f2_t xx = f2_dup(x[i]);
 #pragma unroll
-                        for (int j = 0; j < 8; j++) {
-                            const float d = x[i] - y[j];
-                            acc[i][j] = fmaf(d, d, acc[i][j]);
-                        }
+                        for (int q = 0; q < 4; q++) acc2[i][q] = f2_fma_sq(f2_sub(xx, y2[q]), acc2[i][q]);
+                    }
                 }
                 __syncthreads();
             }
@@ -289,7 +313,8 @@ __global__ void __launch_bounds__(NT, 2) k_scan_fp32(ScanArgs a) {
                 for (int j = 0; j < 8; j++) {
                     const int d = ri - cjr[j];
                     const bool ok = cjr[j] >= 0 && (d >= n || d <= -n);
-                    mn = ok ? fminf(mn, acc[i][j]) : mn;
+                    const float v = (j & 1) ? f2_hi(acc2[i][j >> 1]) : f2_lo(acc2[i][j >> 1]);
+                    mn = ok ? fminf(mn, v) : mn;
                 }
                 mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, 1));
                 mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, 2));

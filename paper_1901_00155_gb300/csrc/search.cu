@@ -20,6 +20,13 @@ namespace {
 
 __global__ void k_set_int(int* p, int v) { *p = v; }
 
+// Count of the Cand list: the word order (Eq. 10) puts the words of smallest
+// frequency first, so Cand (Eq. 7) is order[0 .. ncand); it runs in phase 1
+// only when it has at most phase1_max rows.
+__global__ void k_cand_count(const Ctrl* ctrl, int phase1_max, int* cnt) {
+    *cnt = ctrl->ncand <= phase1_max ? ctrl->ncand : 0;
+}
+
 // The value rows are ranked by for the top-k waves: the running minimum, or in
 // the Gram form the smaller of it and the row's FP32 upper bound (non-negative
 // floats order like their bit patterns).
@@ -43,96 +50,131 @@ __device__ __forceinline__ bool is_alive(const TcBound& b, int i, uint32_t rbits
     return !(D + (b.alpha[i] + b.beta * D + b.gam[i] * sqrtf(fmaxf(D, 0.f) + b.q2[i])) < B);
 }
 
-// Compaction pass 1: predicate per list entry + per-block counts.
-// pred 0: alive against the best-so-far; pred 1: alive and rmin >= top-k
-// threshold; pred 2: member of Cand; pred 3: alive with no finite upper bound
-// yet (the running minimum still holds its initial value).  With sigpos set,
-// rows outside positions [p_lo, p_hi) of the mean order are dropped too.
-__global__ void __launch_bounds__(256) k_compact_flags(ListRef in, const uint32_t* __restrict__ rmin, TcBound tb,
-                                                       const Ctrl* ctrl, int pred, const int32_t* __restrict__ code,
-                                                       const int32_t* __restrict__ hist, int phase1_max,
-                                                       const int32_t* __restrict__ sigpos, int p_lo, int p_hi,
-                                                       uint8_t* __restrict__ flag, int* __restrict__ blk) {
-    __shared__ int sh;
-    if (threadIdx.x == 0) sh = 0;
-    __syncthreads();
+// Order-preserving compaction of a row list in one pass (decoupled look-back).
+// Predicates: pred 0: alive against the best-so-far; pred 1: alive and rank
+// value >= the top-k threshold; pred 2: member of Cand; pred 3: alive with no
+// finite upper bound yet (the running minimum still holds its initial value).
+// With sigpos set, rows outside positions [p_lo, p_hi) of the mean order are
+// dropped too.
+//
+// Block b (a ticket taken at start, so every lower block has started) keeps
+// entries [2048 b, 2048 b + 2048) in 8 coalesced rounds of 256 (thread t holds
+// entry 256 q + t of round q); ranks come from warp ballots.  Warp 0 publishes
+// the block's count, then looks back over the status words of the blocks
+// before it, 32 at a time, adding counts up to the nearest one that holds an
+// inclusive prefix, and publishes its own inclusive prefix; the block then
+// scatters its entries from there.  A status word is (flag << 62) | count:
+// flag 1 = the block's own count, 2 = the inclusive prefix.  The block holding
+// the last entry writes the total.  A wait on a predecessor is bounded by
+// %globaltimer (2 s): on expiry the search records DD_ETIMEOUT.  Status words
+// and tickets are zeroed per search.
+constexpr unsigned long long kStAgg = 1ull << 62, kStPre = 2ull << 62;
+
+__device__ __forceinline__ unsigned long long gtimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__global__ void __launch_bounds__(256) k_compact(ListRef in, const uint32_t* __restrict__ rmin, TcBound tb,
+                                                 Ctrl* ctrl, int pred, const int32_t* __restrict__ code,
+                                                 const int32_t* __restrict__ hist, int phase1_max,
+                                                 const int32_t* __restrict__ sigpos, int p_lo, int p_hi, int site,
+                                                 unsigned long long* __restrict__ status, int32_t* __restrict__ out,
+                                                 int* __restrict__ cnt_out) {
+    __shared__ int sh_b, sh_base;
+    __shared__ int wcnt[8][8];  // [round][warp]
     const int cnt = *in.cnt_dev;
+    if (threadIdx.x == 0) sh_b = atomicAdd(&ctrl->cticket[site], 1);
+    __syncthreads();
+    const int b = sh_b;
+    const int nb = cnt > 0 ? (cnt + kCompactRows - 1) / kCompactRows : 1;  // blocks that hold entries
+    if (b >= nb) return;  // no entries here, and no block waits on a later one
     const int off = in.off_dev ? *in.off_dev : 0;
     const uint32_t bsf = ctrl->bsf;
     const uint32_t thr = pred == 1 ? ctrl->topk_thr : (pred == 3 ? 0x7f000000u : 0u);
-    int local = 0;
-    // coalesced: entry q * 256 + t of the block's 2048 (the scatter pass reads the flags its own way)
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    int i8[8];
+    unsigned bal[8];
 #pragma unroll
     for (int q = 0; q < 8; q++) {
-        const int r = blockIdx.x * kCompactRows + q * 256 + threadIdx.x;
+        const int r = b * kCompactRows + q * 256 + threadIdx.x;
+        bool k = false;
+        i8[q] = -1;
         if (r < cnt) {
             const int i = in.base[off + r];
-            bool keep;
             if (pred == 2) {
                 // Cand (Eq. 7): rows whose word has the smallest frequency
-                keep = hist[code[i]] == ctrl->fmin && ctrl->ncand <= phase1_max;
+                k = hist[code[i]] == ctrl->fmin && ctrl->ncand <= phase1_max;
             } else {
-                keep = is_alive(tb, i, rmin[i], bsf) && rank_bits(tb, i, rmin[i]) >= thr;
+                k = is_alive(tb, i, rmin[i], bsf) && rank_bits(tb, i, rmin[i]) >= thr;
             }
             // sigpos: keep only rows at positions [p_lo, p_hi) of the mean order (a shard)
-            if (sigpos) keep = keep && sigpos[i] >= p_lo && sigpos[i] < p_hi;
-            flag[r] = keep;
-            local += keep;
+            if (sigpos) k = k && sigpos[i] >= p_lo && sigpos[i] < p_hi;
+            i8[q] = i;
+        }
+        bal[q] = __ballot_sync(0xffffffffu, k);
+        if (lane == 0) wcnt[q][wid] = __popc(bal[q]);
+    }
+    __syncthreads();
+    int total = 0;
+#pragma unroll
+    for (int q = 0; q < 8; q++)
+#pragma unroll
+        for (int w = 0; w < 8; w++) total += wcnt[q][w];
+    if (wid == 0) {
+        int prefix = 0;
+        if (b == 0) {
+            if (lane == 0) atomicExch(status, kStPre | (unsigned long long)(unsigned)total);
+        } else {
+            if (lane == 0) atomicExch(status + b, kStAgg | (unsigned long long)(unsigned)total);
+            int j = b - 1;  // the nearest predecessor not yet added
+            unsigned long long t0 = 0;
+            bool ok = true;
+            for (uint32_t it = 0; ok; ++it) {
+                const int jj = j - lane;
+                const unsigned long long v =
+                    jj >= 0 ? *(volatile const unsigned long long*)(status + jj) : kStPre;  // before block 0: 0
+                const unsigned pre = __ballot_sync(0xffffffffu, (v & kStPre) != 0);
+                const unsigned ready = __ballot_sync(0xffffffffu, (v & (kStPre | kStAgg)) != 0);
+                const int fp = pre ? __ffs(pre) - 1 : 32;  // nearest predecessor with an inclusive prefix
+                const unsigned need = fp < 32 ? ((2u << fp) - 1u) : 0xffffffffu;
+                if ((ready & need) != need) {  // a predecessor in the window has not published: wait
+                    if ((it & 63u) == 0u) {
+                        // lane 0's clock decides for the whole warp (the loop stays warp-uniform)
+                        const unsigned long long t = __shfl_sync(0xffffffffu, gtimer(), 0);
+                        if (t0 == 0) t0 = t;
+                        if (t - t0 > 2000000000ull) {
+                            if (lane == 0) atomicExch(&ctrl->err, DD_ETIMEOUT);
+                            ok = false;
+                        }
+                    }
+                    continue;
+                }
+                int val = lane <= fp && jj >= 0 ? (int)(unsigned)(v & 0xffffffffull) : 0;
+                val = __reduce_add_sync(0xffffffffu, val);
+                prefix += val;
+                if (fp < 32) break;
+                j -= 32;
+            }
+            if (lane == 0) atomicExch(status + b, kStPre | (unsigned long long)(unsigned)(prefix + total));
+        }
+        if (lane == 0) {
+            sh_base = prefix;
+            if (b == nb - 1) *cnt_out = prefix + total;
         }
     }
-    if (local) atomicAdd(&sh, local);
     __syncthreads();
-    if (threadIdx.x == 0) blk[blockIdx.x] = sh;
-}
-
-// Compaction pass 2: exclusive scan of the block counts (one block).
-// Compaction pass 2: each block adds up the counts of the blocks before it
-// (at most a few hundred, from L2) for its base, then scatters its kept rows in
-// order; block 0 also writes the total count.
-__global__ void __launch_bounds__(256) k_compact_scatter(ListRef in, const uint8_t* __restrict__ flag,
-                                                         const int* __restrict__ blk, int nblk,
-                                                         int32_t* __restrict__ out, int* __restrict__ cnt_out) {
-    __shared__ int wsum[8];
-    __shared__ int red[8];
-    const int cnt = *in.cnt_dev;
-    const int off = in.off_dev ? *in.off_dev : 0;
-    const int base = blockIdx.x * kCompactRows + threadIdx.x * 8;
-    const int lim = blockIdx.x == 0 ? nblk : blockIdx.x;  // block 0: every block, for the total
-    int pre = 0;
-    for (int b = threadIdx.x; b < lim; b += blockDim.x) pre += blk[b];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) pre += __shfl_xor_sync(0xffffffffu, pre, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = pre;
-    __syncthreads();
-    pre = 0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); w++) pre += red[w];
-    if (blockIdx.x == 0) {
-        if (threadIdx.x == 0) *cnt_out = pre;
-        pre = 0;
-    }
-    if (blockIdx.x * kCompactRows >= cnt) return;
-    int f[8], local = 0;
+    int pos = sh_base;
 #pragma unroll
     for (int q = 0; q < 8; q++) {
-        const int r = base + q;
-        f[q] = (r < cnt) ? flag[r] : 0;
-        local += f[q];
-    }
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    int incl = local;
+        int before = 0;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        int u = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += u;
-    }
-    if (lane == 31) wsum[wid] = incl;
-    __syncthreads();
-    int wbase = 0;
-    for (int q = 0; q < wid; q++) wbase += wsum[q];
-    int pos = pre + wbase + incl - local;
+        for (int w = 0; w < 8; w++) before += w < wid ? wcnt[q][w] : 0;
+        if (bal[q] & (1u << lane)) out[pos + before + __popc(bal[q] & lt)] = i8[q];
 #pragma unroll
-    for (int q = 0; q < 8; q++) {
-        if (f[q]) out[pos++] = in.base[off + base + q];
+        for (int w = 0; w < 8; w++) pos += wcnt[q][w];
     }
 }
 
@@ -299,60 +341,62 @@ __global__ void __launch_bounds__(128) k_tile_ranges(ListRef L, int kind, int K,
     __shared__ int red[4][4];
     const int cnt = *L.cnt_dev;
     const int off = L.off_dev ? *L.off_dev : 0;
-    const int t = blockIdx.x;
-    if (t * 128 >= cnt) return;
-    const int r = t * 128 + threadIdx.x;
-    int lo = 0x7fffffff, hi = -1, qmin = 0x7fffffff, qmax = -1;
-    if (r < cnt) {
-        const int i = L.base[off + r];
-        const int q = sigpos[i];
-        qmin = qmax = q;
-        if (kind == 0) {
-            lo = q - K;
-            hi = q + 1 + K;
-        } else {
-            const float R = row_ub(tb, i, __uint_as_float(rmin[i]));
-            const double w = stats[7];
-            if (!(R < 1e30f) || !(w > 0.0)) {
-                lo = 0;
-                hi = N;
+    // one tile per block iteration (the grid is sized for a few tiles per SM, not for the longest list)
+    for (int t = blockIdx.x; t * 128 < cnt; t += gridDim.x) {
+        __syncthreads();  // red[] of the previous tile has been read
+        const int r = t * 128 + threadIdx.x;
+        int lo = 0x7fffffff, hi = -1, qmin = 0x7fffffff, qmax = -1;
+        if (r < cnt) {
+            const int i = L.base[off + r];
+            const int q = sigpos[i];
+            qmin = qmax = q;
+            if (kind == 0) {
+                lo = q - K;
+                hi = q + 1 + K;
             } else {
-                const double h = sqrt((double)R / (double)n) * (1.0 + 1e-4) + 1e-12;
-                const double kb = ceil(h / w) + 1.0;
-                const int k = kb < (double)kMuBins ? (int)kb : kMuBins;  // NaN -> every bin
-                const int b = mubin[i];
-                lo = binstart[b - k < 0 ? 0 : b - k];
-                hi = binstart[b + k + 1 > kMuBins ? kMuBins : b + k + 1];
+                const float R = row_ub(tb, i, __uint_as_float(rmin[i]));
+                const double w = stats[7];
+                if (!(R < 1e30f) || !(w > 0.0)) {
+                    lo = 0;
+                    hi = N;
+                } else {
+                    const double h = sqrt((double)R / (double)n) * (1.0 + 1e-4) + 1e-12;
+                    const double kb = ceil(h / w) + 1.0;
+                    const int k = kb < (double)kMuBins ? (int)kb : kMuBins;  // NaN -> every bin
+                    const int b = mubin[i];
+                    lo = binstart[b - k < 0 ? 0 : b - k];
+                    hi = binstart[b + k + 1 > kMuBins ? kMuBins : b + k + 1];
+                }
             }
         }
-    }
-    lo = __reduce_min_sync(0xffffffffu, lo);
-    hi = __reduce_max_sync(0xffffffffu, hi);
-    qmin = __reduce_min_sync(0xffffffffu, qmin);
-    qmax = __reduce_max_sync(0xffffffffu, qmax);
-    const int wid = threadIdx.x >> 5;
-    if ((threadIdx.x & 31) == 0) {
-        red[0][wid] = lo;
-        red[1][wid] = hi;
-        red[2][wid] = qmin;
-        red[3][wid] = qmax;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int w2 = 1; w2 < 4; w2++) {
-            lo = min(lo, red[0][w2]);
-            hi = max(hi, red[1][w2]);
-            qmin = min(qmin, red[2][w2]);
-            qmax = max(qmax, red[3][w2]);
+        lo = __reduce_min_sync(0xffffffffu, lo);
+        hi = __reduce_max_sync(0xffffffffu, hi);
+        qmin = __reduce_min_sync(0xffffffffu, qmin);
+        qmax = __reduce_max_sync(0xffffffffu, qmax);
+        const int wid = threadIdx.x >> 5;
+        if ((threadIdx.x & 31) == 0) {
+            red[0][wid] = lo;
+            red[1][wid] = hi;
+            red[2][wid] = qmin;
+            red[3][wid] = qmax;
         }
-        lo = lo < 0 ? 0 : lo;
-        hi = hi > N ? N : hi;
-        int C = (qmin + qmax + 1) / 2;
-        C = C < lo ? lo : (C > hi ? hi : C);
-        const int side = max(hi - C, C - lo);
-        const int nseg = 2 * ((side + seg_cols - 1) / seg_cols);
-        ranges[t] = make_int4(lo, hi, C, nseg);
-        atomicMax(smax, nseg);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int w2 = 1; w2 < 4; w2++) {
+                lo = min(lo, red[0][w2]);
+                hi = max(hi, red[1][w2]);
+                qmin = min(qmin, red[2][w2]);
+                qmax = max(qmax, red[3][w2]);
+            }
+            lo = lo < 0 ? 0 : lo;
+            hi = hi > N ? N : hi;
+            int C = (qmin + qmax + 1) / 2;
+            C = C < lo ? lo : (C > hi ? hi : C);
+            const int side = max(hi - C, C - lo);
+            const int nseg = 2 * ((side + seg_cols - 1) / seg_cols);
+            ranges[t] = make_int4(lo, hi, C, nseg);
+            atomicMax(smax, nseg);
+        }
     }
 }
 
@@ -483,6 +527,16 @@ struct Seq {
     }
     int* cnt_ptr(int slot) { return &p->ctrl->cnt[slot]; }
 
+    // Cand (Eq. 7) as the head of the word order; a shard keeps only its own positions
+    ListRef cand_list(int32_t* out) {
+        if (p_lo != 0 || p_hi != (int)p->N) return compact(constant_list(p->order, (int)p->N), out, 2, true);
+        const int slot = cnt_slot++;
+        k_cand_count<<<1, 1, 0, s>>>(p->ctrl, p->opt.phase1_max, cnt_ptr(slot));
+        p->launches++;
+        check();
+        return ListRef{p->order, nullptr, cnt_ptr(slot)};
+    }
+
     ListRef constant_list(const int32_t* base, int count) {
         const int slot = cnt_slot++;
         k_set_int<<<1, 1, 0, s>>>(cnt_ptr(slot), count);
@@ -592,7 +646,8 @@ struct Seq {
             return nullptr;
         }
         const int tiles = (int)((p->N + 127) / 128);
-        k_tile_ranges<<<tiles, 128, 0, s>>>(rows, kind, K, kSegCols, p->sigpos, p->mubin, p->binstart, p->rmin, tb,
+        const int grid = tiles < p->sm_count * 8 ? tiles : p->sm_count * 8;
+        k_tile_ranges<<<grid, 128, 0, s>>>(rows, kind, K, kSegCols, p->sigpos, p->mubin, p->binstart, p->rmin, tb,
                                             p->stats, p->n, (int)p->N, p->ranges, &p->ctrl->smax[slot]);
         p->launches++;
         check();
@@ -663,8 +718,14 @@ struct Seq {
     }
 
     // cnt_out: write the count there instead of a new slot (refreshing a list in place)
+    int csite = 0;
     ListRef compact(ListRef in, int32_t* out, int pred, bool shard_only = false, int* cnt_out = nullptr) {
-        const int nblk = (int)((p->N + kCompactRows - 1) / kCompactRows);
+        const int nblk = p->cstat_stride;
+        if (csite >= kCompactSites) {
+            err = cudaErrorInvalidValue;
+            return in;
+        }
+        const int site = csite++;
         int* cnt = cnt_out;
         if (!cnt) {
             const int slot = cnt_slot++;
@@ -674,10 +735,10 @@ struct Seq {
             }
             cnt = cnt_ptr(slot);
         }
-        k_compact_flags<<<nblk, 256, 0, s>>>(in, p->rmin, tb, p->ctrl, pred, p->code, p->hist, p->opt.phase1_max,
-                                             shard_only ? p->sigpos : nullptr, p_lo, p_hi, p->flag, p->blk);
-        k_compact_scatter<<<nblk, 256, 0, s>>>(in, p->flag, p->blk, nblk, out, cnt);
-        p->launches += 2;
+        k_compact<<<nblk, 256, 0, s>>>(in, p->rmin, tb, p->ctrl, pred, p->code, p->hist, p->opt.phase1_max,
+                                       shard_only ? p->sigpos : nullptr, p_lo, p_hi, site,
+                                       p->cstat + (size_t)site * nblk, out, cnt);
+        p->launches += 1;
         check();
         return ListRef{out, nullptr, cnt};
     }
@@ -730,7 +791,8 @@ cudaError_t launch_search(dd_plan_s* p, const float* T, dd_result_t* out_dev, cu
     p->bodies.clear();
     cudaError_t e = cudaMemsetAsync(p->ctrl, 0, sizeof(Ctrl), s);
     if (e != cudaSuccess) return e;
-    e = cudaMemsetAsync(p->rmin, 0x7f, sizeof(uint32_t) * p->N, s);
+    e = cudaMemsetAsync(p->cstat, 0, sizeof(unsigned long long) * kCompactSites * p->cstat_stride, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->rmin, 0x7f, sizeof(uint32_t) * p->N, s);
     if (e == cudaSuccess && p->rmin32) e = cudaMemsetAsync(p->rmin32, 0x7f, sizeof(uint32_t) * p->N, s);
     if (e != cudaSuccess) return e;
     e = launch_prep_common(p, T, s);
@@ -782,11 +844,13 @@ cudaError_t launch_search(dd_plan_s* p, const float* T, dd_result_t* out_dev, cu
         }
         join();
         // Algorithm 3 (PotentialDiscord): the Cand rows (rarest SAX words).
-        ListRef cand = q.compact(all, p->list[0], 2);
+        ListRef cand = q.cand_list(p->list[0]);
         q.full(DD_WAVE_CAND, cand);
         // Raise the best-so-far further: full scans of the rows with the
-        // largest upper bounds (the likeliest discords) next.
-        ListRef alive = q.compact(all, p->list[1], 0);
+        // largest upper bounds (the likeliest discords) next.  A row once
+        // ruled out stays ruled out (the best-so-far only grows, upper bounds
+        // only shrink), so every later selection reads the whole list.
+        const ListRef alive = all;
         if (o.refine_k > 0) {
             q.topk(alive, o.refine_k);
             ListRef top = q.compact(alive, p->list[2], 1);
