@@ -254,7 +254,7 @@ def _window(dd, Td, m: int, n: int, peaks, sms: int, reps: int = 3) -> dict:
 
 def _batch(dd, precision: str, count: int = 512) -> dict:
     """Many uneven series (m log-uniform in [2048, 65536], n in {64, 128, 256}) resident on
-    the device, searched by one dd_find_discord_batched call (an engine of 8 workers)."""
+    the device, searched by one dd_find_discord_batched call (an engine of 32 workers)."""
     import torch
     from paper_1901_00155_gb300 import synth
     specs = synth.workload_batch(0, count)
@@ -268,14 +268,18 @@ def _batch(dd, precision: str, count: int = 512) -> dict:
     pairs = sum(_pairs_unordered(s.m - s.n + 1, s.n) for s in specs)
     return {"workload": f"{count} series, m log-uniform [2048, 65536], n in {{64,128,256}}, rw/sine, seed 0",
             "precision": precision, "ms": dt * 1e3, "series_per_s": count / dt,
-            "value": pairs / dt, "unit": "pair-distances/s (brute-force equivalent)", "workers": 8,
+            "value": pairs / dt, "unit": "pair-distances/s (brute-force equivalent)", "workers": 32,
             "failed": sum(1 for r in res if isinstance(r, Exception))}
 
 
-def _serve(dd, precision: str, duration_s: float = 5.0, workers: int = 8, rate: float = 200.0) -> dict:
+SIZE_CLASSES = (("m<2^15", 0, 1 << 15), ("2^15<=m<2^18", 1 << 15, 1 << 18), ("m>=2^18", 1 << 18, 1 << 62))
+
+
+def _serve(dd, precision: str, duration_s: float = 20.0, workers: int = 8, rate: float = 200.0) -> dict:
     """Poisson arrivals (rate per s) of host series (m log-uniform in [4096, 2^20], n in
-    {64, ..., 1024}) into an engine of `workers`; latency = submission -> result on the host
-    (queue + host->device copy + plan + search + result copy)."""
+    {64, ..., 1024}) into an engine of `workers` admitting by device memory; latency =
+    submission -> result on the host (queue + host->device copy + plan + search + result copy),
+    overall and per size class of m."""
     import torch
     from paper_1901_00155_gb300 import synth
     trace = synth.serving_requests(0, rate, duration_s)
@@ -298,13 +302,24 @@ def _serve(dd, precision: str, duration_s: float = 5.0, workers: int = 8, rate: 
         done += E.drain()
         t_end = time.perf_counter()
     failed = sum(1 for c in done if isinstance(c.result, Exception))
-    lat = sorted(c.queue_ms + c.service_ms for c in done)
-    q = lambda f: lat[min(len(lat) - 1, int(f * len(lat)))]
-    return {"workload": f"Poisson {rate:g}/s for {duration_s:g} s ({len(trace)} requests), m log-uniform "
-                        f"[4096, 2^20], n in {{64..1024}}, host series, seed 0",
-            "precision": precision, "workers": workers, "requests": len(done), "failed": failed,
-            "p50_ms": q(0.50), "p99_ms": q(0.99), "max_ms": lat[-1], "mean_ms": sum(lat) / len(lat),
-            "throughput_rps": len(done) / (t_end - t_start)}
+
+    def stats(cs):
+        lat = sorted(c.queue_ms + c.service_ms for c in cs)
+        if not lat:
+            return {"requests": 0}
+        q = lambda f: lat[min(len(lat) - 1, int(f * len(lat)))]  # noqa: E731
+        return {"requests": len(lat), "p50_ms": q(0.50), "p99_ms": q(0.99), "max_ms": lat[-1],
+                "mean_ms": sum(lat) / len(lat), "mean_queue_ms": sum(c.queue_ms for c in cs) / len(cs)}
+
+    measured = [c for c in done if c.id >= 0]
+    by_class = {name: stats([c for c in measured if lo <= trace[c.id][1].m < hi]) for name, lo, hi in SIZE_CLASSES}
+    out = {"workload": f"Poisson {rate:g}/s for {duration_s:g} s ({len(trace)} requests), m log-uniform "
+                       f"[4096, 2^20], n in {{64..1024}}, host series, seed 0",
+           "precision": precision, "workers": workers, "admission": "device-memory budget (default), bypass <= 32",
+           "failed": failed, "throughput_rps": len(measured) / (t_end - t_start)}
+    out.update(stats(measured))
+    out["by_size_class"] = by_class
+    return out
 
 
 def _reference_arm(args, rank: int):

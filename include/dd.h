@@ -224,7 +224,7 @@ DD_API dd_status_t dd_find_discords(dd_plan_t plan, const float* T_dev, int32_t 
  * and subsequence lengths (T_dev[k]: m[k] float32 values on the device,
  * n[k]); one options struct for all (NULL = defaults).  Results go to
  * out[k] (host memory); out[k].status reports each series' own error.
- * Runs on a temporary engine (below) with up to 8 workers, longest series
+ * Runs on a temporary engine (below) with up to 32 workers, longest series
  * first; waits for `stream` first so that the series are ready.  Returns
  * the first error met, DD_OK if every search succeeded. */
 DD_API dd_status_t dd_find_discord_batched(int32_t count, const float* const* T_dev, const int64_t* m, const int32_t* n,
@@ -396,13 +396,19 @@ DD_API const char* dd_status_string(dd_status_t status);
 /* ---- engine: concurrent searches for batches and serving ---------------
  *
  * Not in the paper (which runs one search at a time): a pool of workers,
- * each a host thread with its own CUDA stream, device workspace and plan,
- * takes requests from one FIFO queue and runs them concurrently on the GPU,
- * so that many small searches overlap.  Each worker keeps its last plan and
- * reuses it for requests of the same (m, n); a new shape builds a plan in
- * the worker's workspace without waiting for the other workers.  Every
- * request uses the engine's options.  A request's result equals that of a
- * plan searching the same series alone. */
+ * each a host thread with its own CUDA stream, takes requests from one queue
+ * and runs them concurrently on the GPU, so that many small searches overlap.
+ * Admission is by device memory: every plan lives in a workspace of exactly
+ * its footprint (dd_plan_footprint) taken from an engine-owned stream-ordered
+ * pool, a host series in a staging buffer of 4 m bytes from the same pool,
+ * and a request starts only while the workspaces held by the workers (the
+ * resident plans of idle workers included) plus its own fit the engine's
+ * budget.  A worker takes the first queued request that fits, so smaller
+ * requests pass one that does not -- at most 32 times, after which nothing is
+ * admitted past it until it fits.  A worker keeps its last plan and reuses it
+ * for requests of the same (m, n), and gives it back when nothing queued fits.
+ * Every request uses the engine's options.  A request's result equals that of
+ * a plan searching the same series alone. */
 typedef struct dd_engine_s* dd_engine_t;
 
 typedef struct {
@@ -415,14 +421,19 @@ typedef struct {
 
 enum { DD_SERIES_DEVICE = 0, DD_SERIES_HOST = 1 };
 
-/* workers in [1, 64].  Each worker reserves enough device memory for the
- * plan of any series with m <= m_max and n <= n_max (the largest
- * dd_plan_footprint over those shapes), plus m_max floats for host series.
- * Admission: a request whose plan does not fit, or a host series longer than
- * m_max, completes with DD_ENOMEM.  (m_max, n_max) must itself be a valid
- * shape.  Errors: DD_EINVAL (bad sizes or options), DD_ENOMEM, DD_ECUDA. */
+/* workers in [1, 64].  The budget is workers x (the largest plan footprint of
+ * a series with m <= m_max, n <= n_max, plus m_max floats of staging): the
+ * memory a pool of per-worker workspaces of the largest shape would hold.
+ * Admission: a request whose plan and staging exceed the whole budget, or a
+ * host series longer than m_max, completes with DD_ENOMEM.  (m_max, n_max)
+ * must itself be a valid shape.  Errors: DD_EINVAL (bad sizes or options),
+ * DD_ENOMEM, DD_ECUDA. */
 DD_API dd_status_t dd_engine_create(dd_engine_t* engine, int32_t workers, const dd_options_t* opt, int64_t m_max,
                                     int32_t n_max);
+
+/* The same with an explicit budget of device bytes (0 = the default above). */
+DD_API dd_status_t dd_engine_create_budget(dd_engine_t* engine, int32_t workers, const dd_options_t* opt,
+                                           int64_t m_max, int32_t n_max, size_t budget_bytes);
 
 /* Queues a search of the m values at T (device memory, or host memory with
  * flags = DD_SERIES_HOST) with subsequence length n.  T must stay valid and

@@ -386,17 +386,19 @@ class Completion:
 
 class Engine:
     """Concurrent searches (dd_engine_*): ``workers`` host threads, each with its own
-    CUDA stream, workspace and plan, take requests from one queue.  ``submit`` accepts
+    CUDA stream, take requests from one queue and admit them against ``budget`` bytes of
+    device memory (default: workers x the largest plan of m <= m_max, n <= n_max; smaller
+    requests pass one that does not fit).  ``submit`` accepts
     a CUDA float32 tensor (already complete on its stream) or host data (numpy / CPU
     tensor; the worker copies it); the series is kept alive until its completion is
     polled."""
 
-    def __init__(self, workers: int, m_max: int, n_max: int, precision="fp32", **opts):
+    def __init__(self, workers: int, m_max: int, n_max: int, precision="fp32", budget: int | None = None, **opts):
         self._lib = _lib.load()
         self.options = _options(precision, **opts)
         self._ptr = ctypes.c_void_p()
-        _check(self._lib.dd_engine_create(ctypes.byref(self._ptr), int(workers), ctypes.byref(self.options),
-                                          int(m_max), int(n_max)), "dd_engine_create")
+        _check(self._lib.dd_engine_create_budget(ctypes.byref(self._ptr), int(workers), ctypes.byref(self.options),
+                                                 int(m_max), int(n_max), int(budget or 0)), "dd_engine_create")
         self._keep = {}
         self._next = 0
 

@@ -102,6 +102,8 @@ SIGNATURES = {
                              ctypes.c_int),
     "dd_engine_create": ([ctypes.POINTER(ctypes.c_void_p), ctypes.c_int32, ctypes.POINTER(Options), ctypes.c_int64,
                           ctypes.c_int32], ctypes.c_int),
+    "dd_engine_create_budget": ([ctypes.POINTER(ctypes.c_void_p), ctypes.c_int32, ctypes.POINTER(Options),
+                                 ctypes.c_int64, ctypes.c_int32, ctypes.c_size_t], ctypes.c_int),
     "dd_engine_submit": ([ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32,
                           ctypes.c_int32], ctypes.c_int),
     "dd_engine_poll": ([ctypes.c_void_p, ctypes.POINTER(Completion), ctypes.c_int32, ctypes.c_int32], ctypes.c_int32),

@@ -12,6 +12,7 @@ using dd::Ctrl;
 namespace {
 
 constexpr size_t kAlign = 256;
+constexpr int32_t kBatchWorkers = 32;  // engine workers of a batched call
 constexpr int kPad = 64;  // zero elements after the series copies
 
 struct Carver {
@@ -308,7 +309,7 @@ namespace dd {
 // without graph capture (every shape is used once or a few times) and have no
 // pinned result buffer.
 dd_status_t create_plan(dd_plan_s** plan, int64_t m, int32_t n, const dd_options_t* opt, void* workspace,
-                        size_t workspace_bytes, bool engine, cudaStream_t init) {
+                        size_t workspace_bytes, bool engine, cudaStream_t init, const PlanShared* borrowed) {
     if (!plan) return DD_EINVAL;
     *plan = nullptr;
     dd_options_t o;
@@ -391,10 +392,17 @@ dd_status_t create_plan(dd_plan_s** plan, int64_t m, int32_t n, const dd_options
         k_iota<<<(unsigned)((p->N + 255) / 256), 256, 0, init>>>(p->seq_rows, p->N);
         e = cudaGetLastError();
     }
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->side_stream, cudaStreamNonBlocking);
+    if (borrowed) {
+        p->own_side = false;
+        p->side_stream = borrowed->side;
+        p->ev_fork = borrowed->fork;
+        p->ev_join = borrowed->join;
+    } else {
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->side_stream, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming);
+    }
     if (e == cudaSuccess && !engine) e = cudaStreamCreateWithFlags(&p->body_stream, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming);
     if (e == cudaSuccess && o.precision != DD_FP32) e = dd::tc_make_maps(p);
     if (e == cudaSuccess && o.precision != DD_FP32) e = dd::tc_init_plan(p, init);
     // the host copy above reads p->beta_host: wait for the init stream before returning
@@ -416,10 +424,12 @@ void destroy_plan(dd_plan_s* p, bool wait_device) {
     if (wait_device) cudaDeviceSynchronize();
     if (p->gexec) cudaGraphExecDestroy(p->gexec);
     if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
-    if (p->side_stream) cudaStreamDestroy(p->side_stream);
+    if (p->own_side) {
+        if (p->side_stream) cudaStreamDestroy(p->side_stream);
+        if (p->ev_fork) cudaEventDestroy(p->ev_fork);
+        if (p->ev_join) cudaEventDestroy(p->ev_join);
+    }
     if (p->body_stream) cudaStreamDestroy(p->body_stream);
-    if (p->ev_fork) cudaEventDestroy(p->ev_fork);
-    if (p->ev_join) cudaEventDestroy(p->ev_join);
     for (cudaEvent_t e : p->ev) cudaEventDestroy(e);
     for (cudaEvent_t e : p->call_ev)
         if (e) cudaEventDestroy(e);
@@ -558,7 +568,8 @@ dd_status_t dd_find_discord_batched(int32_t count, const float* const* T_dev, co
     }
     if (m_max == 0) return DD_EINVAL;
     dd_engine_t E = nullptr;
-    dd_status_t st = dd_engine_create(&E, count < 8 ? count : 8, &o, m_max, n_max);
+    // a search of a short series is a chain of small kernels: up to 32 run side by side
+    dd_status_t st = dd_engine_create(&E, count < kBatchWorkers ? count : kBatchWorkers, &o, m_max, n_max);
     if (st != DD_OK) return st;
     // longest series first, so that the last ones to start are short
     std::vector<int32_t> ord((size_t)count);

@@ -321,6 +321,7 @@ struct dd_plan_s {
     std::vector<CondBody> g_bodies;      // the same for the cached graph
     bool in_cond = false;                // capturing a conditional body (no event nodes there)  // SAX / word order run here, beside the mean order
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    bool own_side = true;                // the side stream and fork / join events belong to the plan
     cudaGraphExec_t gexec = nullptr;
     const void* g_T = nullptr;
     const void* g_out = nullptr;
@@ -357,9 +358,16 @@ size_t tc_smem_bytes(int kpad);
 int tc_stages(int kpad);
 bool tc_supported(int n);
 cudaError_t tc_make_maps(dd_plan_s* p);
-// api.cu: plan construction shared by the public entry point and the engine
+// api.cu: plan construction shared by the public entry point and the engine.
+// Engine plans may borrow their worker's side stream and fork / join events
+// (borrowed = non-null: {side stream, fork event, join event}), which the plan
+// then neither creates nor destroys.
+struct PlanShared {
+    cudaStream_t side;
+    cudaEvent_t fork, join;
+};
 dd_status_t create_plan(dd_plan_s** plan, int64_t m, int32_t n, const dd_options_t* opt, void* workspace,
-                        size_t workspace_bytes, bool engine, cudaStream_t init);
+                        size_t workspace_bytes, bool engine, cudaStream_t init, const PlanShared* borrowed = nullptr);
 void destroy_plan(dd_plan_s* p, bool wait_device);
 cudaError_t tc_init_plan(dd_plan_s* p, cudaStream_t s);
 cudaError_t launch_tc_prep(dd_plan_s* p, cudaStream_t s);

@@ -1,18 +1,31 @@
 // engine.cu -- concurrent searches: a pool of worker threads, each with its own
-// CUDA stream, device workspace and plan, fed from one FIFO request queue.
+// CUDA stream, fed from one request queue and admitted against one budget of
+// device memory.
 //
 // The paper runs one search at a time.  On one GB300 a search of a short
 // series is latency-bound (tens of small kernels, a few microseconds each),
 // so many of them are run side by side: each worker enqueues its request's
-// kernels on its own stream, and the GPU overlaps the streams.  A worker
-// keeps its last plan and reuses it for the same (m, n); a new shape builds
-// a plan inside the worker's workspace, initialised on the worker's stream,
-// so no worker waits for another one's searches.
+// kernels on its own stream, and the GPU overlaps the streams.
+//
+// Memory: the engine allocates one device arena of its budget at creation and
+// hands out blocks of it on the host (first fit, 256-byte aligned, coalescing
+// free list): every plan lives in a block of exactly its footprint
+// (dd_plan_footprint), a host series is staged in a block of 4 m bytes.  A
+// request is admitted when its blocks can be allocated, so the workspaces in
+// use (resident plans of idle workers included) never exceed the budget.  A
+// worker keeps its last plan and reuses it for the same (m, n); a worker that
+// finds nothing admissible releases what it holds, so that resident plans
+// never block a request.
+// Scheduling: a worker takes the first queued request that fits; a request that
+// does not fit is passed over by smaller ones behind it, at most kMaxBypass
+// times, after which nothing is admitted past it until it fits.
 
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
 #include <deque>
+#include <iterator>
+#include <map>
 #include <mutex>
 #include <new>
 #include <thread>
@@ -23,6 +36,7 @@
 namespace {
 
 using Clock = std::chrono::steady_clock;
+constexpr int kMaxBypass = 32;
 
 struct Request {
     int64_t id;
@@ -31,20 +45,81 @@ struct Request {
     int32_t n;
     int32_t flags;
     Clock::time_point submitted;
+    size_t need;   // plan footprint (0: invalid sizes, fails without memory)
+    int bypassed;  // times a later request was admitted before this one
+};
+
+// Blocks of the engine's device arena, handed out on the host: first fit over a
+// free list ordered by offset, adjacent free blocks merged on release.
+class Arena {
+public:
+    static constexpr size_t kAlignA = 256;
+    void reset(size_t bytes) {
+        free_.clear();
+        if (bytes) free_[0] = bytes;
+    }
+    static size_t round(size_t b) { return (b + kAlignA - 1) / kAlignA * kAlignA; }
+    // offset of a new block of b bytes, or SIZE_MAX
+    size_t alloc(size_t b) {
+        b = round(b);
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second < b) continue;
+            const size_t off = it->first, rest = it->second - b;
+            free_.erase(it);
+            if (rest) free_[off + b] = rest;
+            return off;
+        }
+        return SIZE_MAX;
+    }
+    // takes exactly [off, off + b) if it lies inside one free block (undoing a release)
+    bool alloc_at(size_t off, size_t b) {
+        b = round(b);
+        auto it = free_.upper_bound(off);
+        if (it == free_.begin()) return false;
+        --it;
+        const size_t s0 = it->first, sz = it->second;
+        if (s0 > off || s0 + sz < off + b) return false;
+        free_.erase(it);
+        if (off > s0) free_[s0] = off - s0;
+        if (s0 + sz > off + b) free_[off + b] = s0 + sz - (off + b);
+        return true;
+    }
+    void release(size_t off, size_t b) {
+        b = round(b);
+        auto it = free_.emplace(off, b).first;
+        auto next = std::next(it);
+        if (next != free_.end() && it->first + it->second == next->first) {
+            it->second += next->second;
+            free_.erase(next);
+        }
+        if (it != free_.begin()) {
+            auto prev = std::prev(it);
+            if (prev->first + prev->second == it->first) {
+                prev->second += it->second;
+                free_.erase(it);
+            }
+        }
+    }
+
+private:
+    std::map<size_t, size_t> free_;  // offset -> bytes
 };
 
 struct Worker {
     std::thread thread;
     cudaStream_t stream = nullptr;
-    void* ws = nullptr;                // plan workspace
+    dd::PlanShared shared{};           // side stream and fork / join events lent to the worker's plans
+    size_t ws_off = SIZE_MAX;          // arena block of the resident plan's workspace
     size_t ws_bytes = 0;
-    float* stage = nullptr;            // device copy of host series
+    size_t stage_off = SIZE_MAX;       // arena block of the device copy of a host series
+    size_t stage_bytes = 0;
     dd_result_t* res_dev = nullptr;
     dd_result_t* res_host = nullptr;   // pinned
     dd_plan_s* plan = nullptr;         // last plan, reused for the same (m, n)
+    size_t held() const { return ws_bytes + stage_bytes; }
 };
 
-// Device bytes that fit a plan of any series with m <= m_max, n <= n_max.  The
+// Device bytes of the plan of any series with m <= m_max, n <= n_max.  The
 // footprint grows with m.  For fixed m it falls with n (fewer subsequences)
 // except where it steps up: while n < paa_w the SAX dictionary grows with n
 // (words have min(paa_w, n) letters), and the padded tensor-core row length
@@ -66,15 +141,20 @@ double ms_between(Clock::time_point a, Clock::time_point b) {
     return std::chrono::duration<double, std::milli>(b - a).count();
 }
 
+size_t stage_need(const Request& r) { return (r.flags & DD_SERIES_HOST) ? sizeof(float) * (size_t)r.m : 0; }
+
 }  // namespace
 
 struct dd_engine_s {
     int device = 0;
     dd_options_t opt{};
     int64_t m_max = 0;
+    size_t budget = 0;                 // device bytes of the arena
+    char* arena_base = nullptr;
+    Arena arena;                       // guarded by mu
     std::vector<Worker> workers;
     std::mutex mu;
-    std::condition_variable cv_work;   // queue not empty / stopping
+    std::condition_variable cv_work;   // queue changed, memory freed, or stopping
     std::condition_variable cv_done;   // a completion arrived
     std::deque<Request> queue;
     std::deque<dd_completion_t> done;
@@ -82,6 +162,8 @@ struct dd_engine_s {
     bool stopping = false;
 
     void run(Worker& w);
+    bool pick(Worker& w, Request& r);
+    void release(Worker& w);
     dd_result_t serve(Worker& w, const Request& r);
 };
 
@@ -97,15 +179,86 @@ dd_result_t failed(dd_status_t st) {
 
 }  // namespace
 
+// Frees the worker's plan and arena blocks (its stream is idle).  Caller holds mu.
+void dd_engine_s::release(Worker& w) {
+    dd::destroy_plan(w.plan, false);
+    w.plan = nullptr;
+    if (w.ws_off != SIZE_MAX) arena.release(w.ws_off, w.ws_bytes);
+    if (w.stage_off != SIZE_MAX) arena.release(w.stage_off, w.stage_bytes);
+    w.ws_off = w.stage_off = SIZE_MAX;
+    w.ws_bytes = w.stage_bytes = 0;
+}
+
+// Chooses the next request for worker w and allocates its blocks (caller holds
+// mu): the first queued request whose blocks can be allocated, passing over at
+// most kMaxBypass times a request whose cannot.  A request that cannot succeed
+// (invalid sizes, more than the whole budget) is taken at once and fails
+// without memory.  On success the request leaves the queue.
+bool dd_engine_s::pick(Worker& w, Request& r) {
+    for (size_t k = 0; k < queue.size(); k++) {
+        Request& q = queue[k];
+        bool take = false;
+        if (q.need == 0 || Arena::round(q.need) + Arena::round(stage_need(q)) > budget ||
+            ((q.flags & DD_SERIES_HOST) && q.m > m_max)) {
+            take = true;
+        } else {
+            const bool same = w.plan && w.plan->m == q.m && w.plan->n == q.n;
+            // a new plan replaces the resident one: its block is free for the new one
+            const size_t old_off = w.ws_off, old_bytes = w.ws_bytes;
+            size_t ws_off = w.ws_off;
+            if (!same) {
+                if (old_off != SIZE_MAX) arena.release(old_off, old_bytes);
+                ws_off = arena.alloc(q.need);
+            }
+            size_t st_off = w.stage_off;
+            bool ok = ws_off != SIZE_MAX;
+            const bool grow_stage = stage_need(q) > w.stage_bytes;
+            if (ok && grow_stage) {
+                if (w.stage_off != SIZE_MAX) arena.release(w.stage_off, w.stage_bytes);
+                st_off = arena.alloc(stage_need(q));
+                if (st_off == SIZE_MAX) {
+                    ok = false;
+                    // put the old staging block back where it was (just freed, nobody took it)
+                    if (w.stage_off != SIZE_MAX) arena.alloc_at(w.stage_off, w.stage_bytes);
+                }
+            }
+            if (!ok) {
+                if (!same) {
+                    if (ws_off != SIZE_MAX) arena.release(ws_off, q.need);
+                    if (old_off != SIZE_MAX) arena.alloc_at(old_off, old_bytes);
+                }
+            } else {
+                if (!same) {
+                    dd::destroy_plan(w.plan, false);  // its block now belongs to the new plan
+                    w.plan = nullptr;
+                    w.ws_off = ws_off;
+                    w.ws_bytes = q.need;
+                }
+                if (grow_stage) {
+                    w.stage_off = st_off;
+                    w.stage_bytes = stage_need(q);
+                }
+                take = true;
+            }
+        }
+        if (take) {
+            r = q;
+            for (size_t j = 0; j < k; j++) queue[j].bypassed++;
+            queue.erase(queue.begin() + (long)k);
+            return true;
+        }
+        if (q.bypassed >= kMaxBypass) return false;  // nothing goes past a starved request
+    }
+    return false;
+}
+
 dd_result_t dd_engine_s::serve(Worker& w, const Request& r) {
-    if (r.n < 1 || r.m < 1) return failed(DD_EINVAL);
-    const size_t need = dd_plan_footprint(r.m, r.n, &opt);
-    if (need == 0) return failed(DD_EINVAL);
-    if (need > w.ws_bytes || ((r.flags & DD_SERIES_HOST) && r.m > m_max)) return failed(DD_ENOMEM);
-    if (!w.plan || w.plan->m != r.m || w.plan->n != r.n) {
-        dd::destroy_plan(w.plan, false);  // the worker's stream is idle here
-        w.plan = nullptr;
-        const dd_status_t st = dd::create_plan(&w.plan, r.m, r.n, &opt, w.ws, w.ws_bytes, true, w.stream);
+    if (r.n < 1 || r.m < 1 || r.need == 0) return failed(DD_EINVAL);
+    if (Arena::round(r.need) + Arena::round(stage_need(r)) > budget || ((r.flags & DD_SERIES_HOST) && r.m > m_max))
+        return failed(DD_ENOMEM);
+    if (!w.plan) {
+        const dd_status_t st = dd::create_plan(&w.plan, r.m, r.n, &opt, arena_base + w.ws_off, w.ws_bytes, true,
+                                               w.stream, &w.shared);
         if (st != DD_OK) {
             w.plan = nullptr;
             return failed(st);
@@ -114,8 +267,9 @@ dd_result_t dd_engine_s::serve(Worker& w, const Request& r) {
     const float* src = r.T;
     cudaError_t e = cudaSuccess;
     if (r.flags & DD_SERIES_HOST) {
-        e = cudaMemcpyAsync(w.stage, r.T, sizeof(float) * (size_t)r.m, cudaMemcpyHostToDevice, w.stream);
-        src = w.stage;
+        float* stage = reinterpret_cast<float*>(arena_base + w.stage_off);
+        e = cudaMemcpyAsync(stage, r.T, sizeof(float) * (size_t)r.m, cudaMemcpyHostToDevice, w.stream);
+        src = stage;
     }
     if (e != cudaSuccess) return failed(DD_ECUDA);
     dd_status_t st = dd_find_discord_async(w.plan, src, w.res_dev, w.stream);
@@ -135,10 +289,17 @@ void dd_engine_s::run(Worker& w) {
         Request r;
         {
             std::unique_lock<std::mutex> lk(mu);
-            cv_work.wait(lk, [&] { return stopping || !queue.empty(); });
-            if (stopping) return;
-            r = queue.front();
-            queue.pop_front();
+            for (;;) {
+                if (stopping) return;
+                if (pick(w, r)) break;
+                if (!queue.empty() && w.held() > 0) {
+                    // nothing fits while this worker holds memory: give it back and look again
+                    release(w);
+                    cv_work.notify_all();
+                    continue;
+                }
+                cv_work.wait(lk);
+            }
         }
         const Clock::time_point t0 = Clock::now();
         dd_completion_t c;
@@ -153,13 +314,14 @@ void dd_engine_s::run(Worker& w) {
             done.push_back(c);
         }
         cv_done.notify_all();
+        cv_work.notify_all();  // memory may have been freed
     }
 }
 
 extern "C" {
 
-dd_status_t dd_engine_create(dd_engine_t* engine, int32_t workers, const dd_options_t* opt, int64_t m_max,
-                             int32_t n_max) {
+dd_status_t dd_engine_create_budget(dd_engine_t* engine, int32_t workers, const dd_options_t* opt, int64_t m_max,
+                                    int32_t n_max, size_t budget_bytes) {
     if (!engine) return DD_EINVAL;
     *engine = nullptr;
     if (workers < 1 || workers > 64) return DD_EINVAL;
@@ -169,20 +331,24 @@ dd_status_t dd_engine_create(dd_engine_t* engine, int32_t workers, const dd_opti
     else
         dd_options_default(&o);
     if (dd_plan_footprint(m_max, n_max, &o) == 0) return DD_EINVAL;
-    const size_t ws = max_footprint(m_max, n_max, &o);
     dd_engine_s* E = new (std::nothrow) dd_engine_s();
     if (!E) return DD_ENOMEM;
     E->opt = o;
     E->m_max = m_max;
+    E->budget = budget_bytes ? budget_bytes
+                             : (size_t)workers * (max_footprint(m_max, n_max, &o) + sizeof(float) * (size_t)m_max);
+    E->budget = Arena::round(E->budget);
     cudaError_t e = cudaGetDevice(&E->device);
+    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&E->arena_base), E->budget);
+    if (e == cudaSuccess) E->arena.reset(E->budget);
     E->workers.resize((size_t)workers);
     for (Worker& w : E->workers) {
         if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&w.stream, cudaStreamNonBlocking);
-        if (e == cudaSuccess) e = cudaMalloc(&w.ws, ws);
-        if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&w.stage), sizeof(float) * (size_t)m_max);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&w.shared.side, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&w.shared.fork, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&w.shared.join, cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&w.res_dev), sizeof(dd_result_t));
         if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void**>(&w.res_host), sizeof(dd_result_t));
-        w.ws_bytes = ws;
     }
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -194,12 +360,17 @@ dd_status_t dd_engine_create(dd_engine_t* engine, int32_t workers, const dd_opti
     return DD_OK;
 }
 
+dd_status_t dd_engine_create(dd_engine_t* engine, int32_t workers, const dd_options_t* opt, int64_t m_max,
+                             int32_t n_max) {
+    return dd_engine_create_budget(engine, workers, opt, m_max, n_max, 0);
+}
+
 dd_status_t dd_engine_submit(dd_engine_t E, int64_t id, const float* T, int64_t m, int32_t n, int32_t flags) {
     if (!E || !T || (flags != DD_SERIES_DEVICE && flags != DD_SERIES_HOST)) return DD_EINVAL;
     {
         std::lock_guard<std::mutex> lk(E->mu);
         if (E->stopping) return DD_EBUSY;
-        E->queue.push_back(Request{id, T, m, n, flags, Clock::now()});
+        E->queue.push_back(Request{id, T, m, n, flags, Clock::now(), dd_plan_footprint(m, n, &E->opt), 0});
         E->outstanding++;
     }
     E->cv_work.notify_one();
@@ -245,13 +416,16 @@ void dd_engine_destroy(dd_engine_t E) {
         if (w.thread.joinable()) w.thread.join();
     for (Worker& w : E->workers) {
         if (w.stream) cudaStreamSynchronize(w.stream);
-        dd::destroy_plan(w.plan, false);
-        if (w.ws) cudaFree(w.ws);
-        if (w.stage) cudaFree(w.stage);
+        if (w.stream) E->release(w);
+        if (w.stream) cudaStreamSynchronize(w.stream);
         if (w.res_dev) cudaFree(w.res_dev);
         if (w.res_host) cudaFreeHost(w.res_host);
+        if (w.shared.side) cudaStreamDestroy(w.shared.side);
+        if (w.shared.fork) cudaEventDestroy(w.shared.fork);
+        if (w.shared.join) cudaEventDestroy(w.shared.join);
         if (w.stream) cudaStreamDestroy(w.stream);
     }
+    if (E->arena_base) cudaFree(E->arena_base);
     delete E;
 }
 

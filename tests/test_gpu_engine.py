@@ -93,3 +93,44 @@ def test_engine_destroy_with_queued_requests():
     for k in range(20):
         E.submit(T, 128, id=k)
     E.close()  # lets the running request finish and drops the queued ones
+
+
+def test_engine_budget_admission_and_bypass():
+    """Admission by device memory: the budget holds one plan of the large series at a time, so
+    the second large request waits for the first while small ones, queued behind it, pass it.
+    Every result equals its result alone."""
+    dd = _dd()
+    big = [synth.make_series(synth.SeriesSpec("rw", 1 << 18, 256, s, ("spike",)))[0] for s in (1, 2)]
+    small = [synth.make_series(synth.SeriesSpec("sine", 8192, 64, 10 + k, ("burst",)))[0] for k in range(6)]
+    fb = dd.Plan.footprint(1 << 18, 256, "tc_fp16")
+    fs = dd.Plan.footprint(8192, 64, "tc_fp16")
+    budget = fb + 4 * fs  # one large plan at a time, with room for small ones beside it
+    with dd.Engine(4, 1 << 18, 256, "tc_fp16", budget=budget) as E:
+        E.submit(torch.from_numpy(big[0]).cuda(), 256, id=100)
+        E.submit(torch.from_numpy(big[1]).cuda(), 256, id=101)
+        for k, T in enumerate(small):
+            E.submit(torch.from_numpy(T).cuda(), 64, id=k)
+        done = {c.id: c for c in E.drain()}
+    assert sorted(done) == list(range(6)) + [100, 101]
+    for k, T in enumerate(small):
+        a = _alone(dd, T, 64, "tc_fp16")
+        assert (done[k].result.index, done[k].result.nn_distance) == (a.index, a.nn_distance)
+    for k, T in enumerate(big):
+        a = _alone(dd, T, 256, "tc_fp16")
+        assert (done[100 + k].result.index, done[100 + k].result.nn_distance) == (a.index, a.nn_distance)
+    # the two large plans never held memory together: the second started after the first ended
+    first, second = sorted((done[100], done[101]), key=lambda c: c.queue_ms)
+    assert second.queue_ms >= first.queue_ms + first.service_ms - 1.0
+    # and a small request queued behind the second large one started before it
+    assert min(done[k].queue_ms for k in range(6)) < second.queue_ms
+
+
+def test_engine_rejects_what_never_fits():
+    dd = _dd()
+    T, _ = synth.make_series(synth.workload_small())
+    with dd.Engine(2, T.size, 128, "fp32", budget=dd.Plan.footprint(4096, 64) + 4 * 4096) as E:
+        E.submit(T, 128, id=1)                    # its plan alone exceeds the budget -> ENOMEM
+        E.submit(T[:4096].copy(), 64, id=2)       # fits
+        done = {c.id: c for c in E.drain()}
+    assert isinstance(done[1].result, dd.DDError) and done[1].result.status == 2
+    assert done[2].result.index == _alone(dd, T[:4096].copy(), 64, "fp32").index
