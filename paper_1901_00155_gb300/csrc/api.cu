@@ -111,7 +111,7 @@ size_t carve(dd_plan_s* p, char* base) {
         p->kpad = (p->n + 63) / 64 * 64;
         p->S16 = c.take<uint16_t>((size_t)N * p->kpad);
         p->A16 = c.take<uint16_t>((size_t)N * p->kpad);
-        p->coldat = c.take<float4>(N + 512);
+        p->coldat = c.take<float4>(N + 2 * dd::kTcColPad);
         p->rowmu = c.take<float>(N);
         p->rowc = c.take<float>(N);
         p->rowsc = c.take<float>(N);

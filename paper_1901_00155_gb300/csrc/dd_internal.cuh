@@ -31,6 +31,8 @@ constexpr int kDgPad = 2048 + 64;        // padding entries after the diagonal-r
 // Relative term beta of the Gram form's per-row bound F_i(D): 2 x 6 u32 (u32 = 2^-24,
 // safety factor 2) for the FP32 rounding of the epilogue's sum D.
 constexpr float kTcBeta = 12.0f * 5.9604644775390625e-08f;
+constexpr int kTcAtom = 64;      // Gram form: 16-bit operand elements per row chunk (one 128-byte line of S)
+constexpr int kTcColPad = 256;   // Gram form: per-column constants padded by one 256-column tile on each side
 
 // FP32 direct-difference tile kernel
 constexpr int kF32BM = 128;  // rows per tile

@@ -275,9 +275,12 @@ __global__ void __launch_bounds__(1024) k_norm_prefix(const double* __restrict__
 }
 
 // ---- Eq. 5 rows: mean and centred sum of squares from the prefix sums -------
+// Also each row's bin of the mean-bucketed order (below): its mean mu_i over
+// [min t^, max t^] in kMuBins equal bins.
 __global__ void __launch_bounds__(256) k_window_stats(const double* __restrict__ P1, const double* __restrict__ P2,
-                                                      int64_t N, int n, double inv_n, double* __restrict__ mu_w,
-                                                      double* __restrict__ c_w) {
+                                                      int64_t N, int n, double inv_n, const double* stats,
+                                                      double* __restrict__ mu_w, double* __restrict__ c_w,
+                                                      int32_t* __restrict__ bin) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     const double S1 = P1[i + n] - P1[i];
@@ -289,6 +292,9 @@ __global__ void __launch_bounds__(256) k_window_stats(const double* __restrict__
     if (c <= noise) c = 0.0;
     mu_w[i] = mu;
     c_w[i] = c;
+    const double b = floor((mu - stats[6]) * stats[9]);
+    // NaN (non-finite series) and out-of-range values land in the end bins
+    bin[i] = (b >= 0.0) ? (b < (double)kMuBins ? (int)b : kMuBins - 1) : 0;
 }
 
 // ---- Eq. 3 (PAA) + Eq. 4 (SAX letters) + Eq. 9 (word code) -----------------
@@ -362,16 +368,33 @@ __device__ __forceinline__ int64_t key_row(const KeySrc& k, int64_t e, int64_t N
 }
 __device__ __forceinline__ int key_of(const KeySrc& k, int64_t row) { return (k.keys[row] >> k.shift) & k.mask; }
 
+// Rows and keys of elements e0, e0 + step, ..., e0 + (G - 1) step, their loads
+// issued together (entries past N or past `lim` get row -1, key -1).
+template <int G>
+__device__ __forceinline__ void load_keys(const KeySrc& ks, int64_t e0, int64_t step, int64_t lim, int64_t N,
+                                          int64_t (&row)[G], int (&key)[G]) {
+#pragma unroll
+    for (int u = 0; u < G; u++) {
+        const int64_t e = e0 + u * step;
+        row[u] = e < lim && e < N ? key_row(ks, e, N) : -1;
+    }
+#pragma unroll
+    for (int u = 0; u < G; u++) key[u] = row[u] >= 0 ? key_of(ks, row[u]) : -1;
+}
+
 __global__ void __launch_bounds__(1024) k_word_hist(KeySrc ks, int64_t N, int D, int32_t* __restrict__ hist,
                                                     int32_t* __restrict__ blockcnt) {
     extern __shared__ int32_t sh_cnt[];
+    constexpr int G = kHistRows / 1024;  // elements per thread (blockDim.x == 1024)
+    const int64_t base = (int64_t)blockIdx.x * kHistRows;
+    int64_t row[G];
+    int key[G];
+    load_keys<G>(ks, base + threadIdx.x, 1024, base + kHistRows, N, row, key);
     for (int h = threadIdx.x; h < D; h += blockDim.x) sh_cnt[h] = 0;
     __syncthreads();
-    const int64_t base = (int64_t)blockIdx.x * kHistRows;
-    for (int r = threadIdx.x; r < kHistRows; r += blockDim.x) {
-        const int64_t e = base + r;
-        if (e < N) atomicAdd(&sh_cnt[key_of(ks, key_row(ks, e, N))], 1);
-    }
+#pragma unroll
+    for (int u = 0; u < G; u++)
+        if (key[u] >= 0) atomicAdd(&sh_cnt[key[u]], 1);
     __syncthreads();
     for (int h = threadIdx.x; h < D; h += blockDim.x) {
         int c = sh_cnt[h];
@@ -507,22 +530,28 @@ __global__ void __launch_bounds__(1024) k_word_plan(const int32_t* __restrict__ 
 
 // ---- Eq. 10: stable scatter of rows into word order ------------------------
 // Block b handles rows [b*kHistRows, (b+1)*kHistRows); warp w a contiguous
-// slice of it; ranks inside a round of 32 rows come from __match_any_sync.
-// Stable scatter: element e (in input order) of key h goes to position
-// (block base of h) + (rank of e among the block's elements of key h).
-__global__ void k_word_scatter(KeySrc ks, int64_t N, int D, const int32_t* __restrict__ blockbase,
+// slice of it, in rounds of 32 rows whose loads are issued 4 rounds at a time;
+// ranks inside a round come from __match_any_sync.  Stable scatter: element e
+// (in input order) of key h goes to position (block base of h) + (rank of e
+// among the block's elements of key h).
+__global__ void __launch_bounds__(1024, 2) k_word_scatter(KeySrc ks, int64_t N, int D, const int32_t* __restrict__ blockbase,
                                int32_t* __restrict__ order, int32_t* __restrict__ pos_of) {
     extern __shared__ int32_t sh_wc[];  // [nwarps][D]
+    constexpr int G = 4;
     const int nw = blockDim.x >> 5;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     for (int x = threadIdx.x; x < nw * D; x += blockDim.x) sh_wc[x] = 0;
     __syncthreads();
-    const int per = kHistRows / nw;
+    const int per = kHistRows / nw;  // a multiple of 32 G (nw <= 32 divides kHistRows)
     const int64_t base = (int64_t)blockIdx.x * kHistRows + (int64_t)wid * per;
     int32_t* wc = sh_wc + wid * D;
-    for (int r = lane; r < per; r += 32) {
-        const int64_t e = base + r;
-        if (e < N) atomicAdd(&wc[key_of(ks, key_row(ks, e, N))], 1);
+    for (int g0 = 0; g0 < per; g0 += 32 * G) {
+        int64_t row[G];
+        int key[G];
+        load_keys<G>(ks, base + g0 + lane, 32, base + per, N, row, key);
+#pragma unroll
+        for (int u = 0; u < G; u++)
+            if (key[u] >= 0) atomicAdd(&wc[key[u]], 1);
     }
     __syncthreads();
     for (int h = threadIdx.x; h < D; h += blockDim.x) {
@@ -535,38 +564,35 @@ __global__ void k_word_scatter(KeySrc ks, int64_t N, int D, const int32_t* __res
     }
     __syncthreads();
     const unsigned lt = (1u << lane) - 1u;
-    for (int r0 = 0; r0 < per; r0 += 32) {
-        const int64_t e = base + r0 + lane;
-        bool ok = (r0 + lane < per) && (e < N);
-        const int64_t i = ok ? key_row(ks, e, N) : 0;
-        int h = ok ? key_of(ks, i) : -1 - lane;  // unique dummy keys for idle lanes
-        unsigned peers = __match_any_sync(0xffffffffu, h);
-        int rank = __popc(peers & lt);
-        int b = ok ? wc[h] : 0;
-        __syncwarp();
-        if (ok) {
-            int pos = b + rank;
-            order[pos] = (int32_t)i;
-            if (pos_of) pos_of[i] = pos;
-            if (rank == 0) wc[h] = b + __popc(peers);
+    for (int g0 = 0; g0 < per; g0 += 32 * G) {
+        int64_t row[G];
+        int key[G];
+        load_keys<G>(ks, base + g0 + lane, 32, base + per, N, row, key);
+#pragma unroll
+        for (int u = 0; u < G; u++) {
+            const bool ok = key[u] >= 0;
+            const int h = ok ? key[u] : -1 - lane;  // unique dummy keys for idle lanes
+            const unsigned peers = __match_any_sync(0xffffffffu, h);
+            const int rank = __popc(peers & lt);
+            const int b = ok ? wc[h] : 0;
+            __syncwarp();
+            if (ok) {
+                const int pos = b + rank;
+                order[pos] = (int32_t)row[u];
+                if (pos_of) pos_of[row[u]] = pos;
+                if (rank == 0) wc[h] = b + __popc(peers);
+            }
+            __syncwarp();
         }
-        __syncwarp();
     }
 }
 
 // ---- mean-bucketed row order --------------------------------------------------
-// Rows binned by their mean mu_i over [min t^, max t^] (kMuBins equal bins).
-// For globally normalised subsequences d^2(i, j) >= n (mu_i - mu_j)^2, so the
-// rows whose distance to row i can be below R lie in the bins within
-// sqrt(R / n) of mu_i: a contiguous range of this order.
-__global__ void __launch_bounds__(256) k_mu_bins(const double* __restrict__ mu_w, int64_t N, const double* stats,
-                                                 int32_t* __restrict__ bin) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N) return;
-    const double b = floor((mu_w[i] - stats[6]) * stats[9]);
-    // NaN (non-finite series) and out-of-range values land in the end bins
-    bin[i] = (b >= 0.0) ? (b < (double)kMuBins ? (int)b : kMuBins - 1) : 0;
-}
+// Rows binned by their mean mu_i over [min t^, max t^] (kMuBins equal bins,
+// computed with the row statistics).  For globally normalised subsequences
+// d^2(i, j) >= n (mu_i - mu_j)^2, so the rows whose distance to row i can be
+// below R lie in the bins within sqrt(R / n) of mu_i: a contiguous range of
+// this order.
 
 // Warps per block of the stable scatter: per-warp counters for every word
 // must fit in shared memory (up to 192 KB), and the warps split the block's
@@ -597,7 +623,7 @@ cudaError_t launch_prep_common(dd_plan_s* p, const float* T, cudaStream_t s) {
     k_norm_scan_totals<<<1, 1024, 0, s>>>(p->bsum, nscan);
     k_norm_prefix<<<nscan, 1024, 0, s>>>(p->t64, m, p->bsum, nscan, p->P1, p->P2);
     const int gN = (int)((N + 255) / 256);
-    k_window_stats<<<gN, 256, 0, s>>>(p->P1, p->P2, N, n, 1.0 / (double)n, p->mu_w, p->c_w);
+    k_window_stats<<<gN, 256, 0, s>>>(p->P1, p->P2, N, n, 1.0 / (double)n, p->stats, p->mu_w, p->c_w, p->mubin);
     p->launches += 6;
     return cudaGetLastError();
 }
@@ -631,7 +657,6 @@ cudaError_t launch_prep_mean(dd_plan_s* p, cudaStream_t s) {
     // radix passes; the input follows a golden-ratio stride permutation, so the
     // rows of a bin are not in time order and neighbours in this order are
     // seldom overlapping subsequences
-    k_mu_bins<<<gN, 256, 0, s>>>(p->mu_w, N, p->stats, p->mubin);
     int32_t* tmp = p->list[3];
     const int nw64 = scatter_warps(64);
     for (int pass = 0; pass < 2; pass++) {
@@ -644,7 +669,7 @@ cudaError_t launch_prep_mean(dd_plan_s* p, cudaStream_t s) {
                                                                           pass == 0 ? nullptr : p->sigpos);
     }
     k_bin_bounds<<<gN, 256, 0, s>>>(p->sig, p->mubin, N, p->binstart);
-    p->launches += 8;
+    p->launches += 7;
     return cudaGetLastError();
 }
 

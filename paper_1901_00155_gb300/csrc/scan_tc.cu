@@ -40,7 +40,7 @@ namespace {
 
 constexpr int TBM = 128;
 constexpr int TBN = 256;
-constexpr int TKA = 64;  // 16-bit elements per 128-byte swizzle atom
+constexpr int TKA = kTcAtom;  // 16-bit elements per 128-byte swizzle atom
 constexpr int kABytesPerAtom = TBM * 128;  // 16 KB
 constexpr int kBBytesPerAtom = TBN * 128;  // 32 KB
 
@@ -56,7 +56,8 @@ constexpr int kEpiThreads = kEpiWarps * 32;
 constexpr int kTcThreadsV2 = 96 + kEpiThreads;  // scheduler, MMA, 8 epilogue warps, TMA producer
 
 constexpr int kColSlots = 4;
-constexpr int kColPad = TBN;  // padding of the per-column constant array on each side
+constexpr int kColPad = kTcColPad;  // padding of the per-column constant array on each side
+static_assert(kColPad == TBN, "the column constants are padded by one B tile");
 
 struct ItemDesc {
     int rt, pa, pb, dir, nct;  // nct < 0: no more items
@@ -566,171 +567,6 @@ __global__ void __launch_bounds__(kTcThreadsV2, 1)
     if (warp == 1) tmem_dealloc(tbase, 512);
 }
 
-// ---------------------------------------------------------------------------
-// Preparation for the Gram form.
-
-// Per row (orig order) and per column (mean-bucketed order): sqrt(n) mu_i,
-// c_i (FP32), sqrt(c_i) rounded up; maxima over all rows.
-__global__ void __launch_bounds__(256) k_tc_rowconst(const double* __restrict__ mu_w, const double* __restrict__ c_w,
-                                                     const int32_t* __restrict__ sigpos, int64_t N, double sqrt_n,
-                                                     float4* __restrict__ coldat,
-                                                     float* __restrict__ rowmu, float* __restrict__ rowc,
-                                                     float* __restrict__ rowsc, Ctrl* ctrl) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    float sc = 0.f, cc = 0.f, am = 0.f;
-    if (i < N) {
-        const float mu = (float)(mu_w[i] * sqrt_n);
-        const float c = (float)c_w[i];
-        cc = __double2float_ru(c_w[i]);
-        sc = __fsqrt_ru(cc);
-        am = fabsf(mu);
-        const int p = sigpos[i];
-        coldat[kColPad + p] = make_float4(mu, c, __int_as_float((int)i), 0.f);
-        rowmu[i] = mu;
-        rowc[i] = c;
-        rowsc[i] = sc;
-    }
-    // non-negative floats order like their bit patterns; one atomic per block
-    __shared__ unsigned red[3][8];
-    const unsigned bsc = __reduce_max_sync(0xffffffffu, __float_as_uint(sc));
-    const unsigned bcc = __reduce_max_sync(0xffffffffu, __float_as_uint(cc));
-    const unsigned bam = __reduce_max_sync(0xffffffffu, __float_as_uint(am));
-    if ((threadIdx.x & 31) == 0) {
-        red[0][threadIdx.x >> 5] = bsc;
-        red[1][threadIdx.x >> 5] = bcc;
-        red[2][threadIdx.x >> 5] = bam;
-    }
-    __syncthreads();
-    if (threadIdx.x < 3) {
-        unsigned v = 0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); w++) v = max(v, red[threadIdx.x][w]);
-        unsigned int* dst = threadIdx.x == 0 ? &ctrl->tc_scmax : (threadIdx.x == 1 ? &ctrl->tc_cmax : &ctrl->tc_mumax);
-        atomicMax(dst, v);
-    }
-}
-
-// Per-row error bound F_i(D) = alpha_i + beta D + gam_i sqrt(D + q2_i) on
-// |D - d^2| for a distance D computed by the Gram tiles (safety factor 2):
-//   operands rounded to u_in (FP16 2^-11, BF16 2^-8), products exact in FP32,
-//   accumulation of n terms with unit 2^-23 (directed rounding allowed):
-//     |g~ - g| <= ((2 u_in + u_in^2) + gamma_n (1 + u_in)^2) sum|x'y'|,
-//     sum|x'y'| <= sqrt(c_i) sqrt(c_j) <= sc_i sc_max = Q_i;
-//   subnormal operands add <= 2^-25 / s per element (scale s);
-//   FP32 rounding of c~, sqrt(n) mu~, the epilogue FMAs and the final sum is
-//   bounded through dm^2 <= D + 2 Q_i and |dm| <= sqrt(D + 2 Q_i).
-__global__ void __launch_bounds__(256) k_tc_rowbound(const float* __restrict__ rowsc, const float* __restrict__ rowc,
-                                                     const float* __restrict__ rowmu, int64_t N, float sqrt_n,
-                                                     float u_in, const double* stats, const double* P2end,
-                                                     const Ctrl* ctrl, float* __restrict__ alpha,
-                                                     float* __restrict__ gam, float* __restrict__ q2) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N) return;
-    const float u32 = 5.9604644775390625e-08f;   // 2^-24
-    const float uacc = 2.384185791015625e-07f;   // 2^-22: allows truncating accumulation
-    const float n = sqrt_n * sqrt_n;
-    const float scmax = __uint_as_float(ctrl->tc_scmax);
-    const float cmax = __uint_as_float(ctrl->tc_cmax);
-    const float mumax = __uint_as_float(ctrl->tc_mumax);
-    const float s = (float)stats[3];
-    const float maxabs = (float)stats[2];
-    const float gn = n * uacc / (1.f - n * uacc);
-    const float uo = u_in + 2.f * u32;  // operand: FP32 centring then one 16-bit rounding
-    const float Kg = 2.f * ((2.f * uo + uo * uo) + gn * (1.f + uo) * (1.f + uo));
-    const float sci = rowsc[i];
-    const float Q = sci * scmax;
-    const float ci = rowc[i];
-    // absolute operand errors: FP32 centring (2.01 u32 max|t^|) and 16-bit subnormals (2^-25 / s)
-    const float ea = 2.01f * u32 * maxabs + 2.9802322387695312e-08f / s;
-    const float eta = 2.f * (ea * sqrt_n * (sci + scmax) + n * ea * ea);
-    const float ec = 512.f * 1.1102230246251565e-16f * (1.f + (float)*P2end);
-    const float A0 = Kg * Q + eta + 4.f * u32 * (ci + cmax) + 2.f * ec + 8.f * u32 * Q;
-    const float G0 = 2.f * u32 * (fabsf(rowmu[i]) + mumax);
-    alpha[i] = 2.002f * A0;
-    gam[i] = 2.002f * G0;
-    q2[i] = 2.002f * Q;
-}
-
-__device__ __forceinline__ __half to16(float x, __half*) { return __float2half_rn(x); }
-__device__ __forceinline__ __nv_bfloat16 to16(float x, __nv_bfloat16*) { return __float2bfloat16_rn(x); }
-
-// Centred rows in the mean-bucketed order: S[p][k] = s (t^_{i+k} - mu_i),
-// i = sig[p], computed in FP32 from the FP32 copy of t^ and rounded once to
-// FP16 / BF16; zero for k in [n, kpad).  (The FP32 centring error, at most
-// 2 u32 max|t^| per element, is part of the row bound.)
-template <typename T16>
-__global__ void __launch_bounds__(256) k_build_S(const float* __restrict__ t32, const double* __restrict__ mu_w,
-                                                 const int32_t* __restrict__ sig, int64_t N, int n, int kpad,
-                                                 const double* stats, T16* __restrict__ S) {
-    // one warp per 4 rows (their loads are issued together)
-    constexpr int R = 4;
-    const int64_t p0 = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * R;
-    if (p0 >= N) return;
-    const int lane = threadIdx.x & 31;
-    const float s = (float)stats[3];
-    int ii[R];
-    float mu[R];
-#pragma unroll
-    for (int r = 0; r < R; r++) {
-        const int64_t p = p0 + r < N ? p0 + r : N - 1;
-        ii[r] = sig[p];
-    }
-    // one FP64 -> FP32 conversion per row (FP64 throughput is low on this GPU)
-    const float mu_l = lane < R ? (float)mu_w[ii[lane < R ? lane : 0]] : 0.f;
-#pragma unroll
-    for (int r = 0; r < R; r++) mu[r] = __shfl_sync(0xffffffffu, mu_l, r);
-    // lane l writes elements 2l, 2l+1 of every 64-element chunk (4-byte stores)
-    for (int k = 2 * lane; k < kpad; k += 64) {
-        float x0[R], x1[R];
-#pragma unroll
-        for (int r = 0; r < R; r++) {
-            x0[r] = k < n ? t32[ii[r] + k] : 0.f;
-            x1[r] = k + 1 < n ? t32[ii[r] + k + 1] : 0.f;
-        }
-#pragma unroll
-        for (int r = 0; r < R; r++) {
-            if (p0 + r >= N) break;
-            const float y0 = k < n ? (x0[r] - mu[r]) * s : 0.f;
-            const float y1 = k + 1 < n ? (x1[r] - mu[r]) * s : 0.f;
-            T16 v[2] = {to16(y0, (T16*)nullptr), to16(y1, (T16*)nullptr)};
-            *reinterpret_cast<uint32_t*>(S + ((int64_t)(k >> 6) * N + p0 + r) * TKA + (k & (TKA - 1))) =
-                *reinterpret_cast<uint32_t*>(v);
-        }
-    }
-}
-
-// Operand scale: a power of two that puts max |x'| <= 2 max|t^| near 2^14 (FP16).
-__global__ void k_tc_scale(double* stats, int is_bf16) {
-    if (threadIdx.x != 0) return;
-    double s = 1.0;
-    if (!is_bf16) {
-        const double mx = 2.0 * stats[2];
-        if (mx > 0.0) {
-            int e = (int)floor(log2(16384.0 / mx));
-            if (e > 24) e = 24;
-            if (e < -24) e = -24;
-            s = ldexp(1.0, e);
-        }
-    }
-    stats[3] = s;
-}
-
-// Packs the operand rows of a list (in list order) for TMA.
-__global__ void __launch_bounds__(256) k_gather_rows(ListRef L, const int32_t* __restrict__ sigpos,
-                                                     const uint4* __restrict__ S, int kpad, int64_t N,
-                                                     uint4* __restrict__ P) {
-    const int cnt = *L.cnt_dev;
-    const int off = L.off_dev ? *L.off_dev : 0;
-    const int per_row = kpad / 8;  // uint4 per row (8 per 64-element chunk)
-    const int64_t total = (int64_t)cnt * per_row;
-    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t r = g / per_row;
-        const int c = (int)(g % per_row);
-        const int i = L.base[off + r];
-        const int64_t plane = (int64_t)(c >> 3) * N;  // chunk-major: [chunk][row][8 uint4]
-        P[(plane + r) * 8 + (c & 7)] = S[(plane + sigpos[i]) * 8 + (c & 7)];
-    }
-}
-
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
@@ -797,36 +633,6 @@ cudaError_t tc_make_maps(dd_plan_s* p) {
     if (!make_map(&p->mapS_B, p->S16, p->N, p->kpad, TBN, bf16)) return cudaErrorInvalidValue;
     if (!make_map(&p->mapP_A, p->A16, p->N, p->kpad, TBM, bf16)) return cudaErrorInvalidValue;
     return cudaSuccess;
-}
-
-cudaError_t launch_tc_prep(dd_plan_s* p, cudaStream_t s) {
-    const int64_t N = p->N;
-    const int n = p->n;
-    const bool bf16 = p->opt.precision == DD_TC_BF16;
-    const int gN = (int)((N + 255) / 256);
-    k_tc_scale<<<1, 32, 0, s>>>(p->stats, bf16 ? 1 : 0);
-    k_tc_rowconst<<<gN, 256, 0, s>>>(p->mu_w, p->c_w, p->sigpos, N, std::sqrt((double)n), p->coldat, p->rowmu,
-                                     p->rowc, p->rowsc, p->ctrl);
-    const float u_in = bf16 ? 0.00390625f : 0.00048828125f;
-    k_tc_rowbound<<<gN, 256, 0, s>>>(p->rowsc, p->rowc, p->rowmu, N, (float)std::sqrt((double)n), u_in, p->stats,
-                                     p->P2 + p->m, p->ctrl, p->alpha, p->gam, p->q2);
-    const int g = (int)((N + 31) / 32);  // 8 warps x 4 rows per block
-    if (bf16)
-        k_build_S<__nv_bfloat16><<<g, 256, 0, s>>>(p->t32, p->mu_w, p->sig, N, n, p->kpad, p->stats,
-                                                   reinterpret_cast<__nv_bfloat16*>(p->S16));
-    else
-        k_build_S<__half><<<g, 256, 0, s>>>(p->t32, p->mu_w, p->sig, N, n, p->kpad, p->stats,
-                                            reinterpret_cast<__half*>(p->S16));
-    p->launches += 4;
-    return cudaGetLastError();
-}
-
-cudaError_t launch_gather_rows(dd_plan_s* p, ListRef L, cudaStream_t s) {
-    const int g = p->sm_count * 4;
-    k_gather_rows<<<g, 256, 0, s>>>(L, p->sigpos, reinterpret_cast<const uint4*>(p->S16), p->kpad, p->N,
-                                    reinterpret_cast<uint4*>(p->A16));
-    p->launches++;
-    return cudaGetLastError();
 }
 
 cudaError_t launch_scan_tc(dd_plan_s* p, const TcArgs& a, bool a_packed, cudaStream_t s) {

@@ -50,6 +50,56 @@ __device__ __forceinline__ bool is_alive(const TcBound& b, int i, uint32_t rbits
     return !(D + (b.alpha[i] + b.beta * D + b.gam[i] * sqrtf(fmaxf(D, 0.f) + b.q2[i])) < B);
 }
 
+// is_alive (and the rank test against thr) for U rows at once: every load of
+// the U rows is issued before any of them is used, so a thread waits on one
+// memory latency per step instead of one per row.  Entries i < 0 are not rows
+// (false).  The decisions are the ones is_alive and rank_bits make; rank gets
+// the rank values.
+template <int U>
+__device__ __forceinline__ void alive_batch(const TcBound& b, const int (&iv)[U], const uint32_t* __restrict__ rmin,
+                                            uint32_t bsf_bits, uint32_t thr, bool (&keep)[U], uint32_t (&rank)[U]) {
+    uint32_t rb[U], r32[U];
+    bool ex[U];
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+        const int i = iv[u];
+        rb[u] = i >= 0 ? rmin[i] : 0u;
+        r32[u] = i >= 0 && b.r32 ? b.r32[i] : 0xffffffffu;
+        ex[u] = i >= 0 && b.excl ? b.excl[i] != 0 : false;
+    }
+    const float B = __uint_as_float(bsf_bits);
+    int st[U];  // 0: not alive, 1: alive, 2: decided by the bound F_i
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+        int v;
+        if (iv[u] < 0 || ex[u]) v = 0;
+        else if (!b.on) v = rb[u] >= bsf_bits;
+        else if (bsf_bits == 0) v = 1;
+        else if (b.r32 && __uint_as_float(r32[u]) < B) v = 0;
+        else v = __uint_as_float(rb[u]) < B ? 2 : 1;
+        st[u] = v;
+    }
+    float al[U], ga[U], q2[U];
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+        const bool need = st[u] == 2;
+        al[u] = need ? b.alpha[iv[u]] : 0.f;
+        ga[u] = need ? b.gam[iv[u]] : 0.f;
+        q2[u] = need ? b.q2[iv[u]] : 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+        bool a = st[u] == 1;
+        if (st[u] == 2) {
+            const float D = __uint_as_float(rb[u]);
+            a = !(D + (al[u] + b.beta * D + ga[u] * sqrtf(fmaxf(D, 0.f) + q2[u])) < B);
+        }
+        // rank value: min(rmin, r32) (r32 reads as all ones where there is none)
+        rank[u] = min(rb[u], r32[u]);
+        keep[u] = a && rank[u] >= thr;
+    }
+}
+
 // Order-preserving compaction of a row list in one pass (decoupled look-back).
 // Predicates: pred 0: alive against the best-so-far; pred 1: alive and rank
 // value >= the top-k threshold; pred 2: member of Cand; pred 3: alive with no
@@ -59,9 +109,10 @@ __device__ __forceinline__ bool is_alive(const TcBound& b, int i, uint32_t rbits
 //
 // Block b (a ticket taken at start, so every lower block has started) keeps
 // entries [2048 b, 2048 b + 2048) in 8 coalesced rounds of 256 (thread t holds
-// entry 256 q + t of round q); ranks come from warp ballots.  Warp 0 publishes
+// entry 256 q + t of round q, the rounds' loads issued together); ranks come
+// from warp ballots.  Warp 0 publishes
 // the block's count, then looks back over the status words of the blocks
-// before it, 32 at a time, adding counts up to the nearest one that holds an
+// before it, 128 at a time, adding counts up to the nearest one that holds an
 // inclusive prefix, and publishes its own inclusive prefix; the block then
 // scatters its entries from there.  A status word is (flag << 62) | count:
 // flag 1 = the block's own count, 2 = the inclusive prefix.  The block holding
@@ -76,7 +127,7 @@ __device__ __forceinline__ unsigned long long gtimer() {
     return t;
 }
 
-__global__ void __launch_bounds__(256) k_compact(ListRef in, const uint32_t* __restrict__ rmin, TcBound tb,
+__global__ void __launch_bounds__(256, 4) k_compact(ListRef in, const uint32_t* __restrict__ rmin, TcBound tb,
                                                  Ctrl* ctrl, int pred, const int32_t* __restrict__ code,
                                                  const int32_t* __restrict__ hist, int phase1_max,
                                                  const int32_t* __restrict__ sigpos, int p_lo, int p_hi, int site,
@@ -95,26 +146,39 @@ __global__ void __launch_bounds__(256) k_compact(ListRef in, const uint32_t* __r
     const uint32_t thr = pred == 1 ? ctrl->topk_thr : (pred == 3 ? 0x7f000000u : 0u);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const unsigned lt = (1u << lane) - 1u;
+    // the block's entries: 8 independent coalesced loads per thread
     int i8[8];
-    unsigned bal[8];
 #pragma unroll
     for (int q = 0; q < 8; q++) {
         const int r = b * kCompactRows + q * 256 + threadIdx.x;
-        bool k = false;
-        i8[q] = -1;
-        if (r < cnt) {
-            const int i = in.base[off + r];
-            if (pred == 2) {
-                // Cand (Eq. 7): rows whose word has the smallest frequency
-                k = hist[code[i]] == ctrl->fmin && ctrl->ncand <= phase1_max;
-            } else {
-                k = is_alive(tb, i, rmin[i], bsf) && rank_bits(tb, i, rmin[i]) >= thr;
-            }
-            // sigpos: keep only rows at positions [p_lo, p_hi) of the mean order (a shard)
-            if (sigpos) k = k && sigpos[i] >= p_lo && sigpos[i] < p_hi;
-            i8[q] = i;
-        }
-        bal[q] = __ballot_sync(0xffffffffu, k);
+        i8[q] = r < cnt ? in.base[off + r] : -1;
+    }
+    bool k8[8];
+    if (pred == 2) {
+        // Cand (Eq. 7): rows whose word has the smallest frequency
+        const bool on = ctrl->ncand <= phase1_max;
+        const int fmin = ctrl->fmin;
+        int c8[8];
+#pragma unroll
+        for (int q = 0; q < 8; q++) c8[q] = i8[q] >= 0 ? code[i8[q]] : 0;
+#pragma unroll
+        for (int q = 0; q < 8; q++) k8[q] = on && i8[q] >= 0 && hist[c8[q]] == fmin;
+    } else {
+        uint32_t rk[8];
+        alive_batch<8>(tb, i8, rmin, bsf, thr, k8, rk);
+    }
+    if (sigpos) {
+        // keep only rows at positions [p_lo, p_hi) of the mean order (a shard)
+        int s8[8];
+#pragma unroll
+        for (int q = 0; q < 8; q++) s8[q] = i8[q] >= 0 ? sigpos[i8[q]] : -1;
+#pragma unroll
+        for (int q = 0; q < 8; q++) k8[q] = k8[q] && s8[q] >= p_lo && s8[q] < p_hi;
+    }
+    unsigned bal[8];
+#pragma unroll
+    for (int q = 0; q < 8; q++) {
+        bal[q] = __ballot_sync(0xffffffffu, k8[q]);
         if (lane == 0) wcnt[q][wid] = __popc(bal[q]);
     }
     __syncthreads();
@@ -133,14 +197,29 @@ __global__ void __launch_bounds__(256) k_compact(ListRef in, const uint32_t* __r
             unsigned long long t0 = 0;
             bool ok = true;
             for (uint32_t it = 0; ok; ++it) {
-                const int jj = j - lane;
-                const unsigned long long v =
-                    jj >= 0 ? *(volatile const unsigned long long*)(status + jj) : kStPre;  // before block 0: 0
-                const unsigned pre = __ballot_sync(0xffffffffu, (v & kStPre) != 0);
-                const unsigned ready = __ballot_sync(0xffffffffu, (v & (kStPre | kStAgg)) != 0);
-                const int fp = pre ? __ffs(pre) - 1 : 32;  // nearest predecessor with an inclusive prefix
-                const unsigned need = fp < 32 ? ((2u << fp) - 1u) : 0xffffffffu;
-                if ((ready & need) != need) {  // a predecessor in the window has not published: wait
+                // a window of the 128 nearest predecessors not yet added:
+                // position w = 32 k + lane is block j - w
+                unsigned long long v[4];
+#pragma unroll
+                for (int k = 0; k < 4; k++) {
+                    const int jj = j - (32 * k + lane);
+                    v[k] = jj >= 0 ? *(volatile const unsigned long long*)(status + jj) : kStPre;  // before block 0: 0
+                }
+                int fp = 128;  // nearest position holding an inclusive prefix
+                bool wait = false;
+#pragma unroll
+                for (int k = 3; k >= 0; k--) {
+                    const unsigned pre = __ballot_sync(0xffffffffu, (v[k] & kStPre) != 0);
+                    if (pre) fp = 32 * k + __ffs(pre) - 1;
+                }
+#pragma unroll
+                for (int k = 0; k < 4; k++) {
+                    const unsigned ready = __ballot_sync(0xffffffffu, (v[k] & (kStPre | kStAgg)) != 0);
+                    const int top = fp - 32 * k;  // positions 32 k .. 32 k + top of this word are needed
+                    const unsigned need = top >= 31 ? 0xffffffffu : (top >= 0 ? (2u << top) - 1u : 0u);
+                    wait = wait || (ready & need) != need;
+                }
+                if (wait) {  // a predecessor in the window has not published
                     if ((it & 63u) == 0u) {
                         // lane 0's clock decides for the whole warp (the loop stays warp-uniform)
                         const unsigned long long t = __shfl_sync(0xffffffffu, gtimer(), 0);
@@ -152,11 +231,16 @@ __global__ void __launch_bounds__(256) k_compact(ListRef in, const uint32_t* __r
                     }
                     continue;
                 }
-                int val = lane <= fp && jj >= 0 ? (int)(unsigned)(v & 0xffffffffull) : 0;
+                int val = 0;
+#pragma unroll
+                for (int k = 0; k < 4; k++) {
+                    const int w = 32 * k + lane;
+                    val += w <= fp && j - w >= 0 ? (int)(unsigned)(v[k] & 0xffffffffull) : 0;
+                }
                 val = __reduce_add_sync(0xffffffffu, val);
                 prefix += val;
-                if (fp < 32) break;
-                j -= 32;
+                if (fp < 128) break;
+                j -= 128;
             }
             if (lane == 0) atomicExch(status + b, kStPre | (unsigned long long)(unsigned)(prefix + total));
         }
@@ -192,14 +276,25 @@ __global__ void __launch_bounds__(256) k_topk_hist(ListRef in, const uint32_t* _
     const uint32_t bsf = ctrl->bsf;
     const int sel = pass == 0 ? 0 : ctrl->topk_bin;
     if (sel >= 0) {
-        for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < cnt; r += gridDim.x * blockDim.x) {
-            const int i = in.base[off + r];
-            if (!is_alive(tb, i, rmin[i], bsf)) continue;
-            const uint32_t b = rank_bits(tb, i, rmin[i]);
-            if (pass == 0)
-                atomicAdd(&h[b >> 19], 1);
-            else if ((int)(b >> 19) == sel)
-                atomicAdd(&h[(b >> 7) & (kTopkBins - 1)], 1);
+        // 4 rows per thread and step, their loads issued together
+        constexpr int U = 4;
+        const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+        for (int64_t r0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r0 < cnt; r0 += U * stride) {
+            int iv[U];
+#pragma unroll
+            for (int u = 0; u < U; u++) iv[u] = r0 + u * stride < cnt ? in.base[off + r0 + u * stride] : -1;
+            bool ok[U];
+            uint32_t rk[U];
+            alive_batch<U>(tb, iv, rmin, bsf, 0u, ok, rk);
+#pragma unroll
+            for (int u = 0; u < U; u++) {
+                if (!ok[u]) continue;
+                const uint32_t b = rk[u];
+                if (pass == 0)
+                    atomicAdd(&h[b >> 19], 1);
+                else if ((int)(b >> 19) == sel)
+                    atomicAdd(&h[(b >> 7) & (kTopkBins - 1)], 1);
+            }
         }
     }
     __syncthreads();
