@@ -435,36 +435,47 @@ __global__ void __launch_bounds__(32 * kColChunks) k_colscan(int32_t* __restrict
     colscan_cols(blockcnt, D, nblk, h, c, hl, h < D ? start[h] : 0, sh);
 }
 
-// Plan of one 64-bin radix pass: bin offsets (exclusive scan of the
-// histogram) and the block bases of every bin.  Two blocks of 32 bins.
-__global__ void __launch_bounds__(32 * kColChunks) k_radix_plan(const int32_t* __restrict__ hist,
-                                                                int32_t* __restrict__ blockcnt, int nblk) {
-    __shared__ int sh[kColChunks][32];
-    __shared__ int st[64];
-    if (threadIdx.y == 0 && threadIdx.x == 0) {
-        int run = 0;
-        for (int b = 0; b < 64; b++) {
-            st[b] = run;
-            run += hist[b];
+// Bin offsets of the mean-bucketed order: binstart[b] = the number of rows in
+// bins below b (exclusive scan of the histogram), so binstart[b] is the first
+// position whose row lies in bin >= b; binstart[kMuBins] = N.  One block of
+// 1024 threads, 4 bins each.
+__global__ void __launch_bounds__(1024) k_bin_start(const int32_t* __restrict__ hist, int64_t N,
+                                                   int32_t* __restrict__ binstart) {
+    __shared__ int part[32];
+    constexpr int kPer = kMuBins / 1024;
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    int c[kPer], s = 0;
+#pragma unroll
+    for (int q = 0; q < kPer; q++) {
+        c[q] = hist[kPer * t + q];
+        s += c[q];
+    }
+    int incl = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += u;
+    }
+    if (lane == 31) part[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        const int v = part[lane];
+        int cc = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int u = __shfl_up_sync(0xffffffffu, cc, o);
+            if (lane >= o) cc += u;
         }
+        part[lane] = cc - v;
     }
     __syncthreads();
-    const int hl = threadIdx.x, c = threadIdx.y;
-    const int h = blockIdx.x * 32 + hl;
-    colscan_cols(blockcnt, 64, nblk, h, c, hl, st[h], sh);
-}
-
-// Bin offsets of the sorted mean order: binstart[b] = first position whose
-// row lies in bin >= b (binstart[kMuBins] = N).
-__global__ void __launch_bounds__(256) k_bin_bounds(const int32_t* __restrict__ sig, const int32_t* __restrict__ mubin,
-                                                    int64_t N, int32_t* __restrict__ binstart) {
-    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= N) return;
-    const int b1 = min(max(mubin[sig[p]], 0), kMuBins - 1);
-    const int b0 = p > 0 ? min(max(mubin[sig[p - 1]], 0), kMuBins - 1) : -1;
-    for (int b = b0 + 1; b <= b1; b++) binstart[b] = (int32_t)p;
-    if (p == N - 1)
-        for (int b = b1 + 1; b <= kMuBins; b++) binstart[b] = (int32_t)N;
+    int run = part[wid] + incl - s;
+#pragma unroll
+    for (int q = 0; q < kPer; q++) {
+        binstart[kPer * t + q] = run;
+        run += c[q];
+    }
+    if (t == 0) binstart[kMuBins] = (int32_t)N;
 }
 
 // ---- Eq. 7 / Eq. 10 plan: words ordered by (frequency, word), offsets,
@@ -533,54 +544,69 @@ __global__ void __launch_bounds__(1024) k_word_plan(const int32_t* __restrict__ 
 // slice of it, in rounds of 32 rows whose loads are issued 4 rounds at a time;
 // ranks inside a round come from __match_any_sync.  Stable scatter: element e
 // (in input order) of key h goes to position (block base of h) + (rank of e
-// among the block's elements of key h).
-__global__ void __launch_bounds__(1024, 2) k_word_scatter(KeySrc ks, int64_t N, int D, const int32_t* __restrict__ blockbase,
-                               int32_t* __restrict__ order, int32_t* __restrict__ pos_of) {
-    extern __shared__ int32_t sh_wc[];  // [nwarps][D]
+// among the block's elements of key h).  The per-warp counters hold
+// block-local positions in 16 bits (a block has kHistRows < 2^16 rows), two
+// keys to a word, so that several blocks fit on an SM for large key ranges;
+// the block base of a key is added when a row is placed.
+__device__ __forceinline__ int get16(const uint32_t* w, int h) {
+    return (int)((w[h >> 1] >> ((h & 1) * 16)) & 0xffffu);
+}
+
+__global__ void __launch_bounds__(1024, 2) k_word_scatter(KeySrc ks, int64_t N, int D,
+                                                          const int32_t* __restrict__ blockbase,
+                                                          int32_t* __restrict__ order, int32_t* __restrict__ pos_of) {
+    extern __shared__ uint32_t sh_wc[];  // [nwarps][ceil(D / 2)], 16-bit counters
     constexpr int G = 4;
     const int nw = blockDim.x >> 5;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    for (int x = threadIdx.x; x < nw * D; x += blockDim.x) sh_wc[x] = 0;
+    const int D2 = (D + 1) >> 1;
+    for (int x = threadIdx.x; x < nw * D2; x += blockDim.x) sh_wc[x] = 0u;
     __syncthreads();
     const int per = kHistRows / nw;  // a multiple of 32 G (nw <= 32 divides kHistRows)
     const int64_t base = (int64_t)blockIdx.x * kHistRows + (int64_t)wid * per;
-    int32_t* wc = sh_wc + wid * D;
+    uint32_t* wc = sh_wc + wid * D2;
     for (int g0 = 0; g0 < per; g0 += 32 * G) {
         int64_t row[G];
         int key[G];
         load_keys<G>(ks, base + g0 + lane, 32, base + per, N, row, key);
 #pragma unroll
         for (int u = 0; u < G; u++)
-            if (key[u] >= 0) atomicAdd(&wc[key[u]], 1);
+            if (key[u] >= 0) atomicAdd(&wc[key[u] >> 1], 1u << ((key[u] & 1) * 16));
     }
     __syncthreads();
-    for (int h = threadIdx.x; h < D; h += blockDim.x) {
-        int run = blockbase[(int64_t)blockIdx.x * D + h];
+    // per key, exclusive scan over the warps (both halves of a word at once:
+    // neither half can carry into the other)
+    for (int h2 = threadIdx.x; h2 < D2; h2 += blockDim.x) {
+        uint32_t run = 0u;
         for (int q = 0; q < nw; q++) {
-            int c = sh_wc[q * D + h];
-            sh_wc[q * D + h] = run;
+            const uint32_t c = sh_wc[q * D2 + h2];
+            sh_wc[q * D2 + h2] = run;
             run += c;
         }
     }
     __syncthreads();
     const unsigned lt = (1u << lane) - 1u;
+    const int64_t bb = (int64_t)blockIdx.x * D;
     for (int g0 = 0; g0 < per; g0 += 32 * G) {
         int64_t row[G];
         int key[G];
         load_keys<G>(ks, base + g0 + lane, 32, base + per, N, row, key);
+        int kb[G];  // block base of each key
+#pragma unroll
+        for (int u = 0; u < G; u++) kb[u] = key[u] >= 0 ? blockbase[bb + key[u]] : 0;
 #pragma unroll
         for (int u = 0; u < G; u++) {
             const bool ok = key[u] >= 0;
             const int h = ok ? key[u] : -1 - lane;  // unique dummy keys for idle lanes
             const unsigned peers = __match_any_sync(0xffffffffu, h);
             const int rank = __popc(peers & lt);
-            const int b = ok ? wc[h] : 0;
+            const int loc = ok ? get16(wc, h) : 0;
             __syncwarp();
             if (ok) {
-                const int pos = b + rank;
+                const int pos = kb[u] + loc + rank;
                 order[pos] = (int32_t)row[u];
                 if (pos_of) pos_of[row[u]] = pos;
-                if (rank == 0) wc[h] = b + __popc(peers);
+                if (rank == 0) atomicAdd(&wc[h >> 1], (uint32_t)__popc(peers) << ((h & 1) * 16));
             }
             __syncwarp();
         }
@@ -594,11 +620,11 @@ __global__ void __launch_bounds__(1024, 2) k_word_scatter(KeySrc ks, int64_t N, 
 // below R lie in the bins within sqrt(R / n) of mu_i: a contiguous range of
 // this order.
 
-// Warps per block of the stable scatter: per-warp counters for every word
-// must fit in shared memory (up to 192 KB), and the warps split the block's
-// rows evenly.
+// Warps per block of the stable scatter: per-warp 16-bit counters for every
+// key fit in 64 KB of shared memory, and the warps split the block's rows
+// evenly.
 int scatter_warps(int D) {
-    int nw = (192 * 1024 / 4) / D;
+    int nw = (64 * 1024 / 4) / ((D + 1) / 2);  // at most 64 KB of counters: several blocks per SM
     if (nw > 32) nw = 32;
     if (nw < 1) nw = 1;
     while (kHistRows % nw) nw--;
@@ -643,7 +669,8 @@ cudaError_t launch_prep_words(dd_plan_s* p, cudaStream_t s) {
     k_word_plan<<<1, 1024, 0, s>>>(p->hist, D, nh, p->blockcnt, p->word_start, p->opt.phase1_max, N, p->ctrl);
     k_colscan<<<(D + 31) / 32, dim3(32, kColChunks), 0, s>>>(p->blockcnt, D, nh, p->word_start);
     int nw = scatter_warps(D);
-    k_word_scatter<<<nh, nw * 32, sizeof(int32_t) * nw * D, s>>>(words, N, D, p->blockcnt, p->order, p->pos_of);
+    k_word_scatter<<<nh, nw * 32, sizeof(uint32_t) * nw * ((D + 1) / 2), s>>>(words, N, D, p->blockcnt, p->order,
+                                                                            p->pos_of);
     p->launches += 5;
     return cudaGetLastError();
 }
@@ -651,25 +678,20 @@ cudaError_t launch_prep_words(dd_plan_s* p, cudaStream_t s) {
 // Part 3: the mean-bucketed order and its bin offsets.
 cudaError_t launch_prep_mean(dd_plan_s* p, cudaStream_t s) {
     const int64_t N = p->N;
-    const int gN = (int)((N + 255) / 256);
     const int nh = (int)((N + kHistRows - 1) / kHistRows);
-    // mean-bucketed order (sig): rows sorted by mean bin with two stable 64-bin
-    // radix passes; the input follows a golden-ratio stride permutation, so the
-    // rows of a bin are not in time order and neighbours in this order are
-    // seldom overlapping subsequences
-    int32_t* tmp = p->list[3];
-    const int nw64 = scatter_warps(64);
-    for (int pass = 0; pass < 2; pass++) {
-        const KeySrc ks{p->mubin, pass == 0 ? nullptr : tmp, pass == 0 ? p->mu_stride : 0, 6 * pass, 63};
-        cudaMemsetAsync(p->hist_mu, 0, sizeof(int32_t) * 64, s);
-        k_word_hist<<<nh, 1024, sizeof(int32_t) * 64, s>>>(ks, N, 64, p->hist_mu, p->blockcnt_mu);
-        k_radix_plan<<<2, dim3(32, kColChunks), 0, s>>>(p->hist_mu, p->blockcnt_mu, nh);
-        k_word_scatter<<<nh, nw64 * 32, sizeof(int32_t) * nw64 * 64, s>>>(ks, N, 64, p->blockcnt_mu,
-                                                                          pass == 0 ? tmp : p->sig,
-                                                                          pass == 0 ? nullptr : p->sigpos);
-    }
-    k_bin_bounds<<<gN, 256, 0, s>>>(p->sig, p->mubin, N, p->binstart);
-    p->launches += 7;
+    // mean-bucketed order (sig): rows sorted by mean bin with one stable
+    // counting sort over the kMuBins bins; the input follows a golden-ratio
+    // stride permutation, so the rows of a bin are not in time order and
+    // neighbours in this order are seldom overlapping subsequences
+    const KeySrc ks{p->mubin, nullptr, p->mu_stride, 0, kMuBins - 1};
+    cudaMemsetAsync(p->hist_mu, 0, sizeof(int32_t) * kMuBins, s);
+    k_word_hist<<<nh, 1024, sizeof(int32_t) * kMuBins, s>>>(ks, N, kMuBins, p->hist_mu, p->blockcnt_mu);
+    k_bin_start<<<1, 1024, 0, s>>>(p->hist_mu, N, p->binstart);
+    k_colscan<<<(kMuBins + 31) / 32, dim3(32, kColChunks), 0, s>>>(p->blockcnt_mu, kMuBins, nh, p->binstart);
+    const int nw = scatter_warps(kMuBins);
+    k_word_scatter<<<nh, nw * 32, sizeof(uint32_t) * nw * (kMuBins / 2), s>>>(ks, N, kMuBins, p->blockcnt_mu,
+                                                                            p->sig, p->sigpos);
+    p->launches += 4;
     return cudaGetLastError();
 }
 

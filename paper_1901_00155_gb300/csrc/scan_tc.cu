@@ -203,8 +203,10 @@ __global__ void __launch_bounds__(kTcThreadsV2, 1)
         // issued together and the next claim is in flight while the batch is
         // published, so the global-memory latency is paid once per batch.
         constexpr int kClaim = 4;
-        // short waves claim one item at a time so that every CTA gets work
-        const int claim = items >= (long long)gridDim.x * kClaim * 2 ? kClaim : 1;
+        // short waves, and every wave's last items, are claimed one at a time so
+        // that every CTA gets work and the CTAs finish together
+        const long long tail = (long long)gridDim.x * kClaim * 2;
+        int claim = items >= tail ? kClaim : 1;
         int ring = 0;
         uint32_t rph = 0;
         unsigned long long pairs = 0, nrun = 0;
@@ -313,7 +315,8 @@ __global__ void __launch_bounds__(kTcThreadsV2, 1)
                 }
             }
             int nbase = 0;
-            if (lane == 0) nbase = atomicAdd(&a.ctrl->work[a.work_slot], claim);
+            const int nclaim = items - (long long)base > tail ? kClaim : 1;
+            if (lane == 0) nbase = atomicAdd(&a.ctrl->work[a.work_slot], nclaim);
 #pragma unroll
             for (int b = 0; b < kClaim; b++) {
                 if (!__any_sync(0xffffffffu, any[b] && pa[b] < pb[b])) continue;
@@ -345,6 +348,7 @@ __global__ void __launch_bounds__(kTcThreadsV2, 1)
                 }
             }
             base = __shfl_sync(0xffffffffu, nbase, 0);
+            claim = nclaim;
         }
         if (lane == 0) {
             if (!ok) {

@@ -262,13 +262,99 @@ __global__ void __launch_bounds__(256, 4) k_compact(ListRef in, const uint32_t* 
     }
 }
 
+// Top-k threshold of one pass, run by the last block (256 threads) of that
+// pass's histogram launch: the bin (from the top) whose cumulative count
+// reaches the number of rows still wanted.  Thread t sums 16 bins in
+// descending order; a block inclusive scan of those sums finds the one bin
+// where the running count crosses it.  Pass 0 records the bin and the rows
+// still needed inside it; pass 1 refines the threshold to 2^7 ulps.
+constexpr int kTopkThreads = 256;
+__device__ void topk_threshold(Ctrl* ctrl, int k, int pass, const int* hist) {
+    __shared__ int part[kTopkThreads / 32];
+    __shared__ int found, above, total;
+    const int sel = pass == 0 ? 0 : ctrl->topk_bin;
+    if (sel < 0) return;  // pass 0 took every row (uniform over the block)
+    const int want = pass == 0 ? k : ctrl->topk_need;
+    constexpr int kPer = kTopkBins / kTopkThreads;
+    const int t = threadIdx.x;  // bins [4095 - kPer t - (kPer - 1), 4095 - kPer t]
+    int c[kPer], s = 0;
+#pragma unroll
+    for (int q = 0; q < kPer; q++) {
+        c[q] = __ldcg(&hist[kTopkBins - 1 - kPer * t - q]);
+        s += c[q];
+    }
+    const int lane = t & 31, wid = t >> 5;
+    int incl = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += u;
+    }
+    if (lane == 31) part[wid] = incl;
+    if (t == 0) found = 0x7fffffff;
+    __syncthreads();
+    if (wid == 0) {
+        const int v = lane < kTopkThreads / 32 ? part[lane] : 0;
+        int cc = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int u = __shfl_up_sync(0xffffffffu, cc, o);
+            if (lane >= o) cc += u;
+        }
+        if (lane < kTopkThreads / 32) part[lane] = cc - v;
+    }
+    __syncthreads();
+    int run = part[wid] + incl - s;
+#pragma unroll
+    for (int q = 0; q < kPer; q++) {
+        const int before = run;
+        run += c[q];
+        if (before < want && run >= want) {
+            atomicMin(&found, kPer * t + q);
+            above = before;  // written by the single crossing thread
+            total = run;
+        }
+    }
+    __syncthreads();
+    if (t == 0) {
+        if (found == 0x7fffffff) {  // fewer rows than wanted
+            if (pass == 0) {
+                ctrl->topk_thr = 0u;  // take them all
+                ctrl->topk_bin = -1;
+            } else {
+                ctrl->topk_thr = (uint32_t)sel << 19;
+            }
+        } else {
+            const int b = kTopkBins - 1 - found;
+            if (pass == 0) {
+                // refine only when the first pass would take over twice the rows wanted
+                ctrl->topk_bin = total > 2 * want ? b : -1;
+                ctrl->topk_need = want - above;
+                ctrl->topk_thr = (uint32_t)b << 19;
+            } else {
+                ctrl->topk_thr = ((uint32_t)sel << 19) | ((uint32_t)b << 7);
+            }
+        }
+    }
+}
+
 // Top-k radix select over the rows' running minima (alive rows only), two
 // passes of 12 bits each: pass 0 histograms float bits >> 19; pass 1
 // histograms bits 7..18 of the rows inside the bin that holds the k-th row.
-__global__ void __launch_bounds__(256) k_topk_hist(ListRef in, const uint32_t* __restrict__ rmin, TcBound tb,
-                                                   Ctrl* ctrl, int pass, const int* gate, int k) {
+// The last block of each pass (a ticket per selection and pass) computes the
+// pass's threshold.
+__global__ void __launch_bounds__(kTopkThreads) k_topk_hist(ListRef in, const uint32_t* __restrict__ rmin,
+                                                            TcBound tb, Ctrl* ctrl, int pass, const int* gate, int k,
+                                                            int site) {
     __shared__ int h[kTopkBins];
-    if (gate && *gate <= k) return;  // too few rows to be worth a separate wave
+    __shared__ bool last;
+    if (gate && *gate <= k) {  // too few rows to be worth a separate wave: select no row
+        if (pass == 0 && blockIdx.x == 0 && threadIdx.x == 0) {
+            ctrl->topk_thr = 0xffffffffu;
+            ctrl->topk_bin = -1;
+        }
+        return;
+    }
     for (int b = threadIdx.x; b < kTopkBins; b += blockDim.x) h[b] = 0;
     __syncthreads();
     const int cnt = *in.cnt_dev;
@@ -301,88 +387,13 @@ __global__ void __launch_bounds__(256) k_topk_hist(ListRef in, const uint32_t* _
     int* dst = pass == 0 ? ctrl->topk_hist : ctrl->topk_hist2;
     for (int b = threadIdx.x; b < kTopkBins; b += blockDim.x)
         if (h[b]) atomicAdd(&dst[b], h[b]);
-}
-
-// Top-k threshold of one pass: the bin (from the top) whose cumulative count
-// reaches the number of rows still wanted.  One block: per-thread sums of 4
-// bins (descending), a block inclusive scan, and the first thread whose run
-// crosses it.  Pass 0 records the bin and the rows still needed inside it;
-// pass 1 refines the threshold to 2^7 ulps.
-__global__ void __launch_bounds__(1024) k_topk_thr(Ctrl* ctrl, int k, int pass, const int* gate) {
-    __shared__ int part[32];
-    if (gate && *gate <= k) {  // select no row
-        if (threadIdx.x == 0 && pass == 0) {
-            ctrl->topk_thr = 0xffffffffu;
-            ctrl->topk_bin = -1;
-        }
-        return;
-    }
-    __shared__ int found;
-    __shared__ int above, total;
-    const int sel = pass == 0 ? 0 : ctrl->topk_bin;
-    if (sel < 0) return;  // pass 0 took every row
-    const int want = pass == 0 ? k : ctrl->topk_need;
-    const int* hist = pass == 0 ? ctrl->topk_hist : ctrl->topk_hist2;
-    const int t = threadIdx.x;  // thread t covers bins [4095 - 4t - 3, 4095 - 4t]
-    int c[4], s = 0;
-#pragma unroll
-    for (int q = 0; q < 4; q++) {
-        c[q] = hist[kTopkBins - 1 - 4 * t - q];
-        s += c[q];
-    }
-    const int lane = t & 31, wid = t >> 5;
-    int incl = s;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int u = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += u;
-    }
-    if (lane == 31) part[wid] = incl;
-    if (t == 0) found = 0x7fffffff;
+    __threadfence();  // this block's counts are visible before its ticket
     __syncthreads();
-    if (wid == 0) {
-        const int v = part[lane];
-        int cc = v;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int u = __shfl_up_sync(0xffffffffu, cc, o);
-            if (lane >= o) cc += u;
-        }
-        part[lane] = cc - v;
-    }
+    if (threadIdx.x == 0) last = atomicAdd(&ctrl->topk_ticket[site], 1) == (int)gridDim.x - 1;
     __syncthreads();
-    int run = part[wid] + incl - s;
-#pragma unroll
-    for (int q = 0; q < 4; q++) {
-        const int before = run;
-        run += c[q];
-        if (before < want && run >= want) {
-            atomicMin(&found, 4 * t + q);
-            above = before;  // written by the single crossing thread
-            total = run;
-        }
-    }
-    __syncthreads();
-    if (t == 0) {
-        if (found == 0x7fffffff) {  // fewer rows than wanted
-            if (pass == 0) {
-                ctrl->topk_thr = 0u;  // take them all
-                ctrl->topk_bin = -1;
-            } else {
-                ctrl->topk_thr = (uint32_t)sel << 19;
-            }
-        } else {
-            const int b = kTopkBins - 1 - found;
-            if (pass == 0) {
-                // refine only when the first pass would take over twice the rows wanted
-                ctrl->topk_bin = total > 2 * want ? b : -1;
-                ctrl->topk_need = want - above;
-                ctrl->topk_thr = (uint32_t)b << 19;
-            } else {
-                ctrl->topk_thr = ((uint32_t)sel << 19) | ((uint32_t)b << 7);
-            }
-        }
-    }
+    if (!last) return;
+    __threadfence();
+    topk_threshold(ctrl, k, pass, dst);
 }
 
 // Rows alive after the last wave have scanned every column: their running
@@ -859,11 +870,15 @@ struct Seq {
         if (topk_calls++ > 0)
             keep(cudaMemsetAsync(p->ctrl->topk_hist, 0, sizeof(p->ctrl->topk_hist) + sizeof(p->ctrl->topk_hist2),
                                  s));
-        for (int pass = 0; pass < 2; pass++) {
-            k_topk_hist<<<2 * p->sm_count, 256, 0, s>>>(in, p->rmin, tb, p->ctrl, pass, gate, k);
-            k_topk_thr<<<1, 1024, 0, s>>>(p->ctrl, k, pass, gate);
+        const int site = 2 * (topk_calls - 1);
+        if (site + 1 >= (int)(sizeof(p->ctrl->topk_ticket) / sizeof(int))) {
+            err = cudaErrorInvalidValue;
+            return;
         }
-        p->launches += 4;
+        for (int pass = 0; pass < 2; pass++)
+            k_topk_hist<<<2 * p->sm_count, kTopkThreads, 0, s>>>(in, p->rmin, tb, p->ctrl, pass, gate, k,
+                                                                 site + pass);
+        p->launches += 2;
         check();
     }
 
@@ -916,6 +931,7 @@ cudaError_t launch_search(dd_plan_s* p, const float* T, dd_result_t* out_dev, cu
         if (!joined) q.keep(cudaStreamWaitEvent(s, p->ev_join, 0));
         joined = true;
     };
+    ListRef rest = all;  // the rows the last wave scanned
     if (!o.early_abandon) {
         // every row scans every column; the argmax runs over all rows
         q.scan(DD_WAVE_EXHAUSTIVE, all, ColSpec{0, 0, (int)p->N, 0}, 0, nullptr, true);
@@ -942,9 +958,10 @@ cudaError_t launch_search(dd_plan_s* p, const float* T, dd_result_t* out_dev, cu
         ListRef cand = q.cand_list(p->list[0]);
         q.full(DD_WAVE_CAND, cand);
         // Raise the best-so-far further: full scans of the rows with the
-        // largest upper bounds (the likeliest discords) next.  A row once
-        // ruled out stays ruled out (the best-so-far only grows, upper bounds
-        // only shrink), so every later selection reads the whole list.
+        // largest upper bounds (the likeliest discords) next.  Few rows die in
+        // the Cand wave, so the selections read every row; a row once ruled out
+        // stays ruled out (the best-so-far only grows, upper bounds only
+        // shrink), so the final candidates are a subset of the last wave's rows.
         const ListRef alive = all;
         if (o.refine_k > 0) {
             q.topk(alive, o.refine_k);
@@ -952,7 +969,7 @@ cudaError_t launch_search(dd_plan_s* p, const float* T, dd_result_t* out_dev, cu
             q.full(DD_WAVE_TOP, top);
         }
         // rows still alive after the top wave (recomputed below if more waves run)
-        ListRef rest = q.compact(alive, p->list[2], 0);
+        rest = q.compact(alive, p->list[2], 0);
         // Algorithm 4 scans a row's other candidates in index order, which for a
         // periodic series meets a match one period away; the mean order scatters
         // those.  So when more than refine_k rows survive, every one of them (in
@@ -984,7 +1001,8 @@ cudaError_t launch_search(dd_plan_s* p, const float* T, dd_result_t* out_dev, cu
     }
     join();
     if (q.tc) {
-        ListRef cands = q.compact(all, p->list[3], 0);
+        // rows still alive after the last wave (a subset of the rows it scanned)
+        ListRef cands = q.compact(rest, p->list[3], 0);
         if (o.early_abandon) {
             // Many rows the Gram bound cannot rule out (data whose nearest-neighbour
             // distances lie within the bound of each other): settle them first with
