@@ -169,6 +169,28 @@ typedef struct {
     const float* q2;     /* [N] offset under the square root */
 } dd_bound_view_t;
 
+/* The mean-bucketed row order that the search visits columns in (no
+ * counterpart in the paper; it makes the pruning bound d^2(i, j) >= n
+ * (mu_i - mu_j)^2 of globally normalised subsequences usable, see Eq. 2 and
+ * the rows of Eq. 5), for inspection and testing.  Row i's bin is
+ *     clamp(floor((mu_i - lo) / w), 0, bins - 1),  lo = min t^, w = (max t^ - lo) / bins,
+ * (mu_i from dd_view_t.mu_w; lo = geom[0] and 1/w = geom[3] below).  The order is a
+ * stable counting sort by bin of the rows taken in the order
+ * e -> (e * stride) mod N (e = 0, 1, ..., N - 1): sig[p] is the row at
+ * position p, sigpos its inverse, binstart[b] the first position of bin b
+ * (binstart[bins] = N).  Pointers are device addresses owned by the plan,
+ * filled by dd_prep and by every search, valid until dd_plan_destroy. */
+typedef struct {
+    int64_t N;
+    int64_t stride;          /* the stride of the input order, coprime with N */
+    int32_t bins;
+    const int32_t* sig;      /* [N] row at each position */
+    const int32_t* sigpos;   /* [N] position of each row */
+    const int32_t* mubin;    /* [N] bin of each row */
+    const int32_t* binstart; /* [bins + 1] */
+    const double* geom;      /* [4] device: lo, w, 1/sigma, 1/w */
+} dd_order_view_t;
+
 /* ---- plans ------------------------------------------------------------- */
 
 /* Fills the defaults listed above. */
@@ -276,6 +298,10 @@ DD_API dd_status_t dd_plan_view(dd_plan_t plan, dd_view_t* view);
  * Errors: DD_EINVAL (null arguments), DD_ENOTSUP (an FP32 plan has no Gram
  * bound). */
 DD_API dd_status_t dd_plan_bound_view(dd_plan_t plan, dd_bound_view_t* view);
+
+/* The plan's mean-bucketed row order (dd_order_view_t).  Errors: DD_EINVAL
+ * (null arguments). */
+DD_API dd_status_t dd_plan_order_view(dd_plan_t plan, dd_order_view_t* view);
 
 /* Number of this library's kernels launched by the plan's last call (a graph
  * replay does not count the kernels of conditional waves it skipped).  Reads

@@ -241,6 +241,23 @@ class Plan:
                 "word_start": t(v.word_start, (D,), "<i4"), "ncand": t(v.ncand, (1,), "<i4"),
                 "t32": t(v.t32, (m,), "<f4")}
 
+    def order_view(self, like) -> dict:
+        """The mean-bucketed row order of the plan's last call (dd_plan_order_view): zero-copy
+        CUDA views of sig, sigpos, mubin, binstart and the bin geometry (lo, 1/w) on the device of
+        ``like``, plus the stride of the input order and the bin count."""
+        torch = _torch()
+        v = _lib.OrderView()
+        _check(self._lib.dd_plan_order_view(self._ptr, ctypes.byref(v)), "dd_plan_order_view")
+        N, bins = int(v.N), int(v.bins)
+
+        def t(ptr, k):
+            return torch.as_tensor(_DevArray(ptr, (k,), "<i4"), device=like.device)
+
+        geom = torch.as_tensor(_DevArray(v.geom, (4,), "<f8"), device=like.device)
+        return {"sig": t(v.sig, N), "sigpos": t(v.sigpos, N), "mubin": t(v.mubin, N),
+                "binstart": t(v.binstart, bins + 1), "stride": int(v.stride), "bins": bins,
+                "lo": geom[0], "inv_w": geom[3]}
+
     def bound_terms(self, like) -> dict:
         """Per-row terms of the Gram form's error bound F_i(D) = alpha_i + beta D + gam_i
         sqrt(max(D, 0) + q2_i) (dd_plan_bound_view), filled by the plan's last call: zero-copy

@@ -41,6 +41,12 @@ class BoundView(ctypes.Structure):
                 ("alpha", ctypes.c_void_p), ("gam", ctypes.c_void_p), ("q2", ctypes.c_void_p)]
 
 
+class OrderView(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int64), ("stride", ctypes.c_int64), ("bins", ctypes.c_int32),
+                ("sig", ctypes.c_void_p), ("sigpos", ctypes.c_void_p), ("mubin", ctypes.c_void_p),
+                ("binstart", ctypes.c_void_p), ("geom", ctypes.c_void_p)]
+
+
 class Profile(ctypes.Structure):
     _fields_ = [("dist_launches", ctypes.c_int32), ("precision", ctypes.c_int32), ("dist_ms", ctypes.c_double),
                 ("computed_pairs", ctypes.c_int64), ("call_ms", ctypes.c_double), ("reserved", ctypes.c_int64 * 4)]
@@ -88,6 +94,7 @@ SIGNATURES = {
     "dd_prep": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
     "dd_plan_view": ([ctypes.c_void_p, ctypes.POINTER(View)], ctypes.c_int),
     "dd_plan_bound_view": ([ctypes.c_void_p, ctypes.POINTER(BoundView)], ctypes.c_int),
+    "dd_plan_order_view": ([ctypes.c_void_p, ctypes.POINTER(OrderView)], ctypes.c_int),
     "dd_plan_last_launches": ([ctypes.c_void_p], ctypes.c_int64),
     "dd_status_string": ([ctypes.c_int], ctypes.c_char_p),
     "dd_probe_fma_rate": ([ctypes.c_int32, ctypes.POINTER(ctypes.c_double), ctypes.c_void_p], ctypes.c_int),

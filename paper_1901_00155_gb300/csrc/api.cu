@@ -663,6 +663,19 @@ dd_status_t dd_plan_bound_view(dd_plan_t p, dd_bound_view_t* v) {
     return DD_OK;
 }
 
+dd_status_t dd_plan_order_view(dd_plan_t p, dd_order_view_t* v) {
+    if (!p || !v) return DD_EINVAL;
+    v->N = p->N;
+    v->stride = p->mu_stride;
+    v->bins = dd::kMuBins;
+    v->sig = p->sig;
+    v->sigpos = p->sigpos;
+    v->mubin = p->mubin;
+    v->binstart = p->binstart;
+    v->geom = p->stats + 6;  // stats[6..9]: lo, w, 1/sigma, 1/w
+    return DD_OK;
+}
+
 int64_t dd_plan_last_launches(dd_plan_t p) {
     if (!p) return -1;
     // a graph replay skips the kernels of conditional bodies whose gate did not pass

@@ -37,6 +37,7 @@ def test_struct_layouts():
     assert ctypes.sizeof(_lib.Wave) == 32
     assert ctypes.sizeof(_lib.Completion) == 64
     assert ctypes.sizeof(_lib.BoundView) == 16 + 3 * 8
+    assert ctypes.sizeof(_lib.OrderView) == 24 + 5 * 8
 
 
 def test_options_default_and_footprint():
