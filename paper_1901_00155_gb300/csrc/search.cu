@@ -905,16 +905,23 @@ cudaError_t launch_search(dd_plan_s* p, const float* T, dd_result_t* out_dev, cu
     if (e == cudaSuccess) e = cudaMemsetAsync(p->rmin, 0x7f, sizeof(uint32_t) * p->N, s);
     if (e == cudaSuccess && p->rmin32) e = cudaMemsetAsync(p->rmin32, 0x7f, sizeof(uint32_t) * p->N, s);
     if (e != cudaSuccess) return e;
-    e = launch_prep_common(p, T, s);
-    if (e != cudaSuccess) return e;
     // The SAX words and the word order (needed from Algorithm 3 on) are built on
-    // a side stream while the mean order, the operand matrix and the first wave
-    // run here.
-    e = cudaEventRecord(p->ev_fork, s);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(p->side_stream, p->ev_fork, 0);
-    if (e == cudaSuccess) e = launch_prep_words(p, p->side_stream);
-    if (e == cudaSuccess) e = cudaEventRecord(p->ev_join, p->side_stream);
+    // a side stream.  In the Gram form they start after the mean order (whose
+    // latency-bound sort they would otherwise crowd) and run beside the operand
+    // build and the first wave; the FP32 form's exhaustive wave visits columns
+    // in the word order, so there they start right after the statistics.
+    const bool tc_plan = p->opt.precision != DD_FP32;
+    auto fork_words = [&]() -> cudaError_t {
+        cudaError_t f = cudaEventRecord(p->ev_fork, s);
+        if (f == cudaSuccess) f = cudaStreamWaitEvent(p->side_stream, p->ev_fork, 0);
+        if (f == cudaSuccess) f = launch_prep_words(p, p->side_stream);
+        if (f == cudaSuccess) f = cudaEventRecord(p->ev_join, p->side_stream);
+        return f;
+    };
+    e = launch_prep_common(p, T, s);
+    if (e == cudaSuccess && !tc_plan) e = fork_words();
     if (e == cudaSuccess) e = launch_prep_mean(p, s);
+    if (e == cudaSuccess && tc_plan) e = fork_words();
     if (e != cudaSuccess) return e;
 
     Seq q(p, s);
