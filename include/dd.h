@@ -261,9 +261,12 @@ DD_API dd_status_t dd_find_discord_batched(int32_t count, const float* const* T_
 DD_API dd_status_t dd_nn_profile(dd_plan_t plan, const float* T_dev, float* nn2_dev, void* stream);
 
 /* Exhaustive nearest-neighbour distances of selected rows: rows_dev[k]
- * (device int32, 0 <= row < N, k < count) -> nn2_dev[k] (device float).
- * Per-window plans (znorm = 1): exact FP64 values rounded to float.
- * Enqueued on `stream`.  Errors: DD_EINVAL, DD_ECUDA. */
+ * (device int32, k < count <= N) -> nn2_dev[k] (device float).  An entry
+ * outside [0, N) gives a non-finite value (NaN; +inf on per-window plans) and
+ * is never used as an index (the call still succeeds: the rows are only read
+ * on the device).  Per-window plans (znorm = 1): exact FP64 values rounded to
+ * float.  Enqueued on `stream`.  Errors: DD_EINVAL (count < 0 or > N, null
+ * pointers), DD_ECUDA. */
 DD_API dd_status_t dd_nn_rows(dd_plan_t plan, const float* T_dev, const int32_t* rows_dev, int32_t count, float* nn2_dev,
                        void* stream);
 

@@ -608,7 +608,7 @@ dd_status_t dd_nn_profile_diag(dd_plan_t p, const float* T_dev, float* nn2_dev, 
 
 dd_status_t dd_nn_rows(dd_plan_t p, const float* T_dev, const int32_t* rows_dev, int32_t count, float* nn2_dev,
                        void* stream) {
-    if (!p || !T_dev || !rows_dev || !nn2_dev || count < 0) return DD_EINVAL;
+    if (!p || !T_dev || !rows_dev || !nn2_dev || count < 0 || count > p->N) return DD_EINVAL;
     if (count == 0) return DD_OK;
     BusyGuard g(p);
     if (!g.ok) return DD_EBUSY;

@@ -583,16 +583,19 @@ __global__ void k_finalize(const Ctrl* ctrl, dd_result_t* out) {
     *out = r;
 }
 
-// nn2[k] = running minimum of rows[k] (exhaustive profile output).
+// nn2[k] = running minimum of rows[k] (exhaustive profile output); NaN for an
+// entry that is not a row (marked -1 by k_sanitize_rows).
 __global__ void k_gather_min(const int32_t* __restrict__ rows, int count, const uint32_t* __restrict__ rmin,
                              float* __restrict__ nn2) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k < count) nn2[k] = __uint_as_float(rmin[rows[k]]);
+    if (k < count) nn2[k] = rows[k] >= 0 ? __uint_as_float(rmin[rows[k]]) : __int_as_float(0x7fc00000);
 }
 
-__global__ void k_check_rows(const int32_t* __restrict__ rows, int count, int64_t N, Ctrl* ctrl) {
+// A caller's row list, copied with every entry outside [0, N) replaced by -1
+// (which every kernel of the wave treats as no row).
+__global__ void k_sanitize_rows(const int32_t* __restrict__ rows, int count, int64_t N, int32_t* __restrict__ out) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k < count && (rows[k] < 0 || rows[k] >= N)) atomicExch(&ctrl->err, DD_EINVAL);
+    if (k < count) out[k] = rows[k] >= 0 && rows[k] < N ? rows[k] : -1;
 }
 
 // ---------------------------------------------------------------------------
@@ -1055,8 +1058,13 @@ cudaError_t launch_profile(dd_plan_s* p, const float* T, const int32_t* rows, in
     if (e != cudaSuccess) return e;
     Seq q(p, s);
     if (q.tc) q.keep(launch_tc_prep(p, s));
-    const int32_t* r = rows ? rows : p->seq_rows;
+    const int32_t* r = p->seq_rows;
     const int c = rows ? count : (int)p->N;
+    if (rows) {  // the caller's rows, with out-of-range entries marked (count <= N, checked by the caller)
+        k_sanitize_rows<<<(c + 255) / 256, 256, 0, s>>>(rows, c, p->N, p->list[0]);
+        p->launches++;
+        r = p->list[0];
+    }
     ListRef L = q.constant_list(r, c);
     q.scan(DD_WAVE_EXHAUSTIVE, L, ColSpec{0, 0, (int)p->N, 0}, 0);
     k_gather_min<<<(c + 255) / 256, 256, 0, s>>>(r, c, p->rmin, nn2);

@@ -225,7 +225,8 @@ __global__ void __launch_bounds__(256) k_gather_rows(ListRef L, const int32_t* _
         const int c = (int)(g % per_row);
         const int i = L.base[off + r];
         const int64_t plane = (int64_t)(c >> 3) * N;  // chunk-major: [chunk][row][8 uint4]
-        P[(plane + r) * 8 + (c & 7)] = S[(plane + sigpos[i]) * 8 + (c & 7)];
+        // an entry that is not a row (-1) packs zeros; its tile row is masked anyway
+        P[(plane + r) * 8 + (c & 7)] = i >= 0 ? S[(plane + sigpos[i]) * 8 + (c & 7)] : make_uint4(0u, 0u, 0u, 0u);
     }
 }
 

@@ -266,3 +266,26 @@ def test_launch_count_excludes_skipped_conditional_waves():
         p.find_discord(Td)
         e = p.last_launches()
     assert 0 < g < e
+
+
+@pytest.mark.parametrize("form", ["fp32", "tc_fp16", "window"])
+def test_nn_rows_out_of_range_entries(form):
+    """dd_nn_rows with entries outside [0, N): they give non-finite values, are never used as
+    indices, and leave the valid rows' values (against the oracle) untouched."""
+    dd = _dd()
+    rng = np.random.default_rng(15)
+    T = np.cumsum(rng.standard_normal(6000)).astype(np.float32)
+    n = 64
+    N = T.size - n + 1
+    rows = np.array([5, -1, N, 100, -(2 ** 31), N + 777, 4000, 2 ** 31 - 1, N - 1], dtype=np.int32)
+    valid = (rows >= 0) & (rows < N)
+    kw = {"znorm": "window"} if form == "window" else {}
+    prec = "fp32" if form == "window" else form
+    with dd.Plan(T.size, n, prec, **kw) as p:
+        got = p.nn_rows(torch.from_numpy(T).cuda(), torch.from_numpy(rows).cuda()).cpu().numpy()
+    assert not np.isfinite(got[~valid]).any()
+    ref, _ = oracle.nn_rows(T, n, rows[valid], znorm="window" if form == "window" else "global")
+    # the Gram form's values are within its per-row bound (about 8 u n with u = 2^-11 here)
+    tol = {"fp32": dict(rtol=RTOL, atol=1e-6), "tc_fp16": dict(rtol=1e-2, atol=8 * 2.0 ** -11 * n),
+           "window": dict(rtol=1e-6, atol=1e-6)}[form]
+    np.testing.assert_allclose(got[valid], ref, **tol)
