@@ -27,13 +27,6 @@ __global__ void k_cand_count(const Ctrl* ctrl, int phase1_max, int* cnt) {
     *cnt = ctrl->ncand <= phase1_max ? ctrl->ncand : 0;
 }
 
-// The value rows are ranked by for the top-k waves: the running minimum, or in
-// the Gram form the smaller of it and the row's FP32 upper bound (non-negative
-// floats order like their bit patterns).
-__device__ __forceinline__ uint32_t rank_bits(const TcBound& b, int i, uint32_t rbits) {
-    return b.r32 ? min(rbits, b.r32[i]) : rbits;
-}
-
 // A row is alive unless one of its distances is proven strictly below the
 // best-so-far: FP32 form D < bsf (Algorithms 3/4); Gram form min(D + F_i(D),
 // r32_i) < bsf, bsf being a proven lower bound there.  Rows excluded from being
@@ -53,8 +46,10 @@ __device__ __forceinline__ bool is_alive(const TcBound& b, int i, uint32_t rbits
 // is_alive (and the rank test against thr) for U rows at once: every load of
 // the U rows is issued before any of them is used, so a thread waits on one
 // memory latency per step instead of one per row.  Entries i < 0 are not rows
-// (false).  The decisions are the ones is_alive and rank_bits make; rank gets
-// the rank values.
+// (false).  The decisions are the ones is_alive makes; rank gets the value
+// rows are ranked by for the top-k waves: the running minimum, or in the Gram
+// form the smaller of it and the row's FP32 upper bound (non-negative floats
+// order like their bit patterns).
 template <int U>
 __device__ __forceinline__ void alive_batch(const TcBound& b, const int (&iv)[U], const uint32_t* __restrict__ rmin,
                                             uint32_t bsf_bits, uint32_t thr, bool (&keep)[U], uint32_t (&rank)[U]) {
