@@ -938,7 +938,9 @@ cudaError_t launch_search(dd_plan_s* p, const float* T, dd_result_t* out_dev, cu
     };
     ListRef rest = all;  // the rows the last wave scanned
     if (!o.early_abandon) {
-        // every row scans every column; the argmax runs over all rows
+        // every row scans every column; the argmax runs over all rows.  The FP32
+        // form visits the columns in the word order: wait for the side stream.
+        join();
         q.scan(DD_WAVE_EXHAUSTIVE, all, ColSpec{0, 0, (int)p->N, 0}, 0, nullptr, true);
         q.complete(all);
     } else {
