@@ -386,6 +386,11 @@ dd_status_t create_plan(dd_plan_s** plan, int64_t m, int32_t n, const dd_options
     if (e == cudaSuccess) e = cudaMemsetAsync(p->t64 + p->m, 0, sizeof(double) * kPad, init);
     if (e == cudaSuccess) e = cudaMemsetAsync(p->t32 + p->m, 0, sizeof(float) * kPad, init);
     if (e == cudaSuccess) e = cudaMemsetAsync(p->excl, 0, (size_t)p->N, init);
+    // index arrays that the search builds on its side stream hold valid row indices
+    // (0) from the start, so no read of them can leave the series, whatever the order
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->order, 0, sizeof(int32_t) * (size_t)p->N, init);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->pos_of, 0, sizeof(int32_t) * (size_t)p->N, init);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->code, 0, sizeof(int32_t) * (size_t)p->N, init);
     if (e == cudaSuccess && p->wdat) e = cudaMemsetAsync(p->wdat + p->N, 0, sizeof(float4) * dd::kDgPad, init);
     if (e == cudaSuccess && p->wmu32) e = cudaMemsetAsync(p->wmu32 + p->N, 0, sizeof(float) * dd::kDgPad, init);
     if (e == cudaSuccess) {
