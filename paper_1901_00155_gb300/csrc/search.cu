@@ -27,6 +27,10 @@ __global__ void k_cand_count(const Ctrl* ctrl, int phase1_max, int* cnt) {
     *cnt = ctrl->ncand <= phase1_max ? ctrl->ncand : 0;
 }
 
+// Rank values at or above this (the running minimum's initial value) mean the
+// row has no finite upper bound yet.
+constexpr uint32_t kNoBound = 0x7f000000u;
+
 // A row is alive unless one of its distances is proven strictly below the
 // best-so-far: FP32 form D < bsf (Algorithms 3/4); Gram form min(D + F_i(D),
 // r32_i) < bsf, bsf being a proven lower bound there.  Rows excluded from being
@@ -46,13 +50,15 @@ __device__ __forceinline__ bool is_alive(const TcBound& b, int i, uint32_t rbits
 // is_alive (and the rank test against thr) for U rows at once: every load of
 // the U rows is issued before any of them is used, so a thread waits on one
 // memory latency per step instead of one per row.  Entries i < 0 are not rows
-// (false).  The decisions are the ones is_alive makes; rank gets the value
+// (false).  keep: alive with a rank value in [thr, thr_hi).  The alive
+// decisions are the ones is_alive makes; rank gets the value
 // rows are ranked by for the top-k waves: the running minimum, or in the Gram
 // form the smaller of it and the row's FP32 upper bound (non-negative floats
 // order like their bit patterns).
 template <int U>
 __device__ __forceinline__ void alive_batch(const TcBound& b, const int (&iv)[U], const uint32_t* __restrict__ rmin,
-                                            uint32_t bsf_bits, uint32_t thr, bool (&keep)[U], uint32_t (&rank)[U]) {
+                                            uint32_t bsf_bits, uint32_t thr, uint32_t thr_hi, bool (&keep)[U],
+                                            uint32_t (&rank)[U]) {
     uint32_t rb[U], r32[U];
     bool ex[U];
 #pragma unroll
@@ -91,14 +97,15 @@ __device__ __forceinline__ void alive_batch(const TcBound& b, const int (&iv)[U]
         }
         // rank value: min(rmin, r32) (r32 reads as all ones where there is none)
         rank[u] = min(rb[u], r32[u]);
-        keep[u] = a && rank[u] >= thr;
+        keep[u] = a && rank[u] >= thr && rank[u] < thr_hi;
     }
 }
 
 // Order-preserving compaction of a row list in one pass (decoupled look-back).
 // Predicates: pred 0: alive against the best-so-far; pred 1: alive and rank
-// value >= the top-k threshold; pred 2: member of Cand; pred 3: alive with no
-// finite upper bound yet (the running minimum still holds its initial value).
+// value >= the top-k threshold (and finite); pred 2: member of Cand; pred 3:
+// alive with no finite upper bound yet (the running minimum still holds its
+// initial value).
 // With sigpos set, rows outside positions [p_lo, p_hi) of the mean order are
 // dropped too.
 //
@@ -138,7 +145,8 @@ __global__ void __launch_bounds__(256, 4) k_compact(ListRef in, const uint32_t* 
     if (b >= nb) return;  // no entries here, and no block waits on a later one
     const int off = in.off_dev ? *in.off_dev : 0;
     const uint32_t bsf = ctrl->bsf;
-    const uint32_t thr = pred == 1 ? ctrl->topk_thr : (pred == 3 ? 0x7f000000u : 0u);
+    const uint32_t thr = pred == 1 ? ctrl->topk_thr : (pred == 3 ? kNoBound : 0u);
+    const uint32_t thr_hi = pred == 1 ? kNoBound : 0xffffffffu;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const unsigned lt = (1u << lane) - 1u;
     // the block's entries: 8 independent coalesced loads per thread
@@ -160,7 +168,7 @@ __global__ void __launch_bounds__(256, 4) k_compact(ListRef in, const uint32_t* 
         for (int q = 0; q < 8; q++) k8[q] = on && i8[q] >= 0 && hist[c8[q]] == fmin;
     } else {
         uint32_t rk[8];
-        alive_batch<8>(tb, i8, rmin, bsf, thr, k8, rk);
+        alive_batch<8>(tb, i8, rmin, bsf, thr, thr_hi, k8, rk);
     }
     if (sigpos) {
         // keep only rows at positions [p_lo, p_hi) of the mean order (a shard)
@@ -333,7 +341,8 @@ __device__ void topk_threshold(Ctrl* ctrl, int k, int pass, const int* hist) {
     }
 }
 
-// Top-k radix select over the rows' running minima (alive rows only), two
+// Top-k radix select over the rows' running minima (alive rows with a finite
+// upper bound only), two
 // passes of 12 bits each: pass 0 histograms float bits >> 19; pass 1
 // histograms bits 7..18 of the rows inside the bin that holds the k-th row.
 // The last block of each pass (a ticket per selection and pass) computes the
@@ -366,7 +375,9 @@ __global__ void __launch_bounds__(kTopkThreads) k_topk_hist(ListRef in, const ui
             for (int u = 0; u < U; u++) iv[u] = r0 + u * stride < cnt ? in.base[off + r0 + u * stride] : -1;
             bool ok[U];
             uint32_t rk[U];
-            alive_batch<U>(tb, iv, rmin, bsf, 0u, ok, rk);
+            // rows without a finite upper bound are not ranked (their full scans
+            // could not be pruned; they are scanned with the rest, abandoning early)
+            alive_batch<U>(tb, iv, rmin, bsf, 0u, kNoBound, ok, rk);
 #pragma unroll
             for (int u = 0; u < U; u++) {
                 if (!ok[u]) continue;
