@@ -89,7 +89,8 @@ typedef struct {
                               time-local wave and refine_k of them, ranked again, a second full
                               scan; 0 = skip both */
     int32_t local_cols;    /* first wave: every row scans the rows of nearest window mean, this many
-                              on each side of its tile (default 128; FP32 form -- the tensor-core
+                              on each side of its tile (default 64: with a 128-row tile, two
+                              128-column tiles of the FP32 kernel; FP32 form -- the tensor-core
                               form's first wave is one 128 x 256 band tile per row tile); 0 = no
                               first wave */
     int32_t word_cols;     /* same-word wave (FP32 form): survivors scan this many rows sharing their

@@ -58,7 +58,7 @@ def _check(st: int, what: str):
 
 
 def _options(precision="fp32", paa_w=4, alphabet=4, early_abandon=True, paa_mode=0, phase1_max=4096,
-             refine_k=128, local_cols=128, word_cols=512, shard_count=1, shard_index=0, znorm="global",
+             refine_k=128, local_cols=64, word_cols=512, shard_count=1, shard_index=0, znorm="global",
              diag=False) -> _lib.Options:
     o = _lib.Options()
     _lib.load().dd_options_default(ctypes.byref(o))

@@ -457,7 +457,7 @@ void dd_options_default(dd_options_t* opt) {
     opt->paa_mode = 0;
     opt->phase1_max = 4096;
     opt->refine_k = 128;
-    opt->local_cols = 128;
+    opt->local_cols = 64;
     opt->word_cols = 512;
 }
 
