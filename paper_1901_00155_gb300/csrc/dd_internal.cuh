@@ -106,6 +106,7 @@ struct ColSpec {
     int mode;
     int v_lo, v_hi;
     int local_cols;
+    int seg_cols;  // FP32 form, lower-bound scans: columns per work item (0: the default)
 };
 
 struct PrepArrays {

@@ -607,6 +607,7 @@ __global__ void k_sanitize_rows(const int32_t* __restrict__ rows, int count, int
 // ---------------------------------------------------------------------------
 // Host-side sequencing (no synchronisation; counts stay on the device).
 constexpr int kSegCols = 512;
+constexpr int kSegColsFull = 128;  // FP32 full scans: one column tile per item, so few rows spread over the SMs
 constexpr int kSettleMin = 64;   // candidate rows above which the Gram form settles them in FP32 first
 constexpr int kTimeCols = 256;   // time-local wave: columns on each side of a row tile
 constexpr int kFillCols = 2048;  // half-width of the neighbourhood of rows the band wave left unbounded
@@ -696,13 +697,14 @@ struct Seq {
             a.sig = p->sig;
             a.ranges = p->ranges;
             a.smax = smax;
-            a.seg_cols = kSegCols;
+            a.seg_cols = col.seg_cols > 0 ? col.seg_cols : kSegCols;
             a.rmin = p->rmin;
             a.ctrl_ro = p->ctrl;
             a.ctrl = p->ctrl;
             a.abandon = abandon;
             a.work_slot = slot;
-            a.min_seg_tiles = col.mode == 4 ? 1 : 4;  // time-local: spread a tile's few columns over blocks
+            // time-local and same-word waves: spread a tile's few columns over blocks
+            a.min_seg_tiles = col.mode == 4 || col.mode == 1 ? 1 : 4;
             a.min_rows = min_rows;
             a.wave = wave;
             const int grid = scan_fp32_grid(p);
@@ -754,7 +756,7 @@ struct Seq {
     }
 
     // Column ranges of the list's tiles (kind 0: local +-K, kind 1: lower bound).
-    const int* ranges(ListRef rows, int kind, int K) {
+    const int* ranges(ListRef rows, int kind, int K, int seg = kSegCols) {
         const int slot = smax_slot++;
         if (smax_slot > 64) {
             err = cudaErrorInvalidValue;
@@ -762,7 +764,7 @@ struct Seq {
         }
         const int tiles = (int)((p->N + 127) / 128);
         const int grid = tiles < p->sm_count * 8 ? tiles : p->sm_count * 8;
-        k_tile_ranges<<<grid, 128, 0, s>>>(rows, kind, K, kSegCols, p->sigpos, p->mubin, p->binstart, p->rmin, tb,
+        k_tile_ranges<<<grid, 128, 0, s>>>(rows, kind, K, seg, p->sigpos, p->mubin, p->binstart, p->rmin, tb,
                                             p->stats, p->n, (int)p->N, p->ranges, &p->ctrl->smax[slot]);
         p->launches++;
         check();
@@ -895,8 +897,11 @@ struct Seq {
     // n (mu_i - mu_j)^2 can still undercut the row's upper bound, nearest mean
     // first, abandoning against the best-so-far; survivors complete.
     void full(int kind, ListRef in) {
-        const int* sm = ranges(in, 1, 0);
-        scan(kind, in, ColSpec{2, 0, 0, 0}, 1, sm);
+        // the FP32 kernel computes whole 128-row tiles even for a few rows: one
+        // column tile per item spreads a short list over more SMs
+        const int seg = tc ? kSegCols : kSegColsFull;
+        const int* sm = ranges(in, 1, 0, seg);
+        scan(kind, in, ColSpec{2, 0, 0, 0, seg}, 1, sm);
         complete(in);
     }
 };
