@@ -72,6 +72,7 @@ struct Ctrl {
     int cticket[kCompactSites];   // block tickets of each compaction (blocks take their place in start order)
     int stat_ticket[2];           // blocks done with the two passes of the Eq. 2 statistics
     int topk_ticket[4];           // blocks done with each top-k histogram pass (two selections per search)
+    int best_ticket;              // blocks done with the exact maximum over the candidates
     int resc_nch;                 // FP64 rescoring: column chunks of the longest candidate range
     int topk_bin;                 // top-k select: bin of the first pass holding the k-th row (-1: take all)
     int topk_need;                // rows still needed from that bin

@@ -118,10 +118,16 @@ __global__ void __launch_bounds__(256) k_rescore64(ListRef cand, TcBound bound, 
     }
 }
 
-// best64 = max over candidates of the exact value; then the smallest index
-// attaining it.
-__global__ void __launch_bounds__(256) k_best64(ListRef cand, const unsigned long long* __restrict__ ex64, Ctrl* ctrl) {
+// The result over the rescored candidates: best64 = the largest exact value,
+// then the smallest index attaining it, then the result struct.  Every block
+// takes part in the maximum; the last block to finish (a ticket) picks the
+// index and writes the result.
+__global__ void __launch_bounds__(256) k_best_final(ListRef cand, const unsigned long long* __restrict__ ex64,
+                                                    Ctrl* ctrl, dd_result_t* out) {
+    __shared__ bool last;
+    __shared__ int red[8];
     const int cnt = *cand.cnt_dev;
+    const int off = cand.off_dev ? *cand.off_dev : 0;
     unsigned long long m = 0;
     for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < cnt; r += gridDim.x * blockDim.x) {
         const unsigned long long v = ex64[r];
@@ -133,45 +139,50 @@ __global__ void __launch_bounds__(256) k_best64(ListRef cand, const unsigned lon
         m = u > m ? u : m;
     }
     if ((threadIdx.x & 31) == 0 && m) atomicMax(&ctrl->best64, m);
-    if (blockIdx.x == 0 && threadIdx.x == 0) ctrl->ncandidates = cnt;
-}
-
-__global__ void __launch_bounds__(256) k_pick64(ListRef cand, const unsigned long long* __restrict__ ex64, Ctrl* ctrl) {
-    const int cnt = *cand.cnt_dev;
-    const int off = cand.off_dev ? *cand.off_dev : 0;
-    const unsigned long long best = ctrl->best64;
-    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < cnt; r += gridDim.x * blockDim.x)
-        if (ex64[r] == best) atomicMin(&ctrl->best_idx, cand.base[off + r]);
-}
-
-__global__ void k_finalize_tc(const Ctrl* ctrl, dd_result_t* out) {
+    __threadfence();  // this block's maximum is visible before its ticket
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(&ctrl->best_ticket, 1) == (int)gridDim.x - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    const unsigned long long best = *(volatile const unsigned long long*)&ctrl->best64;
+    int idx = 0x7fffffff;
+    for (int r = threadIdx.x; r < cnt; r += blockDim.x)
+        if (ex64[r] == best) idx = min(idx, cand.base[off + r]);
+    idx = __reduce_min_sync(0xffffffffu, idx);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = idx;
+    __syncthreads();
     if (threadIdx.x != 0) return;
-    dd_result_t r;
-    r.exact = 1;
-    r.computed_pairs = (int64_t)ctrl->pairs;
-    r.candidates = ctrl->ncandidates;
+    for (int w = 1; w < (int)(blockDim.x >> 5); w++) idx = min(idx, red[w]);
+    const int best_idx = min(idx, *(volatile const int*)&ctrl->best_idx);
+    ctrl->best_idx = best_idx;
+    ctrl->ncandidates = cnt;
+    dd_result_t res;
+    res.exact = 1;
+    res.computed_pairs = (int64_t)ctrl->pairs;
+    res.candidates = cnt;
     if (ctrl->nonfinite) {
-        r.status = DD_ENONFINITE;
-        r.index = -1;
-        r.nn_distance = 0.0;
+        res.status = DD_ENONFINITE;
+        res.index = -1;
+        res.nn_distance = 0.0;
     } else if (ctrl->degenerate) {
-        r.status = DD_OK;
-        r.index = 0;
-        r.nn_distance = 0.0;
+        res.status = DD_OK;
+        res.index = 0;
+        res.nn_distance = 0.0;
     } else if (ctrl->err) {
-        r.status = ctrl->err;
-        r.index = -1;
-        r.nn_distance = 0.0;
-    } else if (ctrl->best_idx == 0x7fffffff) {
-        r.status = DD_ECUDA;
-        r.index = -1;
-        r.nn_distance = 0.0;
+        res.status = ctrl->err;
+        res.index = -1;
+        res.nn_distance = 0.0;
+    } else if (best_idx == 0x7fffffff) {
+        res.status = DD_ECUDA;
+        res.index = -1;
+        res.nn_distance = 0.0;
     } else {
-        r.status = DD_OK;
-        r.index = ctrl->best_idx;
-        r.nn_distance = sqrt(__longlong_as_double((long long)ctrl->best64));
+        res.status = DD_OK;
+        res.index = best_idx;
+        res.nn_distance = sqrt(__longlong_as_double((long long)best));
     }
-    *out = r;
+    *out = res;
 }
 
 __global__ void k_init_best(Ctrl* ctrl) {
@@ -207,10 +218,8 @@ __global__ void k_init_rescore(ListRef cand, TcBound bound, const uint32_t* __re
 cudaError_t launch_best(dd_plan_s* p, ListRef cand, dd_result_t* out_dev, cudaStream_t s) {
     const unsigned long long* ex = reinterpret_cast<const unsigned long long*>(p->ex64);
     k_init_best<<<1, 32, 0, s>>>(p->ctrl);
-    k_best64<<<p->sm_count, 256, 0, s>>>(cand, ex, p->ctrl);
-    k_pick64<<<p->sm_count, 256, 0, s>>>(cand, ex, p->ctrl);
-    k_finalize_tc<<<1, 32, 0, s>>>(p->ctrl, out_dev);
-    p->launches += 4;
+    k_best_final<<<p->sm_count, 256, 0, s>>>(cand, ex, p->ctrl, out_dev);
+    p->launches += 2;
     return cudaGetLastError();
 }
 
@@ -223,10 +232,9 @@ cudaError_t launch_rescore(dd_plan_s* p, ListRef cand, TcBound bound, int work_s
     k_rescore64<<<2 * p->sm_count, 256, 0, s>>>(cand, bound, p->rmin, p->sig, p->mubin, p->binstart, p->stats, p->t64,
                                                  p->t32, p->n, (int)p->N, p->list[0], p->list[1],
                                                  reinterpret_cast<unsigned long long*>(p->ex64), p->ctrl, work_slot);
-    k_best64<<<p->sm_count, 256, 0, s>>>(cand, reinterpret_cast<const unsigned long long*>(p->ex64), p->ctrl);
-    k_pick64<<<p->sm_count, 256, 0, s>>>(cand, reinterpret_cast<const unsigned long long*>(p->ex64), p->ctrl);
-    k_finalize_tc<<<1, 32, 0, s>>>(p->ctrl, out_dev);
-    p->launches += 5;
+    k_best_final<<<p->sm_count, 256, 0, s>>>(cand, reinterpret_cast<const unsigned long long*>(p->ex64), p->ctrl,
+                                              out_dev);
+    p->launches += 3;
     return cudaGetLastError();
 }
 
