@@ -487,6 +487,69 @@ DD_API int64_t dd_engine_outstanding(dd_engine_t engine);
  * frees everything. */
 DD_API void dd_engine_destroy(dd_engine_t engine);
 
+/* ---------------------------------------------------------------- fused batch
+ * A batch plan searches many independent series of uneven lengths together:
+ * every step of the search (Section 2.1's discord of each series, found by the
+ * steps of Algorithms 2-4 with the tensor-core Gram form) is one launch over
+ * all series, and the distance tiles of every series are claimed from one
+ * device work queue by the persistent tcgen05 kernel.  Series with the same
+ * subsequence length n share one set of launches (a group).  Per series:
+ * Eq. 2 normalisation of that series alone, the mean-bucketed row order, a band
+ * wave (every row tile against the 256 columns around it in that order), full
+ * scans of the 128 rows with the largest upper bounds, which fix the series'
+ * own best-so-far, scans of the rows whose upper bound still reaches it
+ * (abandoned against it, Algorithm 4), and exact FP64 rescoring of every row the
+ * per-row error bound cannot rule out.  Each result is that of
+ * dd_find_discord on the same series with the same precision: exact index
+ * (ties -> smallest), FP64 nn_distance (computed_pairs is 0: pairs are not
+ * counted per series).
+ *
+ * The launches of a call are captured into a CUDA graph, which the next call
+ * with the same shapes (count and every (m, n), in order) replays; series
+ * pointers are read by the device from a descriptor table, so only the shapes
+ * key the graph.  Memory is one device allocation made at creation: capacity
+ * max_series series of at most max_values values in total, n <= n_max.  A call
+ * beyond that capacity returns DD_ENOMEM; more than 64 distinct n in one call
+ * returns DD_ENOTSUP.  Invalid series (as dd_plan_create's sizes, n > n_max, or
+ * a null pointer) complete with DD_EINVAL and do not affect the others.  A
+ * non-finite series completes with DD_ENONFINITE, a constant one with index 0
+ * and distance 0. */
+typedef struct dd_batch_s* dd_batch_t;
+
+typedef struct {
+    int32_t seg_cols;     /* columns per work item of the full-scan waves: a multiple of 256
+                             in [256, 65536] (default 512) */
+    int32_t settle_min;   /* a series with more FP64 candidates than this (rows whose Gram
+                             bounds overlap the best-so-far) first settles them with direct FP32
+                             full scans and their rigorous FP32 bounds (default 8; >= 0) */
+    int32_t reserved[2];  /* must be zero */
+} dd_batch_config_t;
+
+DD_API void dd_batch_config_default(dd_batch_config_t* cfg);
+
+/* Device bytes dd_batch_create allocates for this capacity (0 if invalid:
+ * max_series in [1, 65536], n_max in [1, 65536], max_values >= 1 and
+ * max_values + 384 max_series <= 2^30). */
+DD_API size_t dd_batch_footprint(int32_t max_series, int64_t max_values, int32_t n_max);
+
+/* opt: precision DD_TC_FP16 or DD_TC_BF16 (else DD_ENOTSUP), znorm 0, no shards,
+ * diag 0; the SAX and wave options do not apply.  cfg may be null (defaults).
+ * Errors: DD_EINVAL, DD_ENOTSUP, DD_ENOMEM, DD_ECUDA. */
+DD_API dd_status_t dd_batch_create(dd_batch_t* batch, int32_t max_series, int64_t max_values, int32_t n_max,
+                                   const dd_options_t* opt, const dd_batch_config_t* cfg);
+
+/* Searches count series (T_dev[k]: m[k] values on the device, complete in
+ * stream order on `stream`; m, n, out: host arrays).  Blocking: returns when
+ * out[] (host memory) holds every result.  Returns DD_OK or the first
+ * non-DD_OK result status; DD_EBUSY if another thread is using the batch. */
+DD_API dd_status_t dd_batch_search(dd_batch_t batch, int32_t count, const float* const* T_dev, const int64_t* m,
+                                   const int32_t* n, dd_result_t* out, void* stream);
+
+/* Calls that replayed the captured graph of the previous call's shapes. */
+DD_API int64_t dd_batch_graph_replays(dd_batch_t batch);
+
+DD_API void dd_batch_destroy(dd_batch_t batch);
+
 #ifdef __cplusplus
 }
 #endif

@@ -17,7 +17,8 @@ from dataclasses import dataclass
 
 from . import _lib
 
-__all__ = ["Plan", "Engine", "Completion", "DiscordResult", "DDError", "find_discord", "find_discord_batched", "PRECISIONS"]
+__all__ = ["Plan", "Engine", "Batch", "Completion", "DiscordResult", "DDError", "find_discord", "find_discord_batched",
+           "PRECISIONS"]
 
 PRECISIONS = {"fp32": _lib.DD_FP32, "tc_fp16": _lib.DD_TC_FP16, "tc_bf16": _lib.DD_TC_BF16}
 # "global": the whole series z-normalised (Eq. 2); "window": every subsequence on its own
@@ -360,11 +361,30 @@ def group_by_tuned_options(ms, ns, table, precision=None, **opts):
     return groups
 
 
-def find_discord_batched(series, ns, precision=None, stream=None, table=None, **opts):
+def find_discord_batched(series, ns, precision=None, stream=None, table=None, fused=False, seg_cols=None,
+                         settle_min=None, **opts):
     """Independent searches over CUDA float32 tensors of possibly different lengths.  With a
     tuning table, each series runs with the options tuned for its (n, m bucket), explicit options
     taking precedence: one batched call per distinct option set, results in the input order.
-    ``precision`` defaults to "fp32" (with a table: to the tuned form)."""
+    ``precision`` defaults to "fp32" (with a table: to the tuned form).
+
+    ``fused=True`` (tensor-core precisions only) searches the whole list with one fused batch
+    (dd_batch_*: every step one launch over all series) instead of the engine's concurrent
+    per-series searches; a table (tuning.tune_batch) then supplies the schedule (``seg_cols``,
+    ``settle_min``, precision) of the batch's dominant (n, m bucket) class, explicit arguments
+    taking precedence."""
+    if fused:
+        if table is not None:
+            from . import tuning
+            tuned = tuning.lookup_batch(table, [s.numel() for s in series], ns)
+            precision = precision if precision is not None else tuned.get("precision")
+            seg_cols = seg_cols if seg_cols is not None else tuned.get("seg_cols")
+            settle_min = settle_min if settle_min is not None else tuned.get("settle_min")
+        if precision is None:
+            precision = "tc_fp16"
+        with Batch(len(series), sum(s.numel() for s in series), max(int(x) for x in ns), precision,
+                   seg_cols=seg_cols, settle_min=settle_min, **opts) as b:
+            return b.search(series, ns, stream)
     if table is not None:
         results = [None] * len(series)
         for o, pos in group_by_tuned_options([s.numel() for s in series], ns, table, precision, **opts):
@@ -391,6 +411,69 @@ def find_discord_batched(series, ns, precision=None, stream=None, table=None, **
     if st != _lib.DD_OK and all(isinstance(r, DDError) for r in results):
         raise DDError(st, "dd_find_discord_batched")
     return results
+
+
+class Batch:
+    """A fused batch plan (dd_batch_*): capacity ``max_series`` series of ``max_values`` values
+    in total, subsequence lengths up to ``n_max``, tensor-core precision.  ``search`` runs every
+    series with one launch per step of the search for all of them (per distinct n), captured into
+    a CUDA graph that the next call with the same shapes replays; each result equals that of
+    ``find_discord`` on the series alone."""
+
+    def __init__(self, max_series: int, max_values: int, n_max: int, precision="tc_fp16", seg_cols=None,
+                 settle_min=None, **opts):
+        self._lib = _lib.load()
+        self.options = _options(precision, **opts)
+        cfg = _lib.BatchConfig()
+        self._lib.dd_batch_config_default(ctypes.byref(cfg))
+        if seg_cols is not None:
+            cfg.seg_cols = int(seg_cols)
+        if settle_min is not None:
+            cfg.settle_min = int(settle_min)
+        self.config = cfg
+        self._ptr = ctypes.c_void_p()
+        _check(self._lib.dd_batch_create(ctypes.byref(self._ptr), int(max_series), int(max_values), int(n_max),
+                                         ctypes.byref(self.options), ctypes.byref(cfg)), "dd_batch_create")
+
+    @staticmethod
+    def footprint(max_series: int, max_values: int, n_max: int) -> int:
+        return int(_lib.load().dd_batch_footprint(int(max_series), int(max_values), int(n_max)))
+
+    def search(self, series, ns, stream=None) -> list:
+        """Results in input order: DiscordResult, or DDError for a series that failed."""
+        k = len(series)
+        for s in series:
+            _check_series(s, s.numel())
+        ptrs = (ctypes.c_void_p * max(k, 1))(*[ctypes.c_void_p(s.data_ptr()) for s in series])
+        ms = (ctypes.c_int64 * max(k, 1))(*[s.numel() for s in series])
+        nn = (ctypes.c_int32 * max(k, 1))(*[int(x) for x in ns])
+        out = (_lib.Result * max(k, 1))()
+        st = self._lib.dd_batch_search(self._ptr, k, ptrs, ms, nn, out, _stream_ptr(stream))
+        # a failure of the whole call marks every entry with its status
+        if st in (_lib.DD_EBUSY, _lib.DD_ENOMEM, _lib.DD_ENOTSUP, _lib.DD_ECUDA) and all(r.status == st
+                                                                                       for r in out[:k]):
+            raise DDError(st, "dd_batch_search")
+        return [_as_result(r) if r.status == _lib.DD_OK else DDError(r.status, "batch item") for r in out[:k]]
+
+    def graph_replays(self) -> int:
+        return int(self._lib.dd_batch_graph_replays(self._ptr))
+
+    def close(self):
+        if getattr(self, "_ptr", None) and self._ptr.value:
+            self._lib.dd_batch_destroy(self._ptr)
+            self._ptr = ctypes.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 @dataclass

@@ -61,6 +61,10 @@ DD_SERIES_DEVICE = 0
 DD_SERIES_HOST = 1
 
 
+class BatchConfig(ctypes.Structure):
+    _fields_ = [("seg_cols", ctypes.c_int32), ("settle_min", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
+
+
 class Wave(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("rows", ctypes.c_int32), ("items", ctypes.c_int64),
                 ("pairs", ctypes.c_int64), ("ms", ctypes.c_double)]
@@ -116,6 +120,15 @@ SIGNATURES = {
     "dd_engine_poll": ([ctypes.c_void_p, ctypes.POINTER(Completion), ctypes.c_int32, ctypes.c_int32], ctypes.c_int32),
     "dd_engine_outstanding": ([ctypes.c_void_p], ctypes.c_int64),
     "dd_engine_destroy": ([ctypes.c_void_p], None),
+    "dd_batch_config_default": ([ctypes.POINTER(BatchConfig)], None),
+    "dd_batch_footprint": ([ctypes.c_int32, ctypes.c_int64, ctypes.c_int32], ctypes.c_size_t),
+    "dd_batch_create": ([ctypes.POINTER(ctypes.c_void_p), ctypes.c_int32, ctypes.c_int64, ctypes.c_int32,
+                         ctypes.POINTER(Options), ctypes.POINTER(BatchConfig)], ctypes.c_int),
+    "dd_batch_search": ([ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_void_p),
+                         ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(Result),
+                         ctypes.c_void_p], ctypes.c_int),
+    "dd_batch_graph_replays": ([ctypes.c_void_p], ctypes.c_int64),
+    "dd_batch_destroy": ([ctypes.c_void_p], None),
 }
 
 

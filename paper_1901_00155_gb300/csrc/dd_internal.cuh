@@ -223,6 +223,10 @@ struct TcArgs {
     const int32_t* sigpos;  // orig row -> position in the mean order
     int local_k;            // mode 2: > 0 limits row i to positions within local_k of its own
     int stall;              // fault injection (tests): issue no operand copy
+    // fused batch (batch.cu): per list tile its series, per series its best-so-far
+    // (float bits); null for a single-series search
+    const int32_t* tser;
+    const uint32_t* sbsf;
 };
 
 }  // namespace dd

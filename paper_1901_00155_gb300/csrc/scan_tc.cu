@@ -126,6 +126,11 @@ __device__ __forceinline__ void item_geometry(const TcArgs& a, int item, int RT,
 // a tile's 256 columns).  Work items flow from warp 0 to the others through
 // a ring of descriptors; operand k-chunks through a ring of stages; tiles
 // through two TMEM accumulators.  Nothing waits on an unbounded barrier.
+//
+// kBatch: the rows of each list tile belong to one series of a fused batch
+// (batch.cu) and are tested against that series' own best-so-far,
+// a.sbsf[a.tser[tile]], instead of the control block's.
+template <bool kBatch>
 __global__ void __launch_bounds__(kTcThreadsV2, 1)
     k_scan_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, TcArgs a) {
     extern __shared__ unsigned char smraw[];
@@ -227,7 +232,7 @@ __global__ void __launch_bounds__(kTcThreadsV2, 1)
         while (ok && base >= 0 && base < items && !*abort) {
             int rt[kClaim], pa[kClaim], pb[kClaim], dir[kClaim];
             float4 rowd[kClaim][4];  // per row: (sqrt(n) mu, c, running minimum, orig index bits)
-            float segL[kClaim], segH[kClaim];
+            float segL[kClaim], segH[kClaim], bsfv[kClaim];
             const float bsf = __uint_as_float(*((volatile const unsigned*)&ctrl->bsf));
 #pragma unroll
             for (int b = 0; b < kClaim; b++) {
@@ -238,6 +243,8 @@ __global__ void __launch_bounds__(kTcThreadsV2, 1)
                 if (item < items) item_geometry(a, (int)item, RT, nseg0, pos0, rt[b], pa[b], pb[b], dir[b]);
                 // the row tile is known without the column range: load its rows in parallel with it
                 const int rtb = item < items ? (a.mode == 3 ? (int)item : (int)(item % RT)) : RT;
+                bsfv[b] = bsf;
+                if (kBatch && rtb < RT) bsfv[b] = __uint_as_float(*((volatile const unsigned*)(a.sbsf + a.tser[rtb])));
 #pragma unroll
                 for (int q = 0; q < 4; q++) {
                     const int r = rtb * TBM + q * 32 + lane;
@@ -258,10 +265,10 @@ __global__ void __launch_bounds__(kTcThreadsV2, 1)
                 }
             }
             // the error bound of a row is needed to test it against a best-so-far or a lower bound
-            const bool need_bound = seg_check || local || (a.abandon && bsf > 0.f);
             bool any[kClaim];
 #pragma unroll
             for (int b = 0; b < kClaim; b++) {
+                const bool need_bound = seg_check || local || (a.abandon && bsfv[b] > 0.f);
                 const bool up = dir[b] > 0;
                 bool fin = true;  // no live row needs this segment or any farther one on its side
                 any[b] = !a.abandon && !local;
@@ -287,7 +294,7 @@ __global__ void __launch_bounds__(kTcThreadsV2, 1)
                     float R = D + bound_F(D, a.alpha[i], a.gam[i], a.q2[i], a.beta);
                     if (a.r32) R = fminf(R, __uint_as_float(a.r32[i]));
                     // a row whose upper bound is below the best-so-far stays below it
-                    if (a.abandon && R < bsf) continue;
+                    if (a.abandon && R < bsfv[b]) continue;
                     bool need = true, need_far = true;
                     if (seg_check) {
                         const float x = rowd[b][q].x;
@@ -641,9 +648,14 @@ cudaError_t tc_make_maps(dd_plan_s* p) {
 
 cudaError_t launch_scan_tc(dd_plan_s* p, const TcArgs& a, bool a_packed, cudaStream_t s) {
     const size_t smem = tc_smem_bytes(p->kpad);
-    cudaError_t e = cudaFuncSetAttribute(k_scan_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const bool batch = a.sbsf != nullptr;
+    cudaError_t e = cudaFuncSetAttribute(batch ? k_scan_tc<true> : k_scan_tc<false>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_scan_tc<<<p->sm_count, kTcThreadsV2, smem, s>>>(a_packed ? p->mapP_A : p->mapS_A, p->mapS_B, a);
+    if (batch)
+        k_scan_tc<true><<<p->sm_count, kTcThreadsV2, smem, s>>>(a_packed ? p->mapP_A : p->mapS_A, p->mapS_B, a);
+    else
+        k_scan_tc<false><<<p->sm_count, kTcThreadsV2, smem, s>>>(a_packed ? p->mapP_A : p->mapS_A, p->mapS_B, a);
     return cudaGetLastError();
 }
 

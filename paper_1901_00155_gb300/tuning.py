@@ -13,6 +13,13 @@ such searches, and options the caller passes explicitly always win over an entry
 
 Shapes are bucketed by m to the next power of two (2^11 .. 2^31), so one tuned entry serves every
 series of that length class with the same n.  Tables are plain JSON.
+
+The fused batch (dd_batch_*) has its own schedule: columns per work item of its full-scan waves
+(seg_cols), the candidate count above which a series settles its candidates with direct FP32 full
+scans before the FP64 rescoring (settle_min), and the tensor-core precision.  tune_batch times them
+on a seeded batch of each (n, m bucket) class and keeps the fastest under "batch_entries"; every
+candidate schedule must return the same discord for every series (exact FP64 rescoring: the same
+index, distances within 1e-9 relative).
 """
 from __future__ import annotations
 
@@ -169,3 +176,120 @@ def load(path: str) -> dict:
     if table.get("version") != TABLE_VERSION:
         raise TuningError(f"{path}: table version {table.get('version')} != {TABLE_VERSION}")
     return table
+
+
+# Schedules of the fused batch that change only its speed.
+BATCH_CANDIDATES = tuple(
+    {"precision": "tc_fp16", "seg_cols": sc, "settle_min": st}
+    for sc in (256, 512, 1024)
+    for st in (4, 8, 16, 32)
+)
+
+
+def batch_key(m: int, n: int) -> str:
+    return f"batch/n{int(n)}/m{bucket(m)}"
+
+
+def time_batch(options: dict, series, ns, reps: int = 3, warmup: int = 1):
+    """Median wall time (ms) of a blocking dd_batch_search with `options` (the first call captures
+    the graph and is not timed), and the per-series results [(index, nn_distance)]."""
+    import statistics
+    import time
+
+    import torch
+
+    from . import Batch
+
+    opts = dict(options)
+    prec = opts.pop("precision", "tc_fp16")
+    with Batch(len(series), sum(int(t.numel()) for t in series), max(int(x) for x in ns), prec, **opts) as b:
+        res = None
+        for _ in range(warmup):
+            res = b.search(series, ns)
+        ts = []
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            res = b.search(series, ns)
+            ts.append((time.perf_counter() - t0) * 1e3)
+    return statistics.median(ts), [(r.index, r.nn_distance) for r in res]
+
+
+def _default_batch(m_bucket: int, n: int, count: int, seed: int):
+    """`count` seeded series of the class: m log-uniform in (m_bucket / 2, m_bucket], half random
+    walks, half sine + noise, one injected anomaly each (the batch workload's structure)."""
+    import numpy as np
+    import torch
+
+    from . import synth
+
+    rng = np.random.default_rng(seed)
+    lo = max(3 * int(n), m_bucket // 2 + 1)
+    out = []
+    for k in range(count):
+        m = int(round(math.exp(rng.uniform(math.log(lo), math.log(m_bucket)))))
+        kind = "rw" if k % 2 == 0 else "sine"
+        anomaly = ("burst",) if kind == "rw" else ("phase",)
+        spec = synth.SeriesSpec(kind, m, int(n), int(seed * 100003 + k), anomaly if m >= 4 * n + 256 else ())
+        out.append(torch.from_numpy(synth.make_series(spec)[0]).cuda())
+    return out
+
+
+def _same_results(a, b, rtol: float) -> bool:
+    return len(a) == len(b) and all(i == j and math.isclose(x, y, rel_tol=rtol, abs_tol=1e-12)
+                                    for (i, x), (j, y) in zip(a, b))
+
+
+def tune_batch(classes, candidates=None, count: int = 32, reps: int = 3, seed: int = 0, timer=None, batch=None,
+               rtol: float = 1e-9, unsupported=None, table: dict | None = None) -> dict:
+    """Tune the fused batch for every (m, n) class of `classes` (m is bucketed); returns `table`
+    (or a new one) with "batch_entries" filled in.
+
+    timer(options, series, ns, reps) -> (ms, results) times one schedule (default: time_batch);
+    batch(m_bucket, n, count, seed) builds the class's series (default: _default_batch)."""
+    candidates = list(candidates if candidates is not None else BATCH_CANDIDATES)
+    if not candidates:
+        raise ValueError("no candidate schedules")
+    timer = timer or time_batch
+    batch = batch or _default_batch
+    if unsupported is None:
+        from . import DDError as unsupported  # noqa: N813
+    out = table if table is not None else {"version": TABLE_VERSION, "entries": {}}
+    entries = out.setdefault("batch_entries", {})
+    for m, n in classes:
+        mb = bucket(m)
+        series = batch(mb, n, count, seed)
+        ns = [int(n)] * len(series)
+        trials, ref = [], None
+        for opts in candidates:
+            try:
+                ms, res = timer(dict(opts), series, ns, reps)
+            except unsupported:
+                trials.append({"options": dict(opts), "ms": None})
+                continue
+            if ref is None:
+                ref = res
+            elif not _same_results(ref, res, rtol):
+                raise TuningError(f"batch schedules disagree on class n={n} m<={mb}: {opts}")
+            trials.append({"options": dict(opts), "ms": float(ms)})
+        ok = [t for t in trials if t["ms"] is not None]
+        if not ok:
+            raise TuningError(f"no candidate schedule supports class n={n} m<={mb}")
+        best = min(ok, key=lambda t: t["ms"])
+        entries[batch_key(mb, n)] = {"m_bucket": mb, "n": int(n), "count": len(series), "options": best["options"],
+                                     "ms": best["ms"], "trials": trials}
+    return out
+
+
+def lookup_batch(table: dict, ms, ns) -> dict:
+    """The tuned schedule for a batch: that of its (n, m bucket) class with the most work
+    (sum of m n over the class's series); {} if that class has no entry."""
+    if not table or table.get("version") != TABLE_VERSION or not len(ms):
+        return {}
+    work = {}
+    for m, n in zip(ms, ns):
+        k = batch_key(int(m), int(n))
+        work[k] = work.get(k, 0) + int(m) * int(n)
+    top = max(work, key=lambda k: (work[k], k))
+    e = table.get("batch_entries", {}).get(top)
+    return dict(e["options"]) if e else {}

@@ -38,6 +38,7 @@ def test_struct_layouts():
     assert ctypes.sizeof(_lib.Completion) == 64
     assert ctypes.sizeof(_lib.BoundView) == 16 + 3 * 8
     assert ctypes.sizeof(_lib.OrderView) == 24 + 5 * 8
+    assert ctypes.sizeof(_lib.BatchConfig) == 16
 
 
 def test_options_default_and_footprint():
@@ -140,3 +141,42 @@ def test_sharded_footprint_matches_unsharded():
     for prec in ("fp32", "tc_fp16"):
         a = dd.Plan.footprint(1 << 16, 256, prec)
         assert a > 0 and dd.Plan.footprint(1 << 16, 256, prec, shard_count=4, shard_index=3) == a
+
+
+def test_batch_entry_points_reject_bad_arguments_without_device_work():
+    """The fused batch: defaults, footprint limits and argument checks before any CUDA call."""
+    lib = _lib.load()
+    cfg = _lib.BatchConfig()
+    lib.dd_batch_config_default(ctypes.byref(cfg))
+    assert cfg.seg_cols == 512 and cfg.settle_min == 8 and list(cfg.reserved) == [0, 0]
+    fp = lib.dd_batch_footprint(512, 10_200_000, 256)
+    assert 10 << 30 < fp < 16 << 30  # two 16-bit operand matrices of ~10.4 M rows x 256 dominate
+    assert lib.dd_batch_footprint(0, 1000, 64) == 0
+    assert lib.dd_batch_footprint(4, 0, 64) == 0
+    assert lib.dd_batch_footprint(4, 1000, 0) == 0
+    assert lib.dd_batch_footprint(4, 1000, 70000) == 0
+    assert lib.dd_batch_footprint(4, 1 << 30, 64) == 0  # beyond 2^30 rows
+    b = ctypes.c_void_p()
+    o = _lib.Options()
+    lib.dd_options_default(ctypes.byref(o))
+    assert lib.dd_batch_create(ctypes.byref(b), 4, 1000, 64, ctypes.byref(o), None) == _lib.DD_ENOTSUP  # FP32
+    o.precision = 1
+    o.znorm = 1
+    assert lib.dd_batch_create(ctypes.byref(b), 4, 1000, 64, ctypes.byref(o), None) == _lib.DD_ENOTSUP
+    o.znorm = 0
+    for bad in (0, 100, 1 << 17):
+        cfg.seg_cols = bad
+        assert lib.dd_batch_create(ctypes.byref(b), 4, 1000, 64, ctypes.byref(o), ctypes.byref(cfg)) == \
+            _lib.DD_EINVAL
+    lib.dd_batch_config_default(ctypes.byref(cfg))
+    cfg.settle_min = -1
+    assert lib.dd_batch_create(ctypes.byref(b), 4, 1000, 64, ctypes.byref(o), ctypes.byref(cfg)) == _lib.DD_EINVAL
+    lib.dd_batch_config_default(ctypes.byref(cfg))
+    cfg.reserved[1] = 3
+    assert lib.dd_batch_create(ctypes.byref(b), 4, 1000, 64, ctypes.byref(o), ctypes.byref(cfg)) == _lib.DD_EINVAL
+    assert lib.dd_batch_create(None, 4, 1000, 64, ctypes.byref(o), None) == _lib.DD_EINVAL
+    assert lib.dd_batch_create(ctypes.byref(b), 0, 1000, 64, ctypes.byref(o), None) == _lib.DD_EINVAL
+    assert b.value is None
+    assert lib.dd_batch_search(None, 1, None, None, None, None, None) == _lib.DD_EINVAL
+    assert lib.dd_batch_graph_replays(None) == -1
+    lib.dd_batch_destroy(None)

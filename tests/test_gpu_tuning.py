@@ -47,3 +47,25 @@ def test_batched_with_table_matches_solo():
             nn, _ = oracle.nn_rows(T, n, [g.index])
             assert nn[0] == pytest.approx(d2_ref, rel=1e-4)
     assert got[0].exact and not got[1].exact  # the tuned (tensor-core) and the default (FP32) forms
+
+
+def test_tune_batch_class_against_oracle():
+    """The fused batch's schedule tuner on one small class: every candidate schedule returns the
+    same discords (the tuner checks), the winner is one of them, and a fused batched call with the
+    table finds the oracle's discord of every series."""
+    import paper_1901_00155_gb300 as dd
+    from paper_1901_00155_gb300 import tuning
+    cands = [{"precision": "tc_fp16", "seg_cols": 256, "settle_min": 4},
+             {"precision": "tc_fp16", "seg_cols": 1024, "settle_min": 32}]
+    table = tuning.tune_batch([(4096, 64)], cands, count=8, reps=2, seed=5)
+    e = table["batch_entries"]["batch/n64/m4096"]
+    assert e["options"] in cands and e["ms"] > 0 and e["count"] == 8
+    series = tuning._default_batch(4096, 64, 8, 5)
+    got = dd.find_discord_batched(series, [64] * 8, fused=True, table=table)
+    for T, g in zip(series, got):
+        Th = T.cpu().numpy()
+        i_ref, d2_ref = oracle.discord_brute(Th, 64)
+        assert g.exact and g.nn_distance == pytest.approx(math.sqrt(d2_ref), rel=1e-6)
+        if g.index != i_ref:
+            nn, _ = oracle.nn_rows(Th, 64, [g.index])
+            assert nn[0] == pytest.approx(d2_ref, rel=1e-12)

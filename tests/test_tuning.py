@@ -163,3 +163,71 @@ def test_same_form_candidates_must_agree_on_the_index():
     b = tuning.Trial({"precision": "tc_bf16"}, 1.0, 4, 2.0 * (1 + 1e-6))
     assert tuning._agree(a, b, 1e-4)
     assert not tuning._agree(a, tuning.Trial({"precision": "fp32"}, 1.0, 4, 2.0), 1e-4)
+
+
+# ---- fused batch schedules -------------------------------------------------------------------
+
+def _fake_batch(times, disagree=None, unsupported=()):
+    calls = []
+
+    def timer(opts, series, ns, reps):
+        calls.append((tuple(sorted(opts.items())), len(series), tuple(ns), reps))
+        k = (opts["seg_cols"], opts["settle_min"])
+        if k in unsupported:
+            raise Unsupported(k)
+        res = [(i, 1.0 + i) for i in range(len(series))]
+        if disagree == k:
+            res[0] = (5, 1.0)
+        return times[k], res
+    return timer, calls
+
+
+BCANDS = [{"precision": "tc_fp16", "seg_cols": sc, "settle_min": st} for sc in (256, 512) for st in (4, 8)]
+
+
+def _fake_series(mb, n, count, seed):
+    return [("series", mb, n, k, seed) for k in range(count)]
+
+
+def test_tune_batch_picks_fastest_schedule_per_class():
+    times = {(256, 4): 5.0, (256, 8): 4.0, (512, 4): 3.0, (512, 8): 3.5}
+    timer, calls = _fake_batch(times)
+    t = tuning.tune_batch([(40000, 128), (3000, 64)], BCANDS, count=6, reps=2, timer=timer, batch=_fake_series,
+                          unsupported=Unsupported)
+    e = t["batch_entries"]
+    assert set(e) == {"batch/n128/m65536", "batch/n64/m4096"}
+    assert e["batch/n128/m65536"]["options"] == {"precision": "tc_fp16", "seg_cols": 512, "settle_min": 4}
+    assert e["batch/n128/m65536"]["ms"] == 3.0 and len(e["batch/n128/m65536"]["trials"]) == 4
+    assert all(c[1] == 6 and c[3] == 2 for c in calls)
+    assert {c[2] for c in calls} == {(128,) * 6, (64,) * 6}
+
+
+def test_tune_batch_rejects_disagreeing_schedules_and_skips_unsupported():
+    times = {(256, 4): 5.0, (256, 8): 4.0, (512, 4): 3.0, (512, 8): 3.5}
+    timer, _ = _fake_batch(times, disagree=(512, 8))
+    with pytest.raises(tuning.TuningError):
+        tuning.tune_batch([(4000, 64)], BCANDS, timer=timer, batch=_fake_series, unsupported=Unsupported)
+    timer, _ = _fake_batch(times, unsupported={(512, 4)})
+    t = tuning.tune_batch([(4000, 64)], BCANDS, timer=timer, batch=_fake_series, unsupported=Unsupported)
+    e = t["batch_entries"]["batch/n64/m4096"]
+    assert e["options"]["settle_min"] == 8 and e["options"]["seg_cols"] == 512
+    assert [x["ms"] for x in e["trials"]].count(None) == 1
+    timer, _ = _fake_batch(times, unsupported=set(times))
+    with pytest.raises(tuning.TuningError):
+        tuning.tune_batch([(4000, 64)], BCANDS, timer=timer, batch=_fake_series, unsupported=Unsupported)
+
+
+def test_lookup_batch_uses_the_class_with_most_work(tmp_path):
+    times = {(256, 4): 5.0, (256, 8): 4.0, (512, 4): 3.0, (512, 8): 3.5}
+    timer, _ = _fake_batch(times)
+    t = tuning.tune_batch([(40000, 128)], BCANDS, timer=timer, batch=_fake_series, unsupported=Unsupported)
+    p = tmp_path / "t.json"
+    tuning.save(t, str(p))
+    t2 = tuning.load(str(p))
+    # most work in n=128, m in (32768, 65536]
+    assert tuning.lookup_batch(t2, [40000, 50000, 3000], [128, 128, 256]) == \
+        {"precision": "tc_fp16", "seg_cols": 512, "settle_min": 4}
+    # most work in a class without an entry
+    assert tuning.lookup_batch(t2, [40000, 60000, 60000], [128, 256, 256]) == {}
+    assert tuning.lookup_batch({}, [1000], [64]) == {}
+    assert tuning.lookup(t2, 40000, 128) == {}  # single-series entries are separate
