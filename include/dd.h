@@ -521,7 +521,7 @@ typedef struct {
                              in [256, 65536] (default 512) */
     int32_t settle_min;   /* a series with more FP64 candidates than this (rows whose Gram
                              bounds overlap the best-so-far) first settles them with direct FP32
-                             full scans and their rigorous FP32 bounds (default 8; >= 0) */
+                             full scans and their rigorous FP32 bounds (default 16; >= 0) */
     int32_t reserved[2];  /* must be zero */
 } dd_batch_config_t;
 
@@ -544,6 +544,12 @@ DD_API dd_status_t dd_batch_create(dd_batch_t* batch, int32_t max_series, int64_
  * non-DD_OK result status; DD_EBUSY if another thread is using the batch. */
 DD_API dd_status_t dd_batch_search(dd_batch_t batch, int32_t count, const float* const* T_dev, const int64_t* m,
                                    const int32_t* n, dd_result_t* out, void* stream);
+
+/* The schedule of the group of subsequence length n (cfg null: back to the batch's
+ * own), e.g. the one a tuner found fastest for that n.  Takes effect at the next
+ * call, which captures a new graph.  DD_EINVAL for a null batch, n < 1 or an
+ * invalid cfg; DD_EBUSY while a search runs. */
+DD_API dd_status_t dd_batch_set_schedule(dd_batch_t batch, int32_t n, const dd_batch_config_t* cfg);
 
 /* Calls that replayed the captured graph of the previous call's shapes. */
 DD_API int64_t dd_batch_graph_replays(dd_batch_t batch);

@@ -370,20 +370,24 @@ def find_discord_batched(series, ns, precision=None, stream=None, table=None, fu
 
     ``fused=True`` (tensor-core precisions only) searches the whole list with one fused batch
     (dd_batch_*: every step one launch over all series) instead of the engine's concurrent
-    per-series searches; a table (tuning.tune_batch) then supplies the schedule (``seg_cols``,
-    ``settle_min``, precision) of the batch's dominant (n, m bucket) class, explicit arguments
-    taking precedence."""
+    per-series searches; a table (tuning.tune_batch) then supplies each group's schedule
+    (``seg_cols``, ``settle_min``) from the (n, m bucket) class with the most work among that n's
+    series, and the precision of the batch's dominant class; explicit arguments take precedence."""
     if fused:
+        per_n = {}
         if table is not None:
             from . import tuning
-            tuned = tuning.lookup_batch(table, [s.numel() for s in series], ns)
+            ms = [s.numel() for s in series]
+            tuned = tuning.lookup_batch(table, ms, ns)
             precision = precision if precision is not None else tuned.get("precision")
-            seg_cols = seg_cols if seg_cols is not None else tuned.get("seg_cols")
-            settle_min = settle_min if settle_min is not None else tuned.get("settle_min")
+            if seg_cols is None and settle_min is None:
+                per_n = tuning.lookup_batch_per_n(table, ms, ns)
         if precision is None:
             precision = "tc_fp16"
         with Batch(len(series), sum(s.numel() for s in series), max(int(x) for x in ns), precision,
                    seg_cols=seg_cols, settle_min=settle_min, **opts) as b:
+            for n_, o in per_n.items():
+                b.set_schedule(n_, o.get("seg_cols"), o.get("settle_min"))
             return b.search(series, ns, stream)
     if table is not None:
         results = [None] * len(series)
@@ -454,6 +458,19 @@ class Batch:
                                                                                        for r in out[:k]):
             raise DDError(st, "dd_batch_search")
         return [_as_result(r) if r.status == _lib.DD_OK else DDError(r.status, "batch item") for r in out[:k]]
+
+    def set_schedule(self, n: int, seg_cols=None, settle_min=None):
+        """The schedule of the series with subsequence length n (both None: the batch's own)."""
+        if seg_cols is None and settle_min is None:
+            _check(self._lib.dd_batch_set_schedule(self._ptr, int(n), None), "dd_batch_set_schedule")
+            return
+        cfg = _lib.BatchConfig()
+        ctypes.memmove(ctypes.byref(cfg), ctypes.byref(self.config), ctypes.sizeof(cfg))
+        if seg_cols is not None:
+            cfg.seg_cols = int(seg_cols)
+        if settle_min is not None:
+            cfg.settle_min = int(settle_min)
+        _check(self._lib.dd_batch_set_schedule(self._ptr, int(n), ctypes.byref(cfg)), "dd_batch_set_schedule")
 
     def graph_replays(self) -> int:
         return int(self._lib.dd_batch_graph_replays(self._ptr))

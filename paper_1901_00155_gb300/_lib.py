@@ -128,6 +128,7 @@ SIGNATURES = {
                          ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(Result),
                          ctypes.c_void_p], ctypes.c_int),
     "dd_batch_graph_replays": ([ctypes.c_void_p], ctypes.c_int64),
+    "dd_batch_set_schedule": ([ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(BatchConfig)], ctypes.c_int),
     "dd_batch_destroy": ([ctypes.c_void_p], None),
 }
 

@@ -139,6 +139,7 @@ struct BArr {
     uint32_t* r32;         // [P] rigorous FP32 upper bound of nn^2 from the settle wave (float bits)
     int32_t* list_settle;  // [P]
     int4* ranges_settle;   // [P / 128]
+    int32_t* tser_settle;  // [P / 128]
     int seg_cols;
     int settle_min;        // candidates of a series above which they are settled in FP32 first
     int bf16;
@@ -993,16 +994,18 @@ __global__ void __launch_bounds__(kPT) k_b_cands(BArr A) {
             const int right = (H - C + A.seg_cols - 1) / A.seg_cols, left = (C - L + A.seg_cols - 1) / A.seg_cols;
             const int4 r = make_int4(L, H, C, 2 * (right > left ? right : left));
             A.ranges_settle[t0 + t] = r;
+            A.tser_settle[t0 + t] = s;
             atomicMax(&G->ctrl.smax[2], r.w);
         }
     }
 }
 
-// After the FP32 settle wave: a settled row scanned every column its lower
-// bound admits, so its FP32 upper bound r32 came from its nearest column and
-// r32 - 2 margin(r32) is a rigorous lower bound of its nn^2.  bsf_s is raised
-// with them; the settled rows whose upper bound min(D + F(D), r32) still reaches
-// it go to the FP64 rescoring.
+// After the FP32 settle wave (abandoned against bsf_s, fixed during the wave): a
+// settled row whose upper bound min(D + F(D), r32) still reaches bsf_s was never
+// abandoned, so it scanned every column its lower bound admits, its FP32 upper
+// bound r32 came from its nearest column and r32 - 2 margin(r32) is a rigorous
+// lower bound of its nn^2.  bsf_s is raised with them; the settled rows whose
+// upper bound still reaches it go to the FP64 rescoring.
 __global__ void __launch_bounds__(kPT) k_b_cands2(BArr A) {
     __shared__ int s_claim;
     __shared__ unsigned shu[32];
@@ -1018,12 +1021,14 @@ __global__ void __launch_bounds__(kPT) k_b_cands2(BArr A) {
         if (!S.valid || S.ncand <= A.settle_min) continue;
         const int base = S.base, N = S.N;
         const float nf = (float)S.n;
+        const float bsf0 = __uint_as_float(A.sbsf[s]);
         unsigned lbm = A.sbsf[s];
         for (int i = tid; i < N; i += kPT) {
             const int64_t g = (int64_t)base + i;
             if (A.flag[g] != 3) continue;
             const float up = __uint_as_float(A.r32[g]);
-            if (!(up < 1e30f)) continue;
+            // a row abandoned during the settle wave (upper bound below bsf_s) did not finish
+            if (!(up < 1e30f) || fminf(b_ub(A, g), up) < bsf0) continue;
             const float lb = up - 2.f * b_margin32(up, nf, M);
             if (lb > 0.f) lbm = max(lbm, __float_as_uint(lb));
         }
@@ -1235,6 +1240,7 @@ void carve_group(BCarver& c, BArr& A, void** A16, int64_t P, int ns, int kpad) {
     A.r32 = c.take<uint32_t>((size_t)P);
     A.list_settle = c.take<int32_t>((size_t)P);
     A.ranges_settle = c.take<int4>((size_t)P / 128 + 1);
+    A.tser_settle = c.take<int32_t>((size_t)P / 128 + 1);
     A.mu_w = c.take<double>((size_t)P);
     A.c_w = c.take<double>((size_t)P);
     A.ex64 = c.take<unsigned long long>((size_t)P);
@@ -1317,11 +1323,27 @@ struct dd_batch_s {
     std::vector<dd_plan_s*> gplans;     // per group: the tensor maps and operand pointers
     std::vector<dd::BArr> garr;
     std::vector<int> slot_grouped;      // grouped position -> caller's slot
+    std::vector<std::pair<int32_t, dd_batch_config_t>> sched;  // per-n schedules (dd_batch_set_schedule)
     std::atomic<int> busy{0};
     int64_t calls = 0, replays = 0;
 };
 
 namespace {
+
+// The schedule of the group of subsequence length n.
+const dd_batch_config_t& schedule_of(const dd_batch_s* b, int32_t n) {
+    for (const auto& e : b->sched)
+        if (e.first == n) return e.second;
+    return b->cfg;
+}
+
+bool valid_config(const dd_batch_config_t& c) {
+    if (c.seg_cols < 256 || c.seg_cols > (1 << 16) || c.seg_cols % 256 != 0) return false;
+    if (c.settle_min < 0) return false;
+    for (int i = 0; i < 2; i++)
+        if (c.reserved[i] != 0) return false;
+    return true;
+}
 
 bool batch_valid_series(int64_t m, int32_t n, int32_t n_max) {
     if (n < 1 || m < 1 || (int64_t)n > m || n > n_max) return false;
@@ -1433,7 +1455,9 @@ cudaError_t enqueue_group(dd_batch_s* b, dd::BArr& A, dd_plan_s* gp, int nblocks
         f.rmin = A.rmin;
         f.ctrl_ro = ctrl;
         f.ctrl = ctrl;
-        f.abandon = 0;
+        f.abandon = 1;
+        f.tser = A.tser_settle;
+        f.sbsf = A.sbsf;
         f.work_slot = 4;
         f.min_seg_tiles = 4;
         f.target_items = 4 * sm;
@@ -1457,7 +1481,7 @@ void dd_batch_config_default(dd_batch_config_t* cfg) {
     if (!cfg) return;
     std::memset(cfg, 0, sizeof(*cfg));
     cfg->seg_cols = 512;
-    cfg->settle_min = 8;
+    cfg->settle_min = 16;
 }
 
 size_t dd_batch_footprint(int32_t max_series, int64_t max_values, int32_t n_max) {
@@ -1482,10 +1506,7 @@ dd_status_t dd_batch_create(dd_batch_t* batch, int32_t max_series, int64_t max_v
         c = *cfg;
     else
         dd_batch_config_default(&c);
-    if (c.seg_cols < 256 || c.seg_cols > (1 << 16) || c.seg_cols % 256 != 0) return DD_EINVAL;
-    if (c.settle_min < 0) return DD_EINVAL;
-    for (int i = 0; i < 2; i++)
-        if (c.reserved[i] != 0) return DD_EINVAL;
+    if (!valid_config(c)) return DD_EINVAL;
     const size_t bytes = dd_batch_footprint(max_series, max_values, n_max);
     if (bytes == 0) return DD_EINVAL;
     dd_batch_s* b = new (std::nothrow) dd_batch_s();
@@ -1530,6 +1551,19 @@ void dd_batch_destroy(dd_batch_t b) {
 }
 
 int64_t dd_batch_graph_replays(dd_batch_t b) { return b ? b->replays : -1; }
+
+dd_status_t dd_batch_set_schedule(dd_batch_t b, int32_t n, const dd_batch_config_t* cfg) {
+    if (!b || n < 1) return DD_EINVAL;
+    if (cfg && !valid_config(*cfg)) return DD_EINVAL;
+    int expected = 0;
+    if (!b->busy.compare_exchange_strong(expected, 1)) return DD_EBUSY;
+    auto it = std::find_if(b->sched.begin(), b->sched.end(), [&](const auto& e) { return e.first == n; });
+    if (it != b->sched.end()) b->sched.erase(it);
+    if (cfg) b->sched.emplace_back(n, *cfg);
+    b->gkey.clear();  // the next call captures its graph with the new schedule
+    b->busy.store(0);
+    return DD_OK;
+}
 
 }  // extern "C"
 
@@ -1594,8 +1628,9 @@ extern "C" dd_status_t dd_batch_search(dd_batch_t b, int32_t count, const float*
             A.ns = j1 - j0;
             A.n = n[order[(size_t)j0]];
             A.bf16 = b->opt.precision == DD_TC_BF16 ? 1 : 0;
-            A.seg_cols = b->cfg.seg_cols;
-            A.settle_min = b->cfg.settle_min;
+            const dd_batch_config_t& gc = schedule_of(b, A.n);
+            A.seg_cols = gc.seg_cols;
+            A.settle_min = gc.settle_min;
             A.binstart = b->W.binstart;
             A.sbsf = b->W.sbsf;
             A.res = b->W.res;

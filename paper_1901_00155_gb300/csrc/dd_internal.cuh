@@ -194,6 +194,10 @@ struct ScanArgs {
     TcBound tb;
     uint32_t* r32;
     const double* stats;      // [2] = max |t^| of the series (FP32 error bound)
+    // fused batch (batch.cu): per list tile its series, per series its best-so-far
+    // (float bits); null for a single-series search
+    const int32_t* tser;
+    const uint32_t* sbsf;
 };
 
 // Upper / lower bounds of a row's nearest-neighbour distance from its running

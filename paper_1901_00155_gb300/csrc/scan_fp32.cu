@@ -225,7 +225,8 @@ __global__ void __launch_bounds__(NT, 2) k_scan_fp32(ScanArgs a) {
                     const int ri = sm.row[tid];
                     if (ri >= 0) {
                         const float g = __uint_as_float(*((volatile const unsigned*)(a.rmin + ri)));
-                        const float bsf = __uint_as_float(*((volatile const unsigned*)&ctrl->bsf));
+                        const float bsf = __uint_as_float(
+                            *((volatile const unsigned*)(a.sbsf ? a.sbsf + a.tser[rt] : &ctrl->bsf)));
                         const float mn = fminf(sm.rmin[tid], g);
                         alive = assist ? !(fminf(row_ub(a.tb, ri, g), fp32_upper(sm.rmin[tid], nf, tmax)) < bsf)
                                        : !(mn < bsf);

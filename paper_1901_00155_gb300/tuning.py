@@ -293,3 +293,21 @@ def lookup_batch(table: dict, ms, ns) -> dict:
     top = max(work, key=lambda k: (work[k], k))
     e = table.get("batch_entries", {}).get(top)
     return dict(e["options"]) if e else {}
+
+
+def lookup_batch_per_n(table: dict, ms, ns) -> dict:
+    """Per subsequence length n of a batch: the tuned schedule of the (n, m bucket) class with the
+    most work among that n's series ({n: options}, only for classes with an entry)."""
+    if not table or table.get("version") != TABLE_VERSION:
+        return {}
+    work = {}
+    for m, n in zip(ms, ns):
+        k = (int(n), batch_key(int(m), int(n)))
+        work[k] = work.get(k, 0) + int(m) * int(n)
+    out = {}
+    for n in sorted({int(x) for x in ns}):
+        top = max((k for k in work if k[0] == n), key=lambda k: (work[k], k[1]))
+        e = table.get("batch_entries", {}).get(top[1])
+        if e:
+            out[n] = dict(e["options"])
+    return out

@@ -172,3 +172,25 @@ def test_batch_many_lengths_and_capacity():
         assert e.value.status == 2  # DD_ENOMEM
         with pytest.raises(dd.DDError):
             b.search([_cuda(items[0][0])] * (len(items) + 1), [items[0][1]] * (len(items) + 1))
+
+
+def test_batch_schedules_change_speed_only():
+    """Per-n schedules (columns per work item, settle threshold 0 = every candidate settled in
+    FP32 first, or never) give the same exact results; a new schedule recaptures the graph."""
+    dd = _dd()
+    items = _random_mix(31, 24, m_hi=9000, ns=(64, 128, 256))
+    series = [_cuda(T) for T, _ in items]
+    ns = [n for _, n in items]
+    with dd.Batch(len(items), sum(T.size for T, _ in items), 256, "tc_fp16") as b:
+        ref = b.search(series, ns)
+        for sched in ({64: (256, 0), 128: (1024, 0), 256: (512, 0)},
+                      {64: (2048, 10 ** 6), 128: (256, 10 ** 6), 256: (256, 1)}):
+            for n, (sc, st) in sched.items():
+                b.set_schedule(n, sc, st)
+            got = b.search(series, ns)
+            for r, q in zip(ref, got):
+                assert (r.index, r.nn_distance) == (q.index, q.nn_distance)
+        assert b.graph_replays() == 0
+        b.set_schedule(64)  # back to the batch's own
+        again = b.search(series, ns)
+        assert [(r.index, r.nn_distance) for r in again] == [(r.index, r.nn_distance) for r in ref]

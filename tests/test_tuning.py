@@ -231,3 +231,15 @@ def test_lookup_batch_uses_the_class_with_most_work(tmp_path):
     assert tuning.lookup_batch(t2, [40000, 60000, 60000], [128, 256, 256]) == {}
     assert tuning.lookup_batch({}, [1000], [64]) == {}
     assert tuning.lookup(t2, 40000, 128) == {}  # single-series entries are separate
+
+
+def test_lookup_batch_per_n():
+    times = {(256, 4): 5.0, (256, 8): 4.0, (512, 4): 3.0, (512, 8): 3.5}
+    timer, _ = _fake_batch(times)
+    t = tuning.tune_batch([(40000, 128)], BCANDS, timer=timer, batch=_fake_series, unsupported=Unsupported)
+    times2 = {(256, 4): 1.0, (256, 8): 4.0, (512, 4): 3.0, (512, 8): 3.5}
+    timer2, _ = _fake_batch(times2)
+    t = tuning.tune_batch([(3000, 64)], BCANDS, timer=timer2, batch=_fake_series, unsupported=Unsupported, table=t)
+    per_n = tuning.lookup_batch_per_n(t, [40000, 3000, 2500, 5000, 9000], [128, 64, 64, 256, 128])
+    assert per_n == {128: {"precision": "tc_fp16", "seg_cols": 512, "settle_min": 4},
+                     64: {"precision": "tc_fp16", "seg_cols": 256, "settle_min": 4}}
