@@ -409,6 +409,9 @@ def main():
     ap.add_argument("--no-probe", action="store_true", help="skip the FP16 / FP32 / FP64 peak probes")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 512-series batched search")
+    ap.add_argument("--batch-only", action="store_true",
+                    help="run only the 512-series batch (fused and engine) and print its JSON object")
+    ap.add_argument("--batch-reps", type=int, default=5, help="timed fused-batch calls (median)")
     ap.add_argument("--eager", action="store_true",
                     help="enqueue each search's kernels directly instead of replaying its CUDA graph "
                          "(per-kernel profilers cannot profile kernels of graphs with conditional nodes)")
@@ -439,6 +442,10 @@ def main():
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    if args.batch_only:
+        print(json.dumps(_batch(dd, "tc_fp16" if args.precision in ("all", "best") else args.precision,
+                                reps=max(1, args.batch_reps))))
+        return
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     if world > 1:
         dist.init_process_group("nccl", device_id=dev)
@@ -557,7 +564,7 @@ def main():
     side_form = "tc_fp16" if "tc_fp16" in results else head_form
     batch = serve = None
     if not args.no_batch:
-        batch = _batch(dd, side_form)
+        batch = _batch(dd, side_form, reps=max(1, args.batch_reps))
     if not args.no_serve:
         serve = _serve(dd, side_form)
     exh = None

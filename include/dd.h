@@ -521,7 +521,7 @@ typedef struct {
                              in [256, 65536] (default 512) */
     int32_t settle_min;   /* a series with more FP64 candidates than this (rows whose Gram
                              bounds overlap the best-so-far) first settles them with direct FP32
-                             full scans and their rigorous FP32 bounds (default 16; >= 0) */
+                             full scans and their rigorous FP32 bounds (default 8; >= 0) */
     int32_t reserved[2];  /* must be zero */
 } dd_batch_config_t;
 

@@ -1481,7 +1481,7 @@ void dd_batch_config_default(dd_batch_config_t* cfg) {
     if (!cfg) return;
     std::memset(cfg, 0, sizeof(*cfg));
     cfg->seg_cols = 512;
-    cfg->settle_min = 16;
+    cfg->settle_min = 8;
 }
 
 size_t dd_batch_footprint(int32_t max_series, int64_t max_values, int32_t n_max) {
