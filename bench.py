@@ -148,7 +148,9 @@ class ClockSampler:
 
 def _kernel_traffic(precision: str):
     """dram bytes per launch of the distance kernel from the committed ncu
-    summary, or None if the kernel source changed since it was taken."""
+    summary, or None if a source it depends on changed since it was taken: the
+    kernel itself and the search that schedules its waves (the sha-256 of the
+    files' bytes concatenated in the listed order, first 16 hex digits)."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
@@ -158,12 +160,13 @@ def _kernel_traffic(precision: str):
     ent = d.get(precision)
     if not ent:
         return None
-    src = os.path.join(ROOT, "paper_1901_00155_gb300", "csrc", ent["source"])
     try:
-        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        blob = b"".join(open(os.path.join(ROOT, "paper_1901_00155_gb300", "csrc", f), "rb").read()
+                        for f in ent["sources"])
     except Exception:
         return None
-    return ent["dram_bytes_per_launch"] if h == ent.get("source_sha256_16") else None
+    h = hashlib.sha256(blob).hexdigest()[:16]
+    return ent["dram_bytes_per_launch"] if h == ent.get("sources_sha256_16") else None
 
 
 def _exhaustive(dd, Td, m: int, n: int, forms, peaks, sms: int, rows: int = 8192, reps: int = 3) -> dict:

@@ -542,6 +542,21 @@ __global__ void __launch_bounds__(256) k_complete32(ListRef in, const uint32_t* 
     if ((threadIdx.x & 31) == 0 && best > bsf) atomicMax(&ctrl->bsf, best);
 }
 
+// Appends the rows of src to the list dst[0, *cnt) (one block): at most cap
+// entries in all; *cnt becomes the new length.
+__global__ void __launch_bounds__(1024) k_append_list(ListRef src, int32_t* __restrict__ dst, int* __restrict__ cnt,
+                                                      int cap) {
+    __shared__ int n0;
+    if (threadIdx.x == 0) n0 = *cnt;
+    __syncthreads();
+    const int ns = *src.cnt_dev;
+    const int off = src.off_dev ? *src.off_dev : 0;
+    const int take = min(ns, max(cap - n0, 0));
+    for (int r = threadIdx.x; r < take; r += blockDim.x) dst[n0 + r] = src.base[off + r];
+    __syncthreads();
+    if (threadIdx.x == 0) *cnt = n0 + take;
+}
+
 __global__ void k_copy_list(ListRef src, int32_t* __restrict__ dst, int* __restrict__ cnt_out) {
     const int cnt = *src.cnt_dev;
     const int off = src.off_dev ? *src.off_dev : 0;
@@ -861,6 +876,13 @@ struct Seq {
     }
 
     // dst[0, *src.cnt) = src rows, count into cnt_out
+    // Appends src to the list at dst whose count is *cnt (at most N entries).
+    void append(ListRef src, int32_t* dst, const int* cnt) {
+        k_append_list<<<1, 1024, 0, s>>>(src, dst, const_cast<int*>(cnt), (int)p->N);
+        p->launches++;
+        check();
+    }
+
     void copy_list(ListRef src, int32_t* dst, int* cnt_out) {
         k_copy_list<<<p->sm_count * 2, 256, 0, s>>>(src, dst, cnt_out);
         p->launches++;
@@ -977,19 +999,25 @@ cudaError_t launch_search(dd_plan_s* p, const float* T, dd_result_t* out_dev, cu
             }
         }
         join();
-        // Algorithm 3 (PotentialDiscord): the Cand rows (rarest SAX words).
+        // Algorithm 3 (PotentialDiscord): full scans of the Cand rows (rarest SAX
+        // words).  They run in one wave with the rows of largest upper bound
+        // (the likeliest discords), which raise the best-so-far further: the
+        // top rows are selected first, from the first wave's bounds, and the
+        // Cand rows appended to their list (a row in both is scanned twice in
+        // the wave; Cand rows beyond N entries stay alive for the rest wave).
+        // Few rows die in these waves, so the selections read every row; a row
+        // once ruled out stays ruled out (the best-so-far only grows, upper
+        // bounds only shrink), so the final candidates are a subset of the
+        // last wave's rows.
         ListRef cand = q.cand_list(p->list[0]);
-        q.full(DD_WAVE_CAND, cand);
-        // Raise the best-so-far further: full scans of the rows with the
-        // largest upper bounds (the likeliest discords) next.  Few rows die in
-        // the Cand wave, so the selections read every row; a row once ruled out
-        // stays ruled out (the best-so-far only grows, upper bounds only
-        // shrink), so the final candidates are a subset of the last wave's rows.
         const ListRef alive = all;
         if (o.refine_k > 0) {
             q.topk(alive, o.refine_k);
-            ListRef top = q.compact(alive, p->list[2], 1);
-            q.full(DD_WAVE_TOP, top);
+            ListRef first = q.compact(alive, p->list[2], 1);
+            q.append(cand, p->list[2], first.cnt_dev);
+            q.full(DD_WAVE_CAND, first);
+        } else {
+            q.full(DD_WAVE_CAND, cand);
         }
         // rows still alive after the top wave (recomputed below if more waves run)
         rest = q.compact(alive, p->list[2], 0);
