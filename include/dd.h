@@ -521,8 +521,10 @@ typedef struct {
                              in [256, 65536] (default 512) */
     int32_t settle_min;   /* a series with more FP64 candidates than this (rows whose Gram
                              bounds overlap the best-so-far) first settles them with direct FP32
-                             full scans and their rigorous FP32 bounds (default 8; >= 0) */
-    int32_t reserved[2];  /* must be zero */
+                             full scans and their rigorous FP32 bounds (default 4; >= 0) */
+    int32_t settle_rows;  /* rows per tile of those FP32 full scans: 32, 64 (default) or 128 (one
+                             series' candidates per tile) */
+    int32_t reserved[1];  /* must be zero */
 } dd_batch_config_t;
 
 DD_API void dd_batch_config_default(dd_batch_config_t* cfg);

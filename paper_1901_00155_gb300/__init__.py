@@ -362,7 +362,7 @@ def group_by_tuned_options(ms, ns, table, precision=None, **opts):
 
 
 def find_discord_batched(series, ns, precision=None, stream=None, table=None, fused=False, seg_cols=None,
-                         settle_min=None, **opts):
+                         settle_min=None, settle_rows=None, **opts):
     """Independent searches over CUDA float32 tensors of possibly different lengths.  With a
     tuning table, each series runs with the options tuned for its (n, m bucket), explicit options
     taking precedence: one batched call per distinct option set, results in the input order.
@@ -371,7 +371,7 @@ def find_discord_batched(series, ns, precision=None, stream=None, table=None, fu
     ``fused=True`` (tensor-core precisions only) searches the whole list with one fused batch
     (dd_batch_*: every step one launch over all series) instead of the engine's concurrent
     per-series searches; a table (tuning.tune_batch) then supplies each group's schedule
-    (``seg_cols``, ``settle_min``) from the (n, m bucket) class with the most work among that n's
+    (``seg_cols``, ``settle_min``, ``settle_rows``) from the (n, m bucket) class with the most work among that n's
     series, and the precision of the batch's dominant class; explicit arguments take precedence."""
     if fused:
         per_n = {}
@@ -380,14 +380,14 @@ def find_discord_batched(series, ns, precision=None, stream=None, table=None, fu
             ms = [s.numel() for s in series]
             tuned = tuning.lookup_batch(table, ms, ns)
             precision = precision if precision is not None else tuned.get("precision")
-            if seg_cols is None and settle_min is None:
+            if seg_cols is None and settle_min is None and settle_rows is None:
                 per_n = tuning.lookup_batch_per_n(table, ms, ns)
         if precision is None:
             precision = "tc_fp16"
         with Batch(len(series), sum(s.numel() for s in series), max(int(x) for x in ns), precision,
-                   seg_cols=seg_cols, settle_min=settle_min, **opts) as b:
+                   seg_cols=seg_cols, settle_min=settle_min, settle_rows=settle_rows, **opts) as b:
             for n_, o in per_n.items():
-                b.set_schedule(n_, o.get("seg_cols"), o.get("settle_min"))
+                b.set_schedule(n_, o.get("seg_cols"), o.get("settle_min"), o.get("settle_rows"))
             return b.search(series, ns, stream)
     if table is not None:
         results = [None] * len(series)
@@ -425,7 +425,7 @@ class Batch:
     ``find_discord`` on the series alone."""
 
     def __init__(self, max_series: int, max_values: int, n_max: int, precision="tc_fp16", seg_cols=None,
-                 settle_min=None, **opts):
+                 settle_min=None, settle_rows=None, **opts):
         self._lib = _lib.load()
         self.options = _options(precision, **opts)
         cfg = _lib.BatchConfig()
@@ -434,6 +434,8 @@ class Batch:
             cfg.seg_cols = int(seg_cols)
         if settle_min is not None:
             cfg.settle_min = int(settle_min)
+        if settle_rows is not None:
+            cfg.settle_rows = int(settle_rows)
         self.config = cfg
         self._ptr = ctypes.c_void_p()
         _check(self._lib.dd_batch_create(ctypes.byref(self._ptr), int(max_series), int(max_values), int(n_max),
@@ -459,9 +461,9 @@ class Batch:
             raise DDError(st, "dd_batch_search")
         return [_as_result(r) if r.status == _lib.DD_OK else DDError(r.status, "batch item") for r in out[:k]]
 
-    def set_schedule(self, n: int, seg_cols=None, settle_min=None):
-        """The schedule of the series with subsequence length n (both None: the batch's own)."""
-        if seg_cols is None and settle_min is None:
+    def set_schedule(self, n: int, seg_cols=None, settle_min=None, settle_rows=None):
+        """The schedule of the series with subsequence length n (all None: the batch's own)."""
+        if seg_cols is None and settle_min is None and settle_rows is None:
             _check(self._lib.dd_batch_set_schedule(self._ptr, int(n), None), "dd_batch_set_schedule")
             return
         cfg = _lib.BatchConfig()
@@ -470,6 +472,8 @@ class Batch:
             cfg.seg_cols = int(seg_cols)
         if settle_min is not None:
             cfg.settle_min = int(settle_min)
+        if settle_rows is not None:
+            cfg.settle_rows = int(settle_rows)
         _check(self._lib.dd_batch_set_schedule(self._ptr, int(n), ctypes.byref(cfg)), "dd_batch_set_schedule")
 
     def graph_replays(self) -> int:

@@ -62,7 +62,8 @@ DD_SERIES_HOST = 1
 
 
 class BatchConfig(ctypes.Structure):
-    _fields_ = [("seg_cols", ctypes.c_int32), ("settle_min", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
+    _fields_ = [("seg_cols", ctypes.c_int32), ("settle_min", ctypes.c_int32), ("settle_rows", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 1)]
 
 
 class Wave(ctypes.Structure):

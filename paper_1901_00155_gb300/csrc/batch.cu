@@ -138,10 +138,11 @@ struct BArr {
     int64_t* cbase;        // [P] first rescoring chunk of each candidate
     uint32_t* r32;         // [P] rigorous FP32 upper bound of nn^2 from the settle wave (float bits)
     int32_t* list_settle;  // [P]
-    int4* ranges_settle;   // [P / 128]
-    int32_t* tser_settle;  // [P / 128]
+    int4* ranges_settle;   // [P / 32] (tiles of settle_rows rows)
+    int32_t* tser_settle;  // [P / 32]
     int seg_cols;
     int settle_min;        // candidates of a series above which they are settled in FP32 first
+    int settle_rows;       // rows per settle tile (32, 64 or 128)
     int bf16;
 };
 
@@ -903,11 +904,11 @@ __device__ __forceinline__ float b_margin32(float e, float n, float M) {
 // top rows and survivors whose upper bound reaches the raised bsf_s.  Up to
 // settle_min of them go to the FP64 rescoring at once; more (rows whose Gram
 // bounds overlap, e.g. the windows around an anomaly of a noisy periodic
-// series) are first settled by direct FP32 full scans (one 128-row FP32 tile
-// costs about as much as eight rows of the column-by-column FP32 screen of the
-// rescoring, hence the default of 8): they are written in mean
-// order into whole tiles of the settle list, each tile's column range the union
-// of its rows' lower-bound ranges.
+// series) are first settled by direct FP32 full scans, whose tiles of
+// settle_rows rows share every staged column among their rows (a few rows
+// already outrun the column-by-column FP32 screen of the rescoring): they are
+// written in mean order into whole tiles of the settle list, each tile's
+// column range the union of its rows' lower-bound ranges.
 __global__ void __launch_bounds__(kPT) k_b_cands(BArr A) {
     __shared__ int s_claim, s_t0;
     __shared__ unsigned shu[32];
@@ -951,14 +952,15 @@ __global__ void __launch_bounds__(kPT) k_b_cands(BArr A) {
             }
             continue;
         }
-        const int ntile = (cnt + kBTop - 1) / kBTop;
+        const int TR = A.settle_rows;  // rows per settle tile
+        const int ntile = (cnt + TR - 1) / TR;
         if (tid == 0) {
             s_t0 = atomicAdd(&G->settle_tiles, ntile);
-            atomicAdd(&G->settle_rows, ntile * kBTop);
+            atomicAdd(&G->settle_rows, ntile * TR);
         }
         __syncthreads();
         const int t0 = s_t0;
-        int32_t* out = A.list_settle + (int64_t)t0 * kBTop;
+        int32_t* out = A.list_settle + (int64_t)t0 * TR;
         int run = 0;
         for (int p0 = 0; p0 < N; p0 += kPT) {
             const int p = p0 + tid;
@@ -978,13 +980,13 @@ __global__ void __launch_bounds__(kPT) k_b_cands(BArr A) {
             }
             run += total;
         }
-        for (int j = cnt + tid; j < ntile * kBTop; j += kPT) out[j] = -1;
+        for (int j = cnt + tid; j < ntile * TR; j += kPT) out[j] = -1;
         __syncthreads();
         for (int t = tid; t < ntile; t += kPT) {
             int L = base + N, H = base;
-            const int rows = min(kBTop, cnt - t * kBTop);
+            const int rows = min(TR, cnt - t * TR);
             for (int r = 0; r < rows; r++) {
-                const int g = out[(int64_t)t * kBTop + r];
+                const int g = out[(int64_t)t * TR + r];
                 int l, h;
                 b_lb_range(A, S, s, g, b_ub(A, g), l, h);
                 L = min(L, l);
@@ -1239,8 +1241,8 @@ void carve_group(BCarver& c, BArr& A, void** A16, int64_t P, int ns, int kpad) {
     A.P2 = c.take<double>((size_t)P + 64);
     A.r32 = c.take<uint32_t>((size_t)P);
     A.list_settle = c.take<int32_t>((size_t)P);
-    A.ranges_settle = c.take<int4>((size_t)P / 128 + 1);
-    A.tser_settle = c.take<int32_t>((size_t)P / 128 + 1);
+    A.ranges_settle = c.take<int4>((size_t)P / 32 + 1);
+    A.tser_settle = c.take<int32_t>((size_t)P / 32 + 1);
     A.mu_w = c.take<double>((size_t)P);
     A.c_w = c.take<double>((size_t)P);
     A.ex64 = c.take<unsigned long long>((size_t)P);
@@ -1340,8 +1342,8 @@ const dd_batch_config_t& schedule_of(const dd_batch_s* b, int32_t n) {
 bool valid_config(const dd_batch_config_t& c) {
     if (c.seg_cols < 256 || c.seg_cols > (1 << 16) || c.seg_cols % 256 != 0) return false;
     if (c.settle_min < 0) return false;
-    for (int i = 0; i < 2; i++)
-        if (c.reserved[i] != 0) return false;
+    if (c.settle_rows != 32 && c.settle_rows != 64 && c.settle_rows != 128) return false;
+    if (c.reserved[0] != 0) return false;
     return true;
 }
 
@@ -1458,6 +1460,7 @@ cudaError_t enqueue_group(dd_batch_s* b, dd::BArr& A, dd_plan_s* gp, int nblocks
         f.abandon = 1;
         f.tser = A.tser_settle;
         f.sbsf = A.sbsf;
+        f.bm = A.settle_rows;
         f.work_slot = 4;
         f.min_seg_tiles = 4;
         f.target_items = 4 * sm;
@@ -1481,7 +1484,8 @@ void dd_batch_config_default(dd_batch_config_t* cfg) {
     if (!cfg) return;
     std::memset(cfg, 0, sizeof(*cfg));
     cfg->seg_cols = 512;
-    cfg->settle_min = 8;
+    cfg->settle_min = 4;
+    cfg->settle_rows = 64;
 }
 
 size_t dd_batch_footprint(int32_t max_series, int64_t max_values, int32_t n_max) {
@@ -1631,6 +1635,7 @@ extern "C" dd_status_t dd_batch_search(dd_batch_t b, int32_t count, const float*
             const dd_batch_config_t& gc = schedule_of(b, A.n);
             A.seg_cols = gc.seg_cols;
             A.settle_min = gc.settle_min;
+            A.settle_rows = gc.settle_rows;
             A.binstart = b->W.binstart;
             A.sbsf = b->W.sbsf;
             A.res = b->W.res;

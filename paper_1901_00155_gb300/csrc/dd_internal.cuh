@@ -198,6 +198,7 @@ struct ScanArgs {
     // (float bits); null for a single-series search
     const int32_t* tser;
     const uint32_t* sbsf;
+    int bm;                   // rows per tile: 0 or 128 (default), 64, 32
 };
 
 // Upper / lower bounds of a row's nearest-neighbour distance from its running

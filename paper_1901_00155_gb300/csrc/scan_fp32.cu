@@ -26,12 +26,17 @@
 namespace dd {
 namespace {
 
-constexpr int BM = kF32BM, BN = kF32BN, BK = kF32BK, NT = kF32Threads;
-constexpr int SROW = BM + 4;  // floats per k-row of a transposed tile (keeps 16-B alignment)
+constexpr int BN = kF32BN, BK = kF32BK, NT = kF32Threads;
 
+// BM rows per tile: 128 (every wave of a search), or 64 / 32 (the fused batch's
+// settle tiles, which hold one series' few candidates).  A thread's micro-tile is
+// BM / 16 rows x 8 columns.
+template <int BM>
 struct __align__(16) F32Smem {
+    static constexpr int SROW = BM + 4;  // floats per k-row of the transposed row tile (16-B aligned)
+    static constexpr int SCOL = BN + 4;
     float a[2][BK][SROW];
-    float b[2][BK][SROW];
+    float b[2][BK][SCOL];
     int row[BM];
     int col[BN];
     float rmin[BM];
@@ -54,7 +59,8 @@ __device__ __forceinline__ void cp_async_wait() {
 }
 
 // Stage k-chunk [k0, k0+BK) of the tile's rows and columns (transposed).
-__device__ __forceinline__ void stage_chunk(F32Smem& sm, int buf, const float* __restrict__ t32, int k0, int n) {
+template <int BM>
+__device__ __forceinline__ void stage_chunk(F32Smem<BM>& sm, int buf, const float* __restrict__ t32, int k0, int n) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int k = k0 + lane;
     const bool kin = k < n;
@@ -108,9 +114,11 @@ __device__ __forceinline__ float fp32_upper(float e, float n, float M) {
     return e + 2.f * ((gn + 4.f * u) * e + 8.f * u * M * sqrtf(n * e) + n * mu6 * mu6) + 1e-30f;
 }
 
+template <int BM>
 __global__ void __launch_bounds__(NT, 2) k_scan_fp32(ScanArgs a) {
+    constexpr int RI = BM / 16;  // rows of a thread's micro-tile
     extern __shared__ __align__(16) unsigned char smraw[];
-    F32Smem& sm = *reinterpret_cast<F32Smem*>(smraw);
+    F32Smem<BM>& sm = *reinterpret_cast<F32Smem<BM>*>(smraw);
     const Ctrl* ctrl = a.ctrl_ro;
     if (ctrl->nonfinite || ctrl->degenerate) return;
     const int cnt = *a.rows.cnt_dev;
@@ -266,9 +274,9 @@ __global__ void __launch_bounds__(NT, 2) k_scan_fp32(ScanArgs a) {
             }
 
             // acc2[i][q] holds columns 2q, 2q + 1 of row i
-            f2_t acc2[8][4];
+            f2_t acc2[RI][4];
 #pragma unroll
-            for (int i = 0; i < 8; i++)
+            for (int i = 0; i < RI; i++)
 #pragma unroll
                 for (int q = 0; q < 4; q++) acc2[i][q] = 0ull;
 
@@ -286,14 +294,24 @@ __global__ void __launch_bounds__(NT, 2) k_scan_fp32(ScanArgs a) {
                 __syncthreads();
 #pragma unroll 8
                 for (int kk = 0; kk < BK; kk++) {
-                    const float4 a0 = *reinterpret_cast<const float4*>(&sm.a[buf][kk][ty * 4]);
-                    const float4 a1 = *reinterpret_cast<const float4*>(&sm.a[buf][kk][64 + ty * 4]);
+                    float x[RI];
+                    if constexpr (BM == 128) {
+                        const float4 a0 = *reinterpret_cast<const float4*>(&sm.a[buf][kk][ty * 4]);
+                        const float4 a1 = *reinterpret_cast<const float4*>(&sm.a[buf][kk][64 + ty * 4]);
+                        x[0] = a0.x; x[1] = a0.y; x[2] = a0.z; x[3] = a0.w;
+                        x[4] = a1.x; x[5] = a1.y; x[6] = a1.z; x[7] = a1.w;
+                    } else if constexpr (BM == 64) {
+                        const float4 a0 = *reinterpret_cast<const float4*>(&sm.a[buf][kk][ty * 4]);
+                        x[0] = a0.x; x[1] = a0.y; x[2] = a0.z; x[3] = a0.w;
+                    } else {
+                        const float2 a0 = *reinterpret_cast<const float2*>(&sm.a[buf][kk][ty * 2]);
+                        x[0] = a0.x; x[1] = a0.y;
+                    }
                     const ulonglong2 b0 = *reinterpret_cast<const ulonglong2*>(&sm.b[buf][kk][tx * 4]);
                     const ulonglong2 b1 = *reinterpret_cast<const ulonglong2*>(&sm.b[buf][kk][64 + tx * 4]);
-                    const float x[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
                     const f2_t y2[4] = {b0.x, b0.y, b1.x, b1.y};
 #pragma unroll
-                    for (int i = 0; i < 8; i++) {
+                    for (int i = 0; i < RI; i++) {
                         const f2_t xx = f2_dup(x[i]);
 #pragma unroll
                         for (int q = 0; q < 4; q++) acc2[i][q] = f2_fma_sq(f2_sub(xx, y2[q]), acc2[i][q]);
@@ -306,8 +324,8 @@ __global__ void __launch_bounds__(NT, 2) k_scan_fp32(ScanArgs a) {
 #pragma unroll
             for (int j = 0; j < 8; j++) cjr[j] = sm.col[j < 4 ? tx * 4 + j : 64 + tx * 4 + (j - 4)];
 #pragma unroll
-            for (int i = 0; i < 8; i++) {
-                const int r = i < 4 ? ty * 4 + i : 64 + ty * 4 + (i - 4);
+            for (int i = 0; i < RI; i++) {
+                const int r = BM == 128 ? (i < 4 ? ty * 4 + i : 64 + ty * 4 + (i - 4)) : ty * RI + i;
                 const int ri = sm.row[r];
                 float mn = INFINITY;
 #pragma unroll
@@ -356,16 +374,24 @@ __global__ void __launch_bounds__(NT, 2) k_scan_fp32(ScanArgs a) {
 
 int scan_fp32_grid(const dd_plan_s* p) { return p->sm_count * 2; }
 
-cudaError_t launch_scan_fp32(const ScanArgs& a, int grid, cudaStream_t s) {
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_scan_fp32, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)sizeof(F32Smem));
+template <int BM>
+cudaError_t launch_bm(const ScanArgs& a, int grid, cudaStream_t s) {
+    static std::atomic<int> attr_set{0};
+    if (!attr_set.load()) {
+        cudaError_t e = cudaFuncSetAttribute(k_scan_fp32<BM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)sizeof(F32Smem<BM>));
         if (e != cudaSuccess) return e;
-        attr_set = true;
+        attr_set.store(1);
     }
-    k_scan_fp32<<<grid, NT, sizeof(F32Smem), s>>>(a);
+    k_scan_fp32<BM><<<grid, NT, sizeof(F32Smem<BM>), s>>>(a);
     return cudaGetLastError();
+}
+
+cudaError_t launch_scan_fp32(const ScanArgs& a, int grid, cudaStream_t s) {
+    if (a.bm == 64) return launch_bm<64>(a, grid, s);
+    if (a.bm == 32) return launch_bm<32>(a, grid, s);
+    if (a.bm != 0 && a.bm != 128) return cudaErrorInvalidValue;
+    return launch_bm<128>(a, grid, s);
 }
 
 }  // namespace dd

@@ -16,7 +16,8 @@ series of that length class with the same n.  Tables are plain JSON.
 
 The fused batch (dd_batch_*) has its own schedule: columns per work item of its full-scan waves
 (seg_cols), the candidate count above which a series settles its candidates with direct FP32 full
-scans before the FP64 rescoring (settle_min), and the tensor-core precision.  tune_batch times them
+scans before the FP64 rescoring (settle_min), the rows of those FP32 tiles (settle_rows), and the
+tensor-core precision.  tune_batch times them
 on a seeded batch of each (n, m bucket) class and keeps the fastest under "batch_entries"; every
 candidate schedule must return the same discord for every series (exact FP64 rescoring: the same
 index, distances within 1e-9 relative).
@@ -180,9 +181,10 @@ def load(path: str) -> dict:
 
 # Schedules of the fused batch that change only its speed.
 BATCH_CANDIDATES = tuple(
-    {"precision": "tc_fp16", "seg_cols": sc, "settle_min": st}
+    {"precision": "tc_fp16", "seg_cols": sc, "settle_min": st, "settle_rows": sr}
     for sc in (256, 512, 1024)
     for st in (4, 8, 16, 32)
+    for sr in (32, 64, 128)
 )
 
 

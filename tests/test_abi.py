@@ -148,7 +148,7 @@ def test_batch_entry_points_reject_bad_arguments_without_device_work():
     lib = _lib.load()
     cfg = _lib.BatchConfig()
     lib.dd_batch_config_default(ctypes.byref(cfg))
-    assert cfg.seg_cols == 512 and cfg.settle_min == 8 and list(cfg.reserved) == [0, 0]
+    assert cfg.seg_cols == 512 and cfg.settle_min == 4 and cfg.settle_rows == 64 and list(cfg.reserved) == [0]
     fp = lib.dd_batch_footprint(512, 10_200_000, 256)
     assert 10 << 30 < fp < 16 << 30  # two 16-bit operand matrices of ~10.4 M rows x 256 dominate
     assert lib.dd_batch_footprint(0, 1000, 64) == 0
@@ -171,8 +171,13 @@ def test_batch_entry_points_reject_bad_arguments_without_device_work():
     lib.dd_batch_config_default(ctypes.byref(cfg))
     cfg.settle_min = -1
     assert lib.dd_batch_create(ctypes.byref(b), 4, 1000, 64, ctypes.byref(o), ctypes.byref(cfg)) == _lib.DD_EINVAL
+    for bad in (0, 16, 96, 256):
+        lib.dd_batch_config_default(ctypes.byref(cfg))
+        cfg.settle_rows = bad
+        assert lib.dd_batch_create(ctypes.byref(b), 4, 1000, 64, ctypes.byref(o), ctypes.byref(cfg)) == \
+            _lib.DD_EINVAL
     lib.dd_batch_config_default(ctypes.byref(cfg))
-    cfg.reserved[1] = 3
+    cfg.reserved[0] = 3
     assert lib.dd_batch_create(ctypes.byref(b), 4, 1000, 64, ctypes.byref(o), ctypes.byref(cfg)) == _lib.DD_EINVAL
     assert lib.dd_batch_create(None, 4, 1000, 64, ctypes.byref(o), None) == _lib.DD_EINVAL
     assert lib.dd_batch_create(ctypes.byref(b), 0, 1000, 64, ctypes.byref(o), None) == _lib.DD_EINVAL

@@ -176,17 +176,19 @@ def test_batch_many_lengths_and_capacity():
 
 def test_batch_schedules_change_speed_only():
     """Per-n schedules (columns per work item, settle threshold 0 = every candidate settled in
-    FP32 first, or never) give the same exact results; a new schedule recaptures the graph."""
+    FP32 first, or never, FP32 settle tiles of 32, 64 or 128 rows) give the same exact results; a
+    new schedule recaptures the graph."""
     dd = _dd()
     items = _random_mix(31, 24, m_hi=9000, ns=(64, 128, 256))
     series = [_cuda(T) for T, _ in items]
     ns = [n for _, n in items]
     with dd.Batch(len(items), sum(T.size for T, _ in items), 256, "tc_fp16") as b:
         ref = b.search(series, ns)
-        for sched in ({64: (256, 0), 128: (1024, 0), 256: (512, 0)},
-                      {64: (2048, 10 ** 6), 128: (256, 10 ** 6), 256: (256, 1)}):
-            for n, (sc, st) in sched.items():
-                b.set_schedule(n, sc, st)
+        for sched in ({64: (256, 0, 32), 128: (1024, 0, 64), 256: (512, 0, 128)},
+                      {64: (512, 0, 128), 128: (512, 0, 32), 256: (256, 0, 32)},
+                      {64: (2048, 10 ** 6, 64), 128: (256, 10 ** 6, 64), 256: (256, 1, 64)}):
+            for n, (sc, st, sr) in sched.items():
+                b.set_schedule(n, sc, st, sr)
             got = b.search(series, ns)
             for r, q in zip(ref, got):
                 assert (r.index, r.nn_distance) == (q.index, q.nn_distance)
