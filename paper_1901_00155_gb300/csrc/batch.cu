@@ -1471,7 +1471,8 @@ cudaError_t enqueue_group(dd_batch_s* b, dd::BArr& A, dd_plan_s* gp, int nblocks
         if ((e = launch_scan_fp32(f, 2 * sm, s)) != cudaSuccess) return e;
     }
     k_b_cands2<<<gser, kPT, 0, s>>>(A);
-    k_b_rescore<<<2 * sm, 256, 0, s>>>(A);
+    // the warp-per-column screen is latency-bound: up to 5 resident blocks per SM (48 registers)
+    k_b_rescore<<<8 * sm, 256, 0, s>>>(A);
     k_b_best<<<sm, 256, 0, s>>>(A);
     return cudaGetLastError();
 }
