@@ -249,7 +249,8 @@ DD_API dd_status_t dd_find_discords(dd_plan_t plan, const float* T_dev, int32_t 
  * out[k] (host memory); out[k].status reports each series' own error.
  * Runs on a temporary engine (below) with up to 32 workers, longest series
  * first; waits for `stream` first so that the series are ready.  Returns
- * the first error met, DD_OK if every search succeeded. */
+ * the first error met, DD_OK if every search succeeded.  For the tensor-core
+ * forms the fused batch (dd_batch_*, below) searches many series faster. */
 DD_API dd_status_t dd_find_discord_batched(int32_t count, const float* const* T_dev, const int64_t* m, const int32_t* n,
                                     const dd_options_t* opt, dd_result_t* out, void* stream);
 
