@@ -71,7 +71,7 @@ struct Ctrl {
     int cond[8];                  // value each conditional graph node of the search took (1 = body ran)
     int cticket[kCompactSites];   // block tickets of each compaction (blocks take their place in start order)
     int stat_ticket[2];           // blocks done with the two passes of the Eq. 2 statistics
-    int topk_ticket[4];           // blocks done with each top-k histogram pass (two selections per search)
+    int topk_ticket[6];           // blocks done with each top-k histogram pass (three selections per search)
     int best_ticket;              // blocks done with the exact maximum over the candidates
     int resc_nch;                 // FP64 rescoring: column chunks of the longest candidate range
     int topk_bin;                 // top-k select: bin of the first pass holding the k-th row (-1: take all)

@@ -624,6 +624,7 @@ __global__ void k_sanitize_rows(const int32_t* __restrict__ rows, int count, int
 constexpr int kSegCols = 512;
 constexpr int kSegColsFull = 128;  // FP32 full scans: one column tile per item, so few rows spread over the SMs
 constexpr int kSettleMin = 64;   // candidate rows above which the Gram form settles them in FP32 first
+constexpr int kSettleTop = 128;  // of those, settled first to raise the best-so-far (above this many)
 constexpr int kTimeCols = 256;   // time-local wave: columns on each side of a row tile
 constexpr int kFillCols = 2048;  // half-width of the neighbourhood of rows the band wave left unbounded
 
@@ -1061,6 +1062,18 @@ cudaError_t launch_search(dd_plan_s* p, const float* T, dd_result_t* out_dev, cu
             // best-so-far with their FP32 lower bounds.  Skipped on the device for
             // short lists.
             q.begin_if(cands.cnt_dev, kSettleMin);
+            // The rows of largest upper bound first (none when at most kSettleTop rows
+            // remain): their FP32 lower bounds raise bsf close to the discord's distance,
+            // so that the full settle wave below abandons the other rows early instead
+            // of scanning all their columns.
+            q.topk(cands, kSettleTop, cands.cnt_dev);
+            ListRef st = q.compact(cands, p->list[0], 1);
+            const int* sm1 = q.ranges(st, 1, 0);
+            q.scan(DD_WAVE_SETTLE, st, ColSpec{2, 0, 0, 0}, 1, sm1, false, true, 0);
+            const int g1 = (int)((p->N + 1023) / 1024);
+            k_complete32<<<g1 < 1024 ? g1 : 1024, 256, 0, q.s>>>(st, p->rmin, q.tb, p->stats, p->n, 0, p->ctrl);
+            p->launches++;
+            q.check();
             const int* sm = q.ranges(cands, 1, 0);
             q.scan(DD_WAVE_SETTLE, cands, ColSpec{2, 0, 0, 0}, 1, sm, false, true, kSettleMin);
             const int g = (int)((p->N + 1023) / 1024);
