@@ -702,7 +702,7 @@ __device__ void b_select_bin(const int* hist, int bins, int need, int* out_bin, 
 // find the threshold; ties at the last level are taken in any order.
 __global__ void __launch_bounds__(kPT) k_b_top(BArr A) {
     __shared__ int hist[kMuBins];
-    __shared__ int s_claim, s_b1, s_a1, s_b2, s_a2, s_cnt, s_tie, s_nfin;
+    __shared__ int s_claim, s_b1, s_a1, s_b2, s_a2, s_cnt, s_tie;
     __shared__ int shi[33];
     const int tid = threadIdx.x;
     BGrp* G = A.G;
@@ -789,7 +789,7 @@ __global__ void __launch_bounds__(kPT) k_b_surv(BArr A) {
     __shared__ int s_claim, s_t0;
     __shared__ int shi[33];
     __shared__ unsigned shu[32];
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int tid = threadIdx.x, lane = tid & 31;
     BGrp* G = A.G;
     for (;;) {
         const int k = claim_series(&G->surv_next, &s_claim);
@@ -855,7 +855,6 @@ __global__ void __launch_bounds__(kPT) k_b_surv(BArr A) {
             A.tser_rest[t0 + t] = s;
             atomicMax(&G->ctrl.smax[1], r.w);
         }
-        (void)wid;
     }
 }
 
