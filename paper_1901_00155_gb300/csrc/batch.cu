@@ -33,8 +33,14 @@
 //                rows; the rows whose upper bound still reaches it are compacted
 //                into whole tiles of their own series
 //   rest wave    their scans, abandoned against the series' best-so-far
-//   k_b_cands    per series: final best-so-far, the candidates and their FP64
-//                column ranges
+//   k_b_cands    per series: best-so-far raised by the completed survivors; the
+//                candidates go to the FP64 rescoring, or, when there are more
+//                than settle_min of them, into settle tiles of settle_rows rows
+//   settle wave  direct FP32 full scans of the settle tiles (scan_fp32.cu),
+//                rigorous FP32 upper bounds r32, rows abandoned against the
+//                series' best-so-far
+//   k_b_cands2   per series: best-so-far raised by the settled rows' FP32
+//                lower bounds; the settled rows that still reach it go to FP64
 //   k_b_rescore  exact FP64 nearest-neighbour distances of the candidates
 //   k_b_best     per series: the largest exact value, smallest index -> result
 #include <cuda_bf16.h>
